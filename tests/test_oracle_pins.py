@@ -1,0 +1,328 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix.
+
+Each test ties the oracle to something other than itself: printed values of the
+worked examples (tests/golden/), closed forms of uniform B-spline integrals,
+an independent B-spline implementation (scipy), the exact Galerkin matrices on
+affine maps (element-wise Gauss brute force), and invariants (partition of
+unity, minimum norm, volume). tests/test_oracle_mutations.py checks that
+plausible mistakes planted in the oracle fail at least one of these pins.
+"""
+import math
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+from conftest import read_golden
+from oracle import wq_oracle as wo
+from oracle import rows_c
+from wq_synth import (affine_cube, graded_breaks, open_knot_vector, perturbed_cube,
+                      uniform_breaks)
+
+
+def _interior_direction(p, h=2.0):
+    chi = np.arange(-10 * (p + 1), 10 * (p + 1) + 1, 1.0) * h
+    d = wo.Direction(open_knot_vector(chi, p), p)
+    i = [k for k in range(d.n) if d.xi[k] == 0.0][-1]   # support [0, (p+1) h]
+    assert d.xi[i + p + 1] == (p + 1) * h
+    return d, i
+
+
+# --- Section 2 worked examples -------------------------------------------------
+
+@pytest.mark.parametrize("p", [1, 2, 3])
+def test_interior_weights_match_printed(p):
+    gold = read_golden("interior_weights.txt")[f"p={p}"]
+    for h in (2.0, 0.125):
+        d, i = _interior_direction(p, h)
+        w = d.W[0, 0, i, d.Q[i]] / h
+        assert len(w) == 2 * p + 1
+        np.testing.assert_allclose(w, gold, rtol=1e-12, atol=1e-14)
+
+
+@pytest.mark.parametrize("p", [1, 2])
+def test_interior_integrals_match_printed(p):
+    gold = read_golden("interior_integrals.txt")[f"p={p}"]
+    d, i = _interior_direction(p, 2.0)
+    got = d.integrals[0, 0, i, d.I[i]] / 2.0
+    np.testing.assert_allclose(got, gold, rtol=0, atol=1e-15)
+
+
+@pytest.mark.parametrize("p", [2, 3])
+def test_bspline_values_match_printed(p):
+    gold = read_golden("bspline_values.txt")[f"p={p}"]
+    d, i = _interior_direction(p, 2.0)
+    x = np.arange(1.0, 2 * p + 2)
+    got = wo.bspline_all(d.xi, p, x, 0)[:, i]
+    np.testing.assert_allclose(got, gold, rtol=0, atol=1e-15)
+
+
+def test_asymmetry_example_matches_printed():
+    gold = read_golden("asymmetry.txt")
+    d, i = _interior_direction(3, 2.0)
+    j = i + 1
+    qi, qj = d.Q[i], d.Q[j]
+    np.testing.assert_array_equal(d.x[qi], np.arange(1.0, 8.0))
+    v_ij = np.sum(d.W[0, 0, i, qi] * d.x[qi] * d.B[0][j, qi])
+    v_ji = np.sum(d.W[0, 0, j, qj] * d.x[qj] * d.B[0][i, qj])
+    assert abs(v_ij - gold["Q_i(c B_j)"][0]) < 5e-5
+    assert abs(v_ji - gold["Q_j(c B_i)"][0]) < 5e-5
+    assert v_ij != v_ji
+
+
+# --- closed forms of uniform integrals (textbook convolution identities) ----------
+
+@pytest.mark.parametrize("p", [2, 3, 4, 5, 6, 8])
+def test_interior_integrals_closed_forms(p):
+    h = 0.25
+    d, i = _interior_direction(p, h)
+    k = np.arange(-p, p + 1)
+    N = wo.cardinal_bspline
+    mass = h * N(2 * p + 1, p + 1 + k)
+    dd = -(N(2 * p - 1, p + 1 + k) - 2 * N(2 * p - 1, p + k) + N(2 * p - 1, p + k - 1)) / h
+    d10 = N(2 * p, p + 1 + k) - N(2 * p, p + k)          # int B'_i B_{i+k}
+    I = d.I[i]
+    np.testing.assert_allclose(d.integrals[0, 0, i, I], mass, rtol=1e-13, atol=1e-15)
+    np.testing.assert_allclose(d.integrals[1, 1, i, I], dd, rtol=1e-12, atol=1e-12)
+    np.testing.assert_allclose(d.integrals[1, 0, i, I], d10, rtol=1e-12, atol=1e-14)
+    np.testing.assert_allclose(d.integrals[0, 1, i, I], -d10, rtol=1e-12, atol=1e-14)
+
+
+@pytest.mark.parametrize("p", [2, 4, 7])
+def test_integrals_independent_of_gauss_count(p):
+    kv = open_knot_vector(graded_breaks(7, seed=3), p)
+    ref = wo.exact_integrals(kv, p, p + 1)
+    for ng in (p + 2, p + 5):
+        np.testing.assert_allclose(wo.exact_integrals(kv, p, ng), ref, rtol=0, atol=1e-12)
+
+
+# --- B-splines against scipy ------------------------------------------------------
+
+@pytest.mark.parametrize("p", [1, 2, 3, 5, 8])
+def test_bsplines_against_scipy(p):
+    interp = pytest.importorskip("scipy.interpolate")
+    kv = open_knot_vector(graded_breaks(6, seed=11), p)
+    x = np.linspace(0.0, 1.0, 97)[1:-1]
+    n = len(kv) - p - 1
+    ours0 = wo.bspline_all(kv, p, x, 0)
+    ours1 = wo.bspline_all(kv, p, x, 1)
+    for j in range(n):
+        c = np.zeros(n)
+        c[j] = 1.0
+        s = interp.BSpline(kv, c, p)
+        np.testing.assert_allclose(ours0[:, j], s(x), atol=1e-14)
+        if p >= 1:
+            np.testing.assert_allclose(ours1[:, j], s.derivative(1)(x), atol=1e-11)
+    np.testing.assert_allclose(ours0.sum(1), 1.0, atol=1e-14)
+    np.testing.assert_allclose(ours1.sum(1), 0.0, atol=1e-11)
+
+
+# --- the point grid (Remark on the choice of points) -------------------------------
+
+@pytest.mark.parametrize("p,nel", [(2, 2), (2, 16), (4, 3), (4, 64), (8, 9)])
+def test_point_grid(p, nel):
+    chi = uniform_breaks(nel)
+    x = wo.quadrature_points(chi, p)
+    assert len(x) == 2 * nel + 2 * p - 1
+    assert np.all(np.diff(x) > 0) and x[0] > 0.0 and x[-1] < 1.0
+    for k in range(1, nel):                     # every interior knot is a point
+        assert np.any(x == chi[k])
+    in_first = x[x < chi[1]]
+    np.testing.assert_allclose(in_first, chi[1] * np.arange(1, p + 2) / (p + 2), rtol=1e-15)
+    d = wo.Direction(open_knot_vector(chi, p), p)
+    for i in range(d.n):                        # Eq. (numb_nodes)
+        assert len(d.Q[i]) >= len(d.I[i])
+        if p + 1 <= i <= d.n - p - 2:           # support avoids both boundary spans
+            assert len(d.Q[i]) == 2 * p + 1
+
+
+# --- rules: exactness, support, minimum norm ---------------------------------------
+
+def _rule_cases():
+    for p in (2, 3, 4, 5, 8):
+        for nel in (2, 3, 7):
+            yield p, uniform_breaks(nel)
+        yield p, graded_breaks(9, seed=p)
+
+
+@pytest.mark.parametrize("p,breaks", list(_rule_cases()))
+def test_rules_exact_supported_minimum_norm(p, breaks):
+    d = wo.Direction(open_knot_vector(breaks, p), p)
+    for a in (0, 1):
+        for b in (0, 1):
+            for i in range(d.n):
+                I, Q = d.I[i], d.Q[i]
+                w = d.W[a, b, i]
+                outside = np.setdiff1d(np.arange(d.nqp), Q)
+                assert np.all(w[outside] == 0.0)                        # Eq. (support)
+                rhs = d.integrals[a, b, i, I]
+                res = d.B[b][I] @ w - rhs                               # Eq. (exact), float64
+                scale = np.abs(d.B[b][I]) @ np.abs(w) + np.abs(rhs)
+                assert np.all(np.abs(res) <= 64 * np.finfo(float).eps * scale)
+                # the same conditions on the unrounded data: residual at the level
+                # of the 80-digit solve, every equation including a dropped one
+                wex = d.W_exact[(a, b, i)]
+                for j in I:
+                    lhs = sum((d.B_exact.get((b, int(j), int(q)), 0) * wq
+                               for q, wq in zip(Q, wex)), Fraction(0))
+                    ex = d.I_exact.get((a, b, i, int(j)), Fraction(0))
+                    assert abs(lhs - ex) <= Fraction(1, 10 ** 40) * (1 + abs(ex))
+                # minimum norm: w is orthogonal to the null space of the system matrix
+                M = d.B[b][np.ix_(I, Q)]
+                M = M / np.linalg.norm(M, axis=1, keepdims=True)      # row scaling keeps the solution set
+                _, s, Vt = np.linalg.svd(M)
+                rank = int(np.sum(s > 1e-12 * s[0]))
+                assert rank == len(I) - b
+                null = Vt[rank:]
+                cond = s[0] / s[rank - 1]
+                tol = max(1e-13, 100 * np.finfo(float).eps * cond)
+                assert np.linalg.norm(null @ w[Q]) <= tol * np.linalg.norm(w[Q])
+
+
+def test_rules_b1_rank_deficient_by_one():
+    for p in (2, 4, 6):
+        d = wo.Direction(open_knot_vector(uniform_breaks(12), p), p)
+        for i in range(d.n):
+            M = d.B[1][np.ix_(d.I[i], d.Q[i])]
+            np.testing.assert_allclose(M.sum(0), 0.0, atol=1e-12 * np.abs(M).max())
+            M = M / np.linalg.norm(M, axis=1, keepdims=True)
+            s = np.linalg.svd(M, compute_uv=False)
+            assert s[-1] < 1e-13 * s[0] and s[-2] > 1e-8 * s[0]
+
+
+def test_rule_weights_positive_kind00_interior():
+    # Figure 2 caption: numerical evidence of positive (0,0) weights.
+    for p in (2, 3, 4, 5):
+        d, i = _interior_direction(p, 1.0)
+        assert np.all(d.W[0, 0, i, d.Q[i]] > 0)
+
+
+# --- coefficients ------------------------------------------------------------------
+
+def test_jacobian_against_finite_differences():
+    interp = pytest.importorskip("scipy.interpolate")
+    patch = perturbed_cube(3, (4, 5, 3), seed=7)
+    orc = wo.Oracle3D(patch.p, patch.knots, patch.ctrl)
+    n1, n2, n3 = orc.n
+    C = patch.ctrl.reshape(n3, n2, n1, 3)
+
+    def design(kv, p, x):
+        n = len(kv) - p - 1
+        return np.stack([interp.BSpline(kv, np.eye(n)[j], p)(x) for j in range(n)], 1)
+
+    def F(z):
+        D = [design(patch.knots[k], patch.p, np.array([z[k]])) for k in range(3)]
+        return np.einsum("kjir,i,j,k->r", C, D[0][0], D[1][0], D[2][0])
+
+    J = wo.jacobians(orc.dirs, patch.ctrl)
+    rng = np.random.default_rng(0)
+    for _ in range(6):
+        q = [int(rng.integers(0, orc.nqp[k])) for k in range(3)]
+        z = np.array([orc.dirs[k].x[q[k]] for k in range(3)])
+        eps = 1e-6
+        fd = np.stack([(F(z + eps * e) - F(z - eps * e)) / (2 * eps) for e in np.eye(3)], 1)
+        np.testing.assert_allclose(J[q[2], q[1], q[0]], fd, atol=1e-7)
+
+
+def test_coefficients_affine_closed_form():
+    A = np.array([[1.3, 0.2, -0.1], [0.1, 0.9, 0.3], [0.0, -0.2, 1.1]])
+    patch = affine_cube(2, (3, 2, 4), A, np.array([0.5, -1.0, 2.0]))
+    orc = wo.Oracle3D(patch.p, patch.knots, patch.ctrl)
+    Ai = np.linalg.inv(A)
+    P = np.linalg.det(A) * Ai @ Ai.T
+    for s, (l, m) in enumerate(wo.COEF_LM):
+        np.testing.assert_allclose(orc.coef[s], P[l, m], rtol=1e-13)
+    np.testing.assert_allclose(orc.coef[6], np.linalg.det(A), rtol=1e-13)
+
+
+# --- whole matrices ------------------------------------------------------------------
+
+AFFINE_CASES = [
+    (2, (2, 3, 2), None),
+    (3, (3, 2, 2), None),
+    (2, (3, 3, 3), "graded"),
+]
+
+
+@pytest.mark.parametrize("p,nel,kind", AFFINE_CASES)
+def test_wq_equals_galerkin_on_affine_maps(p, nel, kind):
+    A = np.array([[1.2, 0.3, 0.1], [-0.2, 0.8, 0.25], [0.15, -0.1, 1.05]])
+    breaks = None
+    if kind == "graded":
+        breaks = [graded_breaks(e, seed=20 + k) for k, e in enumerate(nel)]
+    patch = affine_cube(p, nel, A, np.array([0.1, 0.2, 0.3]), breaks=breaks)
+    orc = wo.Oracle3D(p, patch.knots, patch.ctrl)
+    S_wq, M_wq = orc.dense("stiffness"), orc.dense("mass")
+    S_g, M_g = wo.galerkin_dense(p, patch.knots, patch.ctrl)
+    np.testing.assert_allclose(S_wq, S_g, rtol=0, atol=1e-12 * np.abs(S_g).max())
+    np.testing.assert_allclose(M_wq, M_g, rtol=0, atol=1e-12 * np.abs(M_g).max())
+    assert abs(M_wq.sum() - np.linalg.det(A)) < 1e-12
+    # WQ matrix structure: nonzeros only inside the band |i_k - j_k| <= p
+    assert np.count_nonzero(S_wq[np.abs(S_wq) > 0]) <= orc.row_ptr()[-1]
+
+
+def test_wq_differs_from_galerkin_on_curved_maps():
+    patch = perturbed_cube(2, 3, seed=5, amp=0.05)
+    orc = wo.Oracle3D(2, patch.knots, patch.ctrl)
+    S_g, _ = wo.galerkin_dense(2, patch.knots, patch.ctrl, ng=6)
+    S_wq = orc.dense("stiffness")
+    rel = np.abs(S_wq - S_g).max() / np.abs(S_g).max()
+    assert 1e-6 < rel < 0.05                    # an approximation, not a copy of Galerkin
+    assert np.abs(S_wq - S_wq.T).max() > 1e-10  # and not symmetric (Remark on symmetry)
+
+
+def test_stiffness_rows_annihilate_constants():
+    patch = perturbed_cube(3, (4, 3, 5), seed=9, amp=0.1)
+    orc = wo.Oracle3D(3, patch.knots, patch.ctrl)
+    N = np.prod(orc.n)
+    for r in range(0, N, 7):
+        v = orc.row_values(r, "stiffness")
+        assert abs(v.sum()) <= 1e-13 * np.abs(v).max() * len(v)
+
+
+def test_mass_of_perturbed_cube_close_to_volume():
+    patch = perturbed_cube(2, 4, seed=13, amp=0.05)
+    orc = wo.Oracle3D(2, patch.knots, patch.ctrl)
+    _, M_g = wo.galerkin_dense(2, patch.knots, patch.ctrl, ng=8)
+    vol = M_g.sum()
+    tot = orc.dense("mass").sum()
+    assert abs(tot - vol) < 1e-3 * vol and abs(vol - 1.0) < 0.05
+
+
+def test_kappa_scales_coefficients():
+    patch = perturbed_cube(2, 3, seed=2)
+    base = wo.Oracle3D(2, patch.knots, patch.ctrl)
+    kappa = np.linspace(0.5, 1.5, np.prod(base.nqp))
+    scaled = wo.Oracle3D(2, patch.knots, patch.ctrl, kappa=kappa)
+    np.testing.assert_allclose(scaled.coef, base.coef * kappa.reshape(base.coef.shape[1:])[None])
+
+
+# --- pattern ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("p,nel", [(2, (2, 3, 4)), (3, (5, 2, 3)), (4, (9, 9, 9))])
+def test_pattern_counts(p, nel):
+    patch = perturbed_cube(p, nel, seed=1, amp=0.0)
+    n = patch.n
+    nnz1 = [(2 * p + 1) * nl - p * (p + 1) for nl in n]       # d = 1 formula, Section 3
+    if max(nel) <= 4:
+        orc = wo.Oracle3D(p, patch.knots, patch.ctrl)
+        rp = orc.row_ptr()
+        assert rp[-1] == np.prod(nnz1)
+        cols = orc.row_cols(len(rp) // 2)
+        assert np.all(np.diff(cols) > 0)
+    else:
+        d = [wo.Direction(k, p) for k in patch.knots]
+        assert [sum(len(I) for I in dd.I) for dd in d] == nnz1
+
+
+# --- the C restatement against the Python oracle ----------------------------------------
+
+@pytest.mark.parametrize("which", ["stiffness", "mass"])
+def test_c_rows_match_python_rows(which):
+    patch = perturbed_cube(3, (5, 4, 6), seed=4, amp=0.05)
+    orc = wo.Oracle3D(3, patch.knots, patch.ctrl)
+    rows = np.array([0, 1, 7, 33, 60, 61, np.prod(orc.n) - 1])
+    got = rows_c(orc, rows, which, threads=2)
+    for r, g in zip(rows, got):
+        ref = orc.row_values(int(r), which)
+        np.testing.assert_allclose(g, ref, rtol=0, atol=1e-14 * np.abs(ref).max())
