@@ -1,0 +1,375 @@
+"""Benchmark: WQ 3D stiffness assembly throughput (nnz/s) on one or more GB300s.
+
+One step = the whole path from control points already resident in HBM to the
+CSR stiffness matrix: every set-up kernel of the plan (points, B-spline tables,
+exact integrals, WQ rules, CSR pattern, coefficients; wq_plan_refresh) followed
+by the fused sum-factorised FP64 assembly (wq_assemble_stiffness). Workload:
+p = 4, 64 elements per direction (N_DOF = 68^3, nnz = 592^3), degree-4 spline
+cube with control points at the Greville abscissae plus a seeded +-0.05 h
+perturbation. Every step writes 1.66 GB of values and 0.83 GB of column
+indices, far more than the 126 MB L2, so no L2 flush is inserted.
+
+  python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+
+Under torchrun each rank assembles its own independent copy of the workload
+(weak scaling, no data-path collective); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "WQ 3D stiffness nnz/s and % of HBM-write roofline; mixed vs FP64 at ≤1e-6 error"
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def fp64_peak_tflops(sm_max_mhz: float) -> float:
+    # 152 SMs x 2 FP64 FMA lanes per SM per clock x 2 flops, at the maximum SM clock
+    return 152 * 2 * 2 * sm_max_mhz * 1e6 / 1e12
+
+
+def stiffness_flops_per_nnz(p: int) -> float:
+    """FLOPs per nonzero of the halo-free sum factorisation the kernel implements
+    (each multiply or fused multiply-add counted as 2 flops), interior rows."""
+    b = 2 * p + 1
+    o = 2 * p * p + 2 * p + 1            # sum over j of |Q_i n Q_j| (structural zeros skipped)
+    stage1 = (4 * b + 2 * o) / b
+    stage2 = 2 * (9 * b + 6 * o) / b ** 2
+    stage3 = 4 * 9 * o / b ** 3
+    return 2 * (stage1 + stage2 + stage3)
+
+
+def mass_flops_per_nnz(p: int) -> float:
+    b = 2 * p + 1
+    o = 2 * p * p + 2 * p + 1
+    return 2 * ((b + o) / b + 2 * (b + o) / b ** 2 + 4 * o / b ** 3)
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.file = None
+
+    def start(self):
+        try:
+            self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.file, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.file.flush()
+        rows = []
+        with open(self.file.name) as f:
+            for line in f:
+                parts = [s.strip() for s in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.file.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        loaded = [v for v in sm if v > 0.5 * max(sm)] if sm else []
+        return {"sm_mhz": statistics.median(loaded) if loaded else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
+
+
+def dist_setup(n_gpus: int):
+    import torch
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        return rank, world, local, dist
+    torch.cuda.set_device(0)
+    return 0, 1, 0, None
+
+
+def barrier(dist):
+    if dist is not None:
+        dist.barrier()
+
+
+def max_over_ranks(dist, value: float) -> float:
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def cpu_oracle_sample(patch, seconds: float, seed: int, which: str = "stiffness"):
+    """Time the oracle's C entry sums on host cores over a bounded row sample."""
+    from oracle import Oracle3D, rows_c
+    from wq_synth import sample_rows
+    threads = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    orc = Oracle3D(patch.p, patch.knots, patch.ctrl)
+    setup_s = time.perf_counter() - t0
+    probe = sample_rows(orc.n, orc.p, 27, seed=seed)[:threads]
+    t0 = time.perf_counter()
+    rows_c(orc, probe, which, threads=threads)
+    per_batch = time.perf_counter() - t0
+    count = max(threads, int(len(probe) * seconds / max(per_batch, 1e-3)))
+    rows = sample_rows(orc.n, orc.p, count, seed=seed + 1)
+    t0 = time.perf_counter()
+    vals = rows_c(orc, rows, which, threads=threads)
+    dt = time.perf_counter() - t0
+    nnz = sum(len(v) for v in vals)
+    return {"nnz_per_s": nnz / dt, "rows": len(rows), "nnz": nnz, "seconds": dt, "threads": threads,
+            "setup_seconds": setup_s}
+
+
+def run_reference(args):
+    """--impl reference: the CPU oracle, as it stands, on the machine's host cores."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    from wq_synth import workload_p4_64
+    patch = workload_p4_64()
+    from oracle import Oracle3D, rows_c
+    from wq_synth import sample_rows
+    threads = os.cpu_count() or 1
+    orc = Oracle3D(patch.p, patch.knots, patch.ctrl)
+    probe = sample_rows(orc.n, orc.p, 27, seed=8999)[:threads]
+    t0 = time.perf_counter()
+    rows_c(orc, probe, "stiffness", threads=threads)
+    per_row = (time.perf_counter() - t0) / len(probe)
+    per_step = max(threads, int(args.ref_step_seconds / max(per_row, 1e-6)))
+    rates = []
+    total_nnz, total_s = 0, 0.0
+    for step in range(args.warmup + args.steps):
+        rows = sample_rows(orc.n, orc.p, per_step, seed=9000 + step)
+        t0 = time.perf_counter()
+        vals = rows_c(orc, rows, "stiffness", threads=threads)
+        dt = time.perf_counter() - t0
+        nnz = sum(len(v) for v in vals)
+        if step >= args.warmup:
+            rates.append(nnz / dt)
+            total_nnz += nnz
+            total_s += dt
+    value = total_nnz / total_s
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "nnz/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded perturbed spline cube)",
+        "config": {"workload": "WQ stiffness, p=4, 64^3 elements, N_DOF=68^3, nnz=592^3", "p": 4,
+                   "n_el": 64, "n_dof": int(np.prod(orc.n)), "nnz": int(np.prod([sum(len(I) for I in d.I)
+                                                                                 for d in orc.dirs]))},
+        "cpu_baseline": {"value": value, "unit": "nnz/s", "cores": threads, "kind": "oracle",
+                         "sample": f"{per_step} seeded rows per step (C nested WQ sums, all terms)"},
+        "e2e": {"value": value, "unit": "nnz/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+
+    import paper_1605_01238_gb300 as wq
+    from wq_synth import perturbed_cube, workload_p4_64
+    rank, world, local, dist = dist_setup(args.gpus)
+    patch = workload_p4_64() if (args.p, args.nel) == (4, 64) else \
+        perturbed_cube(args.p, args.nel, seed=1605 + 1)
+    p = patch.p
+    plan = wq.Plan(p, patch.knots, patch.ctrl)
+    nnz, N = plan.nnz, plan.n_rows
+    ctrl_d = torch.as_tensor(patch.ctrl.reshape(-1), device="cuda")
+    vals = torch.empty(nnz, dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def step(ev=None):
+        plan.refresh(ctrl_d)
+        if ev is not None:
+            ev[0].record(stream)
+        plan.stiffness(out=vals)
+        if ev is not None:
+            ev[1].record(stream)
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    plan.sync_check()
+
+    # timed region
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    kev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    launches0 = wq.launch_count()
+    barrier(dist)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for k in range(args.steps):
+        step(kev[k])
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(dist)
+    launches = wq.launch_count() - launches0
+    clocks = sampler.stop()
+    ms_total = e0.elapsed_time(e1)
+    ms_total = max_over_ranks(dist, ms_total)
+    ms_step = ms_total / args.steps
+    kernel_ms = statistics.mean(a.elapsed_time(b) for a, b in kev)
+    plan.sync_check()
+    value = world * nnz / (ms_step * 1e-3)
+    if args.steps_only:
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "value": value, "unit": "nnz/s", "ms_per_step": ms_step,
+                              "assembly_ms": kernel_ms, "p": p, "n_el": args.nel, "nnz": nnz,
+                              "gpu_launches": int(launches)}), flush=True)
+        plan.close()
+        if dist is not None:
+            dist.destroy_process_group()
+        return 0
+
+    # variants (not part of the headline): assembly alone, mass, FP32 contractions
+    def timed(fn, reps=5):
+        fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps
+
+    mass_ms = timed(lambda: plan.mass(out=vals))
+    vals32 = torch.empty(nnz, dtype=torch.float32, device="cuda")
+    f32_ms = timed(lambda: plan.stiffness(out=vals32, dtype=torch.float32, precision="fp32"))
+    f32_f64_ms = timed(lambda: plan.stiffness(out=vals, precision="fp32"))
+    refresh_ms = timed(lambda: plan.refresh(ctrl_d))
+    del vals32
+
+    # end to end through the C ABI with host buffers (pinned)
+    h_ctrl = torch.as_tensor(patch.ctrl.reshape(-1)).pin_memory()
+    h_vals = torch.empty(nnz, dtype=torch.float64).pin_memory()
+    plan.assemble_host("stiffness", h_ctrl, vals, h_vals)
+    barrier(dist)
+    t0 = time.perf_counter()
+    e2e_steps = max(1, min(args.steps, 5))
+    for _ in range(e2e_steps):
+        plan.assemble_host("stiffness", h_ctrl, vals, h_vals)
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    e2e_s = max_over_ranks(dist, e2e_s)
+
+    pk, pk_kind = peaks()
+    fpn = stiffness_flops_per_nnz(p)
+    peak_tf = fp64_peak_tflops(pk.get("sm_max_mhz", 2070.0))
+    achieved_tf = fpn * nnz / (kernel_ms * 1e-3) / 1e12
+    hbm = pk["hbm_gbs"]
+    write_gbs = 8.0 * nnz / (ms_step * 1e-3) / 1e9
+    line = {
+        "metric": METRIC, "value": value, "unit": "nnz/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded perturbed degree-4 spline cube, Greville + U[-0.05h, 0.05h])",
+        "config": {"workload": f"WQ stiffness, p={p}, {args.nel}^3 elements, N_DOF={N}, nnz={nnz} per GPU",
+                   "p": p, "n_el": args.nel, "n_dof": N, "nnz_per_gpu": nnz,
+                   "step": "plan refresh (points, tables, integrals, rules, CSR pattern, coefficients) "
+                           "+ FP64 stiffness assembly",
+                   "l2": "no flush: each step writes 2.5 GB (values + columns) > 126 MB L2",
+                   "parallelism": f"{world} independent patches, one per GPU"},
+        "roofline": {"bound": "alu", "achieved": achieved_tf, "peak": peak_tf, "unit": "TFLOP/s",
+                     "frac": achieved_tf / peak_tf, "traffic": None,
+                     "kernel": f"k_assemble<{p},stiffness,fp64>",
+                     "note": f"FP64 FMA pipe: {fpn:.1f} algorithmic flop/nnz; peak = 152 SMs x 2 DFMA/clk "
+                             f"x {pk.get('sm_max_mhz', 2070.0):.0f} MHz (derived; a DFMA probe measured "
+                             "1.20 TFLOP/s)"},
+        "hbm_write": {"achieved_gbs": write_gbs, "peak_gbs": hbm, "frac": write_gbs / hbm,
+                      "peak_kind": f"{pk_kind} copy bandwidth"},
+        "breakdown_ms": {"assembly": kernel_ms, "refresh": refresh_ms, "mass_fp64": mass_ms,
+                         "stiffness_fp32_f32vals": f32_ms, "stiffness_fp32_f64vals": f32_f64_ms},
+        "variants_nnz_per_s": {"stiffness_fp64_assembly_only": nnz / (kernel_ms * 1e-3),
+                               "mass_fp64_assembly_only": nnz / (mass_ms * 1e-3),
+                               "stiffness_fp32_f32vals": nnz / (f32_ms * 1e-3),
+                               "stiffness_fp32_f64vals": nnz / (f32_f64_ms * 1e-3)},
+        "e2e": {"value": world * nnz / e2e_s, "unit": "nnz/s", "h2d_bytes_per_step": 8 * 3 * N,
+                "d2h_bytes_per_step": 8 * nnz,
+                "call": "wq_assemble_host: H2D control points, refresh, assemble, D2H values"},
+        "gpu_launches": int(launches), "clocks": clocks,
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        cb = cpu_oracle_sample(patch, seconds=args.cpu_seconds, seed=4242)
+        line["cpu_baseline"] = {"value": cb["nnz_per_s"], "unit": "nnz/s", "cores": cb["threads"],
+                                "kind": "oracle",
+                                "sample": f"{cb['rows']} seeded rows ({cb['nnz']} nnz) of the same workload, "
+                                          f"C nested WQ sums, {cb['seconds']:.1f} s; oracle set-up "
+                                          f"{cb['setup_seconds']:.1f} s not included"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    plan.close()
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--ref-step-seconds", type=float, default=4.0,
+                    help="CPU seconds of oracle work per step of --impl reference")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--p", type=int, default=4, help="degree (default: the p=4 workload)")
+    ap.add_argument("--nel", type=int, default=64, help="elements per direction (default 64)")
+    ap.add_argument("--steps-only", action="store_true",
+                    help="time the steps only (no variants, e2e or CPU baseline); for profiler captures")
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

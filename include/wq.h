@@ -1,0 +1,171 @@
+/*
+ * wq.h - C ABI of the GB300 weighted-quadrature (WQ) assembly library.
+ *
+ * The library forms the 3D isogeometric Poisson stiffness matrix S and mass
+ * matrix M of a single-patch spline geometry by weighted quadrature
+ * (Calabro, Sangalli, Tani, "Fast formation of isogeometric Galerkin matrices
+ * by weighted quadrature"), as a CSR matrix in device memory of one GPU:
+ *
+ *   s_ij ~ sum_{l,m} Q_i( c_lm d_m B_j )   (Eq. (stiff), Eq. (coef_stiff))
+ *   m_ij ~ Q_i( c B_j )                    (Eq. (Mass_approx), Eq. (massquadrature))
+ *
+ * Conventions shared by every entry point:
+ *  - Degree p is the same in the three directions, 2 <= p <= 8; each knot vector
+ *    is open (end knots repeated p+1 times) with simple, strictly increasing
+ *    interior knots (maximal regularity C^{p-1}, Section 3), and at least two
+ *    spans per direction.
+ *  - Multi-indices i = (i1, i2, i3) are linearised as i1 + n1*(i2 + n2*i3),
+ *    direction 1 fastest (Section 3).
+ *  - Matrices are full, non-symmetric CSR (WQ does not preserve symmetry,
+ *    Section 2 and the Remark on convergence rates): row_ptr int64[N+1],
+ *    col int32[nnz], columns ascending inside each row; the pattern of row i is
+ *    I_i = I_{1,i1} x I_{2,i2} x I_{3,i3} with I_{l,i} = {j : |i - j| <= p}.
+ *  - "d_" pointers are device pointers of the current CUDA device, "h_" host
+ *    pointers. `stream` is a cudaStream_t (NULL = legacy default stream); every
+ *    asynchronous call only enqueues work on it.
+ *  - Every call returns a wq_status; no exception crosses the ABI and no call
+ *    falls back to the CPU. wq_last_error() gives a message for the calling
+ *    thread. Errors found on the device (det DF <= 0, a breakdown of a rule
+ *    solve, a timed-out wait) are recorded in a device error word and reported
+ *    by wq_sync_check() or by the next synchronous call.
+ */
+#ifndef WQ_H
+#define WQ_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct wq_plan_s* wq_plan_t;
+
+typedef enum wq_status {
+  WQ_OK = 0,
+  WQ_ERR_INVALID_ARG = 1,    /* bad degree, knots, sizes or NULL pointer */
+  WQ_ERR_UNSUPPORTED = 2,    /* d != 3, or an option this build does not provide */
+  WQ_ERR_SINGULAR_RULE = 3,  /* a rule system of Algorithm 2 broke down */
+  WQ_ERR_BAD_GEOMETRY = 4,   /* det DF <= 0 or not finite at a quadrature point */
+  WQ_ERR_OOM = 5,            /* device allocation failed */
+  WQ_ERR_CUDA = 6,           /* a CUDA runtime call failed (or no device) */
+  WQ_ERR_TIMEOUT = 7,        /* a bounded device wait gave up */
+  WQ_ERR_INJECTED = 8        /* failure injected on the host for testing */
+} wq_status;
+
+/* Value type of the output array. */
+enum { WQ_VALUES_F64 = 0, WQ_VALUES_F32 = 1 };
+
+/* Arithmetic of the contraction stages (Eq. (sumfactorization)). The geometry
+ * Jacobian, its inverse and determinant always run in FP64. */
+enum {
+  WQ_PREC_FP64 = 0,          /* FP64 FMA throughout */
+  WQ_PREC_FP32 = 1           /* FP32 FMA, FP32 intermediates */
+};
+
+/* ---- plan ------------------------------------------------------------------
+ * wq_plan_create: builds everything that depends only on the mesh and the
+ * geometry (Algorithm 1 and Algorithm 2, plus the CSR pattern):
+ *   quadrature points (Remark on the choice of points), B-spline values and
+ *   derivatives at the points, exact univariate integrals I^{(a,b)}
+ *   (Eq. (integrals)), the four WQ rules per test function (Eq. (exact),
+ *   Eq. (support), minimum Euclidean norm, Algorithm 2), the coefficients
+ *   c_lm = det DF (DF^{-1} DF^{-T})_lm and c = det DF at every point
+ *   (Eq. (coef_stiff), Eq. (mass2)), and the CSR pattern.
+ * Arguments:
+ *   plan     out: the new plan (owned by the caller, release with wq_plan_destroy)
+ *   d        dimension; must be 3
+ *   p        degree, 2..8
+ *   n_knots  host int64[3]: length of each full knot vector (= n_l + p + 1)
+ *   h_knots  host double*[3]: the three full open knot vectors
+ *   h_ctrl   host double[N_DOF*3]: control points, xyz interleaved, i1 fastest
+ *   stream   CUDA stream for the set-up work
+ * The call copies its host inputs; they may be freed on return. It
+ * synchronises `stream` once at the end to report device-side errors.
+ */
+wq_status wq_plan_create(wq_plan_t* plan, int d, int p, const int64_t n_knots[3],
+                         const double* const h_knots[3], const double* h_ctrl, void* stream);
+
+/* Releases every device and host resource of a plan. NULL is accepted. */
+wq_status wq_plan_destroy(wq_plan_t plan);
+
+/* Sizes: n[3] functions per direction, n_qp[3] points per direction, the number
+ * of rows N = n1 n2 n3 and of non-zeros nnz = prod_l ((2p+1) n_l - p(p+1))
+ * (Section 3, N_NZ for d = 1). Any output pointer may be NULL. */
+wq_status wq_plan_info(wq_plan_t plan, int* p, int64_t n[3], int64_t n_qp[3],
+                       int64_t* n_rows, int64_t* nnz);
+
+/* Device pointers of the plan-owned CSR pattern (valid until wq_plan_destroy):
+ * row_ptr int64[N+1], col int32[nnz]. */
+wq_status wq_plan_pattern(wq_plan_t plan, const int64_t** d_row_ptr, const int32_t** d_col);
+
+/* Replaces the control points and recomputes the coefficients (Algorithm 1,
+ * last loop) on `stream`, without allocating. ctrl is double[N_DOF*3];
+ * ctrl_on_device = 1 for a device pointer, 0 for a host pointer (copied on
+ * `stream`; the host buffer must stay valid until the stream reaches the copy,
+ * and must be pinned for the copy to be asynchronous). */
+wq_status wq_plan_set_geometry(wq_plan_t plan, const double* ctrl, int ctrl_on_device,
+                               void* stream);
+
+/* Re-runs every set-up kernel of the plan in place on `stream` (points, tables,
+ * integrals, rules, CSR pattern and coefficients), without allocating or
+ * synchronising: the whole path from knots and control points to a matrix is
+ * then wq_plan_refresh + wq_assemble_*. ctrl as in wq_plan_set_geometry, or
+ * NULL to keep the plan's current control points. */
+wq_status wq_plan_refresh(wq_plan_t plan, const double* ctrl, int ctrl_on_device, void* stream);
+
+/* ---- assembly ---------------------------------------------------------------
+ * Writes the nnz values of S (resp. M), in the plan's CSR order, to d_vals.
+ *   d_kappa  NULL, or device double[N_QP] (points q1 fastest): a scalar
+ *            coefficient field multiplying c_lm (resp. c) at every point
+ *            (Eq. (mass2): c absorbs the PDE coefficient)
+ *   d_vals   device array of nnz values of type value_dtype, caller-owned
+ *   value_dtype  WQ_VALUES_F64 or WQ_VALUES_F32
+ *   precision    WQ_PREC_FP64 (requires WQ_VALUES_F64) or WQ_PREC_FP32
+ * Asynchronous on `stream`; no allocation, no synchronisation. */
+wq_status wq_assemble_stiffness(wq_plan_t plan, const double* d_kappa, void* d_vals,
+                                int value_dtype, int precision, void* stream);
+wq_status wq_assemble_mass(wq_plan_t plan, const double* d_kappa, void* d_vals,
+                           int value_dtype, int precision, void* stream);
+
+/* End-to-end call with host buffers: copies h_ctrl (NULL = keep) to the device,
+ * refreshes the plan, assembles S (which = 0) or M (which = 1) in FP64 into the
+ * caller's device staging array d_vals (nnz doubles) and copies the values to
+ * h_vals (nnz doubles; pinned memory makes the copies asynchronous). Returns
+ * after `stream` has finished the copy back. */
+wq_status wq_assemble_host(wq_plan_t plan, int which, const double* h_ctrl, double* d_vals,
+                           double* h_vals, void* stream);
+
+/* ---- errors and bookkeeping --------------------------------------------------- */
+
+/* Synchronises `stream`, then reads and clears the plan's device error word. */
+wq_status wq_sync_check(wq_plan_t plan, void* stream);
+
+/* Message of the last failing call on this thread ("" if none). */
+const char* wq_last_error(void);
+
+/* Static name of a status code. */
+const char* wq_status_string(wq_status status);
+
+/* Number of kernels this library has launched in this process. */
+int64_t wq_launch_count(void);
+
+/* ---- inspection (synchronous device-to-host copies, for tests) --------------------
+ * wq_get_points:  h_x double[n_qp[dir]]
+ * wq_get_rules:   h_w double[n[dir] * nq_max] rule of kind (a, b) for every test
+ *                 function i, row i holding w at q = h_q0[i] + t, t < h_nq[i];
+ *                 h_q0, h_nq int32[n[dir]] (either may be NULL); nq_max from
+ *                 wq_get_nq_max.
+ * wq_get_coefficients: h_coef double[7 * N_QP]: c_11 c_12 c_13 c_22 c_23 c_33 c,
+ *                 each on the point grid q1 fastest. */
+wq_status wq_get_nq_max(wq_plan_t plan, int* nq_max);
+wq_status wq_get_points(wq_plan_t plan, int dir, double* h_x);
+wq_status wq_get_rules(wq_plan_t plan, int dir, int a, int b, double* h_w, int32_t* h_q0,
+                       int32_t* h_nq);
+wq_status wq_get_coefficients(wq_plan_t plan, double* h_coef);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* WQ_H */

@@ -1,0 +1,219 @@
+"""GB300 weighted-quadrature (WQ) assembly of 3D isogeometric stiffness and mass
+matrices (Calabro, Sangalli, Tani, "Fast formation of isogeometric Galerkin
+matrices by weighted quadrature").
+
+A thin Python binding over the C ABI of libwq.so (include/wq.h): it marshals
+arguments and wraps device memory in torch tensors. Every step of the method
+runs in the library's CUDA kernels; there is no CPU path. PyTorch provides
+device memory, streams and sparse CSR tensors.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from ._lib import WqError, check, load
+
+__all__ = ["Plan", "WqError", "launch_count", "load", "VALUES_F64", "VALUES_F32", "PREC_FP64", "PREC_FP32"]
+
+VALUES_F64, VALUES_F32 = 0, 1
+PREC_FP64, PREC_FP32 = 0, 1
+_PREC = {"fp64": PREC_FP64, "fp32": PREC_FP32}
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _stream(stream=None) -> ctypes.c_void_p:
+    torch = _torch()
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _dev_ptr(t, dtype, numel: int, name: str) -> int:
+    torch = _torch()
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype or not t.is_contiguous() or t.numel() != numel:
+        raise ValueError(f"{name} must be a contiguous {dtype} tensor of {numel} elements")
+    return t.data_ptr()
+
+
+class _DeviceView:
+    """__cuda_array_interface__ over plan-owned memory; keeps the plan alive."""
+
+    def __init__(self, ptr: int, shape: tuple, typestr: str, owner):
+        self._owner = owner
+        self.__cuda_array_interface__ = {"shape": shape, "typestr": typestr, "data": (ptr, False),
+                                         "version": 3, "strides": None}
+
+
+def launch_count() -> int:
+    """Kernels launched by libwq in this process."""
+    return int(load().wq_launch_count())
+
+
+class Plan:
+    """Mesh- and geometry-dependent data of one 3D patch (wq_plan_create).
+
+    p: degree (2..8); knots: three full open knot vectors; ctrl: (N_DOF, 3)
+    control points with direction 1 fastest.
+    """
+
+    def __init__(self, p: int, knots, ctrl, stream=None):
+        lib = load()
+        self._knots = [np.ascontiguousarray(k, dtype=np.float64) for k in knots]
+        if len(self._knots) != 3:
+            raise ValueError("three knot vectors are required")
+        ctrl = np.ascontiguousarray(ctrl, dtype=np.float64).reshape(-1, 3)
+        n_knots = (ctypes.c_int64 * 3)(*[len(k) for k in self._knots])
+        kptrs = (ctypes.c_void_p * 3)(*[k.ctypes.data for k in self._knots])
+        h = ctypes.c_void_p()
+        check(lib.wq_plan_create(ctypes.byref(h), 3, int(p), n_knots, kptrs,
+                                 ctypes.c_void_p(ctrl.ctypes.data), _stream(stream)))
+        self._h = h
+        pp = ctypes.c_int()
+        n = (ctypes.c_int64 * 3)()
+        nqp = (ctypes.c_int64 * 3)()
+        rows, nnz = ctypes.c_int64(), ctypes.c_int64()
+        check(lib.wq_plan_info(h, ctypes.byref(pp), n, nqp, ctypes.byref(rows), ctypes.byref(nnz)))
+        self.p = pp.value
+        self.n = tuple(n)
+        self.n_qp = tuple(nqp)
+        self.n_rows = rows.value
+        self.nnz = nnz.value
+        nqm = ctypes.c_int()
+        check(lib.wq_get_nq_max(h, ctypes.byref(nqm)))
+        self.nq_max = nqm.value
+
+    # -- lifetime
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            load().wq_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def handle(self) -> ctypes.c_void_p:
+        return self._h
+
+    # -- pattern
+    def pattern(self):
+        """(row_ptr int64[N+1], col int32[nnz]) as zero-copy CUDA tensors."""
+        torch = _torch()
+        rp, cl = ctypes.c_void_p(), ctypes.c_void_p()
+        check(load().wq_plan_pattern(self._h, ctypes.byref(rp), ctypes.byref(cl)))
+        row_ptr = torch.as_tensor(_DeviceView(rp.value, (self.n_rows + 1,), "<i8", self), device="cuda")
+        col = torch.as_tensor(_DeviceView(cl.value, (self.nnz,), "<i4", self), device="cuda")
+        return row_ptr, col
+
+    def csr(self, values):
+        """torch.sparse_csr_tensor over the plan's pattern and the given values."""
+        torch = _torch()
+        row_ptr, col = self.pattern()
+        return torch.sparse_csr_tensor(row_ptr, col, values, size=(self.n_rows, self.n_rows))
+
+    # -- geometry
+    def set_geometry(self, ctrl, stream=None) -> None:
+        """New control points (CUDA tensor or host array); recomputes coefficients."""
+        torch = _torch()
+        if isinstance(ctrl, torch.Tensor) and ctrl.is_cuda:
+            ptr, on_dev = _dev_ptr(ctrl, torch.float64, 3 * self.n_rows, "ctrl"), 1
+        else:
+            arr = np.ascontiguousarray(ctrl, dtype=np.float64).reshape(-1)
+            self._host_ctrl = arr
+            ptr, on_dev = arr.ctypes.data, 0
+        check(load().wq_plan_set_geometry(self._h, ctypes.c_void_p(ptr), on_dev, _stream(stream)))
+
+    def refresh(self, ctrl=None, stream=None) -> None:
+        """Re-run every set-up kernel in place (optionally with new control points)."""
+        torch = _torch()
+        ptr, on_dev = None, 1
+        if ctrl is not None:
+            if isinstance(ctrl, torch.Tensor) and ctrl.is_cuda:
+                ptr = _dev_ptr(ctrl, torch.float64, 3 * self.n_rows, "ctrl")
+            else:
+                arr = np.ascontiguousarray(ctrl, dtype=np.float64).reshape(-1)
+                self._host_ctrl = arr
+                ptr, on_dev = arr.ctypes.data, 0
+        check(load().wq_plan_refresh(self._h, ctypes.c_void_p(ptr), on_dev, _stream(stream)))
+
+    # -- assembly
+    def _assemble(self, fn, kappa, out, dtype, precision, stream):
+        torch = _torch()
+        dtype = dtype or torch.float64
+        vdt = VALUES_F64 if dtype == torch.float64 else VALUES_F32 if dtype == torch.float32 else None
+        if vdt is None:
+            raise ValueError("dtype must be torch.float64 or torch.float32")
+        prec = _PREC[precision] if isinstance(precision, str) else int(precision)
+        if out is None:
+            out = torch.empty(self.nnz, dtype=dtype, device="cuda")
+        vp = _dev_ptr(out, dtype, self.nnz, "out")
+        kp = None
+        if kappa is not None:
+            kp = _dev_ptr(kappa, torch.float64, int(np.prod(self.n_qp)), "kappa")
+        check(fn(self._h, ctypes.c_void_p(kp), ctypes.c_void_p(vp), vdt, prec, _stream(stream)))
+        return out
+
+    def stiffness(self, kappa=None, out=None, dtype=None, precision="fp64", stream=None):
+        """CSR values of the WQ stiffness matrix (Eq. (stiff)) in the plan's order."""
+        return self._assemble(load().wq_assemble_stiffness, kappa, out, dtype, precision, stream)
+
+    def mass(self, kappa=None, out=None, dtype=None, precision="fp64", stream=None):
+        """CSR values of the WQ mass matrix (Eq. (Mass_approx))."""
+        return self._assemble(load().wq_assemble_mass, kappa, out, dtype, precision, stream)
+
+    def assemble_host(self, which: str, h_ctrl, d_vals, h_vals, stream=None) -> None:
+        """End-to-end call with host buffers (wq_assemble_host): h_ctrl host float64
+        control points or None, d_vals a CUDA float64 staging tensor of nnz
+        elements, h_vals a host float64 tensor/array of nnz elements."""
+        torch = _torch()
+        vp = _dev_ptr(d_vals, torch.float64, self.nnz, "d_vals")
+        if isinstance(h_vals, torch.Tensor):
+            if h_vals.is_cuda or h_vals.dtype != torch.float64 or h_vals.numel() != self.nnz:
+                raise ValueError("h_vals must be a host float64 tensor of nnz elements")
+            hp = h_vals.data_ptr()
+        else:
+            hp = h_vals.ctypes.data
+        cp = None
+        if h_ctrl is not None:
+            if isinstance(h_ctrl, torch.Tensor):
+                cp = h_ctrl.data_ptr()
+            else:
+                cp = h_ctrl.ctypes.data
+        check(load().wq_assemble_host(self._h, 1 if which == "mass" else 0, ctypes.c_void_p(cp),
+                                      ctypes.c_void_p(vp), ctypes.c_void_p(hp), _stream(stream)))
+
+    def sync_check(self, stream=None) -> None:
+        check(load().wq_sync_check(self._h, _stream(stream)))
+
+    # -- inspection (synchronous copies)
+    def points(self, direction: int) -> np.ndarray:
+        out = np.empty(self.n_qp[direction])
+        check(load().wq_get_points(self._h, direction, ctypes.c_void_p(out.ctypes.data)))
+        return out
+
+    def rules(self, direction: int, a: int, b: int):
+        """(w[n, nq_max], q0[n], nq[n]): rule of kind (a, b) for every test function."""
+        n = self.n[direction]
+        w = np.empty((n, self.nq_max))
+        q0 = np.empty(n, dtype=np.int32)
+        nq = np.empty(n, dtype=np.int32)
+        check(load().wq_get_rules(self._h, direction, a, b, ctypes.c_void_p(w.ctypes.data),
+                                  ctypes.c_void_p(q0.ctypes.data), ctypes.c_void_p(nq.ctypes.data)))
+        return w, q0, nq
+
+    def coefficients(self) -> np.ndarray:
+        """(7, nqp3, nqp2, nqp1): c_11 c_12 c_13 c_22 c_23 c_33 and det DF."""
+        out = np.empty((7, self.n_qp[2], self.n_qp[1], self.n_qp[0]))
+        check(load().wq_get_coefficients(self._h, ctypes.c_void_p(out.ctypes.data)))
+        return out

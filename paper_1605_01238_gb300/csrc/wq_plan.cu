@@ -1,0 +1,880 @@
+// Plan set-up: everything of the WQ method that depends only on the mesh and the
+// geometry, computed on the GPU.
+//
+//   k_gauss          Gauss-Legendre rule with p+1 points (double-double)
+//   k_points         quadrature points (Remark on the choice of quadrature points)
+//   k_qranges        Q_{l,i}: points inside the open support of B_i (Eq. (support))
+//   k_basis_points   B and B' at the points (Algorithm 1, first loop)
+//   k_gauss_basis    B and B' at the Gauss points of every span
+//   k_integrals      exact integrals I^{(a,b)}_{l,i,j} (Eq. (integrals), Algorithm 1)
+//   k_rules          minimum-norm WQ rules of four kinds (Eq. (exact), Algorithm 2)
+//   k_prefix / k_row_ptr / k_cols   Kronecker-structured CSR pattern (Section 3)
+//   k_coef           DF, det DF and c_lm = det DF (DF^{-1} DF^{-T})_lm (Eq. (coef_stiff))
+//
+// The univariate steps run in double-double arithmetic: the rule systems near
+// the boundary are ill-conditioned at high degree (row-scaled condition numbers
+// ~1e7 at p = 8), and float64 data alone would put errors of ~1e-9 into the
+// weights. With double-double points, basis values, integrals and solves, every
+// weight is rounded to float64 once, at the end.
+#include <algorithm>
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <vector>
+
+#include "wq_internal.h"
+
+namespace wq {
+
+// ---------------------------------------------------------------------------
+// Cox-de Boor recursion on one span, in double-double.
+// s is the knot-vector index of the span start (xi_s <= x < xi_{s+1} for points
+// of that span); the p+1 functions B_{s-p+t}, t = 0..p, are returned with their
+// first derivatives, as the span's polynomial pieces evaluated at x.
+__device__ void basis_dd(const double* xi, int p, int s, dd x, dd* val, dd* der) {
+  dd cur[kMaxP + 1], nxt[kMaxP + 1], low[kMaxP + 1];
+  cur[0] = dd_make(1.0);
+  for (int k = 1; k <= p; ++k) {
+    for (int t = 0; t <= k; ++t) {
+      int j = s - k + t;
+      dd v = dd_make(0.0);
+      if (t >= 1) {  // (x - xi_j)/(xi_{j+k} - xi_j) B_{j,k-1}
+        dd num = dd_sub(x, dd_make(xi[j]));
+        dd den = two_sum(xi[j + k], -xi[j]);
+        v = dd_add(v, dd_mul(dd_div(num, den), cur[t - 1]));
+      }
+      if (t <= k - 1) {  // (xi_{j+k+1} - x)/(xi_{j+k+1} - xi_{j+1}) B_{j+1,k-1}
+        dd num = dd_sub(dd_make(xi[j + k + 1]), x);
+        dd den = two_sum(xi[j + k + 1], -xi[j + 1]);
+        v = dd_add(v, dd_mul(dd_div(num, den), cur[t]));
+      }
+      nxt[t] = v;
+    }
+    if (k == p)
+      for (int t = 0; t < p; ++t) low[t] = cur[t];
+    for (int t = 0; t <= k; ++t) cur[t] = nxt[t];
+  }
+  for (int t = 0; t <= p; ++t) {
+    val[t] = cur[t];
+    int j = s - p + t;
+    dd d = dd_make(0.0);
+    if (t >= 1) d = dd_add(d, dd_div(dd_mul_d(low[t - 1], (double)p), two_sum(xi[j + p], -xi[j])));
+    if (t <= p - 1)
+      d = dd_sub(d, dd_div(dd_mul_d(low[t], (double)p), two_sum(xi[j + p + 1], -xi[j + 1])));
+    der[t] = d;
+  }
+}
+
+// Legendre P_m and P_{m-1} at x by the three-term recurrence, double-double.
+__device__ void legendre_dd(int m, dd x, dd* pm, dd* pm1) {
+  dd a = dd_make(1.0), b = x;
+  for (int j = 1; j < m; ++j) {
+    dd c = dd_sub(dd_mul_d(dd_mul(x, b), (double)(2 * j + 1)), dd_mul_d(a, (double)j));
+    c = dd_div(c, dd_make((double)(j + 1)));
+    a = b;
+    b = c;
+  }
+  *pm = b;
+  *pm1 = a;
+}
+
+// m-point Gauss-Legendre nodes g[k] and weights g[m+k] on [-1, 1].
+__global__ void k_gauss(dd* g, int m) {
+  int k = threadIdx.x;
+  if (k >= m) return;
+  double x = cos(M_PI * (k + 0.75) / (m + 0.5));
+  for (int it = 0; it < 8; ++it) {  // Newton in double from the asymptotic guess
+    double a = 1.0, b = x;
+    for (int j = 1; j < m; ++j) {
+      double c = ((2 * j + 1) * x * b - j * a) / (j + 1);
+      a = b;
+      b = c;
+    }
+    double dp = m * (x * b - a) / (x * x - 1.0);
+    x -= b / dp;
+  }
+  dd X = dd_make(x), pm, pm1, dp;
+  for (int it = 0; it < 3; ++it) {  // Newton in double-double
+    legendre_dd(m, X, &pm, &pm1);
+    dd x2m1 = dd_sub(dd_mul(X, X), dd_make(1.0));
+    dp = dd_div(dd_mul_d(dd_sub(dd_mul(X, pm), pm1), (double)m), x2m1);
+    X = dd_sub(X, dd_div(pm, dp));
+  }
+  legendre_dd(m, X, &pm, &pm1);
+  dd x2m1 = dd_sub(dd_mul(X, X), dd_make(1.0));
+  dp = dd_div(dd_mul_d(dd_sub(dd_mul(X, pm), pm1), (double)m), x2m1);
+  // w = 2 / ((1 - x^2) P'_m(x)^2)
+  dd den = dd_mul(dd_neg(x2m1), dd_mul(dp, dp));
+  g[k] = X;
+  g[m + k] = dd_div(dd_make(2.0), den);
+}
+
+struct DirArgs {
+  int p, n, n_el, nqp, nq_stride;
+  const double* knots;
+  double* x;
+  dd* x_dd;
+  int* first;
+  int* q0;
+  int* nq;
+  dd* bt_dd;
+  double* bt;
+  double* bp;
+  dd* gb;
+  dd* integ;
+  double* w;
+  int64_t* prefix;
+  const dd* gauss;
+  int* err;
+};
+
+static DirArgs dir_args(wq_plan_s* pl, int l) {
+  DirData& d = pl->dir[l];
+  DirArgs a;
+  a.p = pl->p;
+  a.n = d.n;
+  a.n_el = d.n_el;
+  a.nqp = d.nqp;
+  a.nq_stride = pl->nq_max;
+  a.knots = d.knots;
+  a.x = d.x;
+  a.x_dd = d.x_dd;
+  a.first = d.first;
+  a.q0 = d.q0;
+  a.nq = d.nq;
+  a.bt_dd = d.bt_dd;
+  a.bt = d.bt;
+  a.bp = d.bp;
+  a.gb = d.gb;
+  a.integ = d.integ;
+  a.w = d.w;
+  a.prefix = d.prefix;
+  a.gauss = pl->gauss;
+  a.err = pl->err;
+  return a;
+}
+
+// Points: p+1 equally spaced points strictly inside each boundary span,
+// x = a + k (b - a)/(p + 2), k = 1..p+1; knots and midpoints elsewhere.
+__global__ void k_points(DirArgs a) {
+  int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= a.nqp) return;
+  const double* chi = a.knots + a.p;  // distinct knots chi_0..chi_{n_el}
+  const int p = a.p, ne = a.n_el;
+  dd x;
+  int first;
+  if (q <= p || q >= 2 * ne + p - 2) {
+    int span = q <= p ? 0 : ne - 1;
+    int k = q <= p ? q + 1 : q - (2 * ne + p - 2) + 1;
+    dd h = two_sum(chi[span + 1], -chi[span]);
+    x = dd_add(dd_make(chi[span]), dd_div(dd_mul_d(h, (double)k), dd_make((double)(p + 2))));
+    first = span;
+  } else {
+    int t = q - p - 1;
+    int k = 1 + t / 2;
+    if ((t & 1) == 0) {
+      x = dd_make(chi[k]);
+    } else {
+      dd s = two_sum(chi[k], chi[k + 1]);
+      x = dd{0.5 * s.hi, 0.5 * s.lo};
+    }
+    first = k;
+  }
+  a.x_dd[q] = x;
+  a.x[q] = dd_to_d(x);
+  a.first[q] = first;
+}
+
+// Q_i = points strictly inside (chi_{max(0,i-p)}, chi_{min(n_el,i+1)}).
+__global__ void k_qranges(DirArgs a) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= a.n) return;
+  int lo = max(0, i - a.p), hi = min(a.n_el, i + 1);
+  int qs = lo == 0 ? 0 : 2 * lo + a.p;
+  int qe = hi == a.n_el ? a.nqp - 1 : 2 * hi + a.p - 2;
+  a.q0[i] = qs;
+  a.nq[i] = qe - qs + 1;
+}
+
+__global__ void k_basis_points(DirArgs a) {
+  int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= a.nqp) return;
+  const int p = a.p;
+  int f = a.first[q];
+  dd val[kMaxP + 1], der[kMaxP + 1];
+  basis_dd(a.knots, p, f + p, a.x_dd[q], val, der);
+  for (int t = 0; t <= p; ++t) {
+    a.bp[(0 * a.nqp + q) * (p + 1) + t] = dd_to_d(val[t]);
+    a.bp[(1 * a.nqp + q) * (p + 1) + t] = dd_to_d(der[t]);
+    int j = f + t;
+    int loc = q - a.q0[j];
+    if (loc >= 0 && loc < a.nq[j]) {
+      size_t i0 = ((size_t)0 * a.n + j) * a.nq_stride + loc;
+      size_t i1 = ((size_t)1 * a.n + j) * a.nq_stride + loc;
+      a.bt_dd[i0] = val[t];
+      a.bt_dd[i1] = der[t];
+      a.bt[i0] = dd_to_d(val[t]);
+      a.bt[i1] = dd_to_d(der[t]);
+    }
+  }
+}
+
+// Basis at the p+1 Gauss points of every span: gb[span][g][b][t].
+__global__ void k_gauss_basis(DirArgs a) {
+  int id = blockIdx.x * blockDim.x + threadIdx.x;
+  const int p = a.p, m = p + 1;
+  if (id >= a.n_el * m) return;
+  int span = id / m, g = id % m;
+  const double* chi = a.knots + p;
+  dd mid = two_sum(chi[span], chi[span + 1]);
+  mid = dd{0.5 * mid.hi, 0.5 * mid.lo};
+  dd half = two_sum(chi[span + 1], -chi[span]);
+  half = dd{0.5 * half.hi, 0.5 * half.lo};
+  dd x = dd_add(mid, dd_mul(half, a.gauss[g]));
+  dd val[kMaxP + 1], der[kMaxP + 1];
+  basis_dd(a.knots, p, span + p, x, val, der);
+  dd* out = a.gb + ((size_t)span * m + g) * 2 * m;
+  for (int t = 0; t <= p; ++t) {
+    out[t] = val[t];
+    out[m + t] = der[t];
+  }
+}
+
+// I^{(a,b)}_{i,j} for j = i - p + t, all four kinds, by Gauss on the common spans.
+__global__ void k_integrals(DirArgs a) {
+  int id = blockIdx.x * blockDim.x + threadIdx.x;
+  const int p = a.p, m = p + 1, bw = 2 * p + 1;
+  if (id >= a.n * bw) return;
+  int i = id / bw, t = id % bw;
+  int j = i - p + t;
+  dd acc[4] = {dd_make(0.0), dd_make(0.0), dd_make(0.0), dd_make(0.0)};
+  if (j >= 0 && j < a.n) {
+    const double* chi = a.knots + p;
+    int k0 = max(max(i, j) - p, 0), k1 = min(min(i, j), a.n_el - 1);
+    for (int k = k0; k <= k1; ++k) {
+      dd half = two_sum(chi[k + 1], -chi[k]);
+      half = dd{0.5 * half.hi, 0.5 * half.lo};
+      const dd* gbk = a.gb + (size_t)k * m * 2 * m;
+      for (int g = 0; g < m; ++g) {
+        dd wg = dd_mul(a.gauss[m + g], half);
+        const dd* row = gbk + (size_t)g * 2 * m;
+        dd bi[2] = {row[i - k], row[m + i - k]};
+        dd bj[2] = {row[j - k], row[m + j - k]};
+        for (int ta = 0; ta < 2; ++ta) {
+          dd wi = dd_mul(wg, bi[ta]);
+          for (int tb = 0; tb < 2; ++tb) acc[2 * ta + tb] = dd_add(acc[2 * ta + tb], dd_mul(wi, bj[tb]));
+        }
+      }
+    }
+  }
+  for (int kind = 0; kind < 4; ++kind) a.integ[((size_t)kind * a.n + i) * bw + t] = acc[kind];
+}
+
+// Minimum-norm rule of kind (a,b) for test function i: one warp per system.
+// Rows (j in I_i) are scaled by powers of two (exact, solution set unchanged);
+// the normal equations (M M^T) y = r are solved by LDL^T and w = M^T y. For
+// b = 1 the rows of M sum to zero and r is consistent; the rank-one term
+// sigma u u^T with u = D^{-1} 1 (the left null vector of the scaled matrix)
+// makes the system definite without changing w.
+__global__ void k_rules(DirArgs a) {
+  const int i = blockIdx.x, kind = blockIdx.y;
+  const int ka = kind >> 1, kb = kind & 1;
+  const int lane = threadIdx.x;
+  const int p = a.p, bw = 2 * p + 1;
+  __shared__ dd M[kMaxI][kMaxQ];
+  __shared__ dd G[kMaxI][kMaxI];
+  __shared__ dd r[kMaxI], y[kMaxI], Dg[kMaxI];
+  __shared__ double scale[kMaxI];
+  __shared__ int bad;
+  const int jlo = max(0, i - p), jhi = min(a.n - 1, i + p);
+  const int m = jhi - jlo + 1;
+  const int q0i = a.q0[i], nqi = a.nq[i];
+  if (lane == 0) bad = 0;
+  for (int e = lane; e < m * nqi; e += 32) {
+    int rr = e / nqi, c = e % nqi;
+    int j = jlo + rr, q = q0i + c;
+    int loc = q - a.q0[j];
+    dd v = dd_make(0.0);
+    if (loc >= 0 && loc < a.nq[j]) v = a.bt_dd[((size_t)kb * a.n + j) * a.nq_stride + loc];
+    M[rr][c] = v;
+  }
+  for (int rr = lane; rr < m; rr += 32) r[rr] = a.integ[((size_t)kind * a.n + i) * bw + (jlo + rr - i + p)];
+  __syncwarp();
+  for (int rr = lane; rr < m; rr += 32) {
+    double mx = 0.0;
+    for (int c = 0; c < nqi; ++c) mx = fmax(mx, fabs(M[rr][c].hi));
+    double s = mx > 0.0 ? ldexp(1.0, -ilogb(mx)) : 0.0;
+    if (!(mx > 0.0)) atomicOr(a.err, kErrSingularRule);
+    scale[rr] = s;
+    for (int c = 0; c < nqi; ++c) M[rr][c] = dd{M[rr][c].hi * s, M[rr][c].lo * s};
+    r[rr] = dd{r[rr].hi * s, r[rr].lo * s};
+  }
+  __syncwarp();
+  for (int e = lane; e < m * m; e += 32) {
+    int rr = e / m, ss = e % m;
+    if (ss > rr) continue;
+    dd acc = dd_make(0.0);
+    for (int c = 0; c < nqi; ++c) acc = dd_add(acc, dd_mul(M[rr][c], M[ss][c]));
+    G[rr][ss] = acc;
+    G[ss][rr] = acc;
+  }
+  __syncwarp();
+  if (kb == 1 && lane == 0) {
+    dd tr = dd_make(0.0), un = dd_make(0.0);
+    for (int rr = 0; rr < m; ++rr) {
+      tr = dd_add(tr, G[rr][rr]);
+      double u = 1.0 / scale[rr];  // exact: scale is a power of two
+      un = dd_add(un, dd_mul_d(dd_make(u), u));
+    }
+    dd sig = dd_div(tr, dd_mul_d(un, (double)m));
+    for (int rr = 0; rr < m; ++rr)
+      for (int ss = 0; ss < m; ++ss)
+        G[rr][ss] = dd_add(G[rr][ss], dd_mul_d(dd_mul_d(sig, 1.0 / scale[rr]), 1.0 / scale[ss]));
+  }
+  __syncwarp();
+  // LDL^T, column by column; L stored in the strict lower triangle of G.
+  double gmax = 0.0;
+  for (int rr = 0; rr < m; ++rr) gmax = fmax(gmax, G[rr][rr].hi);
+  for (int c = 0; c < m; ++c) {
+    if (lane == 0) {
+      dd d = G[c][c];
+      for (int k = 0; k < c; ++k) d = dd_sub(d, dd_mul(dd_mul(G[c][k], G[c][k]), Dg[k]));
+      Dg[c] = d;
+      if (!(d.hi > 1e-28 * gmax)) bad = 1;
+    }
+    __syncwarp();
+    for (int rr = c + 1 + lane; rr < m; rr += 32) {
+      dd v = G[rr][c];
+      for (int k = 0; k < c; ++k) v = dd_sub(v, dd_mul(dd_mul(G[rr][k], G[c][k]), Dg[k]));
+      G[rr][c] = dd_div(v, Dg[c]);
+    }
+    __syncwarp();
+  }
+  if (lane == 0) {
+    if (bad) atomicOr(a.err, kErrSingularRule);
+    for (int rr = 0; rr < m; ++rr) {  // L z = r
+      dd v = r[rr];
+      for (int k = 0; k < rr; ++k) v = dd_sub(v, dd_mul(G[rr][k], y[k]));
+      y[rr] = v;
+    }
+    for (int rr = 0; rr < m; ++rr) y[rr] = dd_div(y[rr], Dg[rr]);
+    for (int rr = m - 1; rr >= 0; --rr) {  // L^T y = z / D
+      dd v = y[rr];
+      for (int k = rr + 1; k < m; ++k) v = dd_sub(v, dd_mul(G[k][rr], y[k]));
+      y[rr] = v;
+    }
+  }
+  __syncwarp();
+  double* wout = a.w + ((size_t)kind * a.n + i) * a.nq_stride;
+  for (int c = lane; c < a.nq_stride; c += 32) {
+    if (c < nqi) {
+      dd acc = dd_make(0.0);
+      for (int rr = 0; rr < m; ++rr) acc = dd_add(acc, dd_mul(M[rr][c], y[rr]));
+      wout[c] = dd_to_d(acc);
+    } else {
+      wout[c] = 0.0;
+    }
+  }
+  (void)ka;
+}
+
+// Prefix sums of the band widths |I_i| = min(n-1, i+p) - max(0, i-p) + 1.
+__global__ void k_prefix(DirArgs a) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  int64_t s = 0;
+  for (int i = 0; i < a.n; ++i) {
+    a.prefix[i] = s;
+    s += min(a.n - 1, i + a.p) - max(0, i - a.p) + 1;
+  }
+  a.prefix[a.n] = s;
+}
+
+struct PatternArgs {
+  int p;
+  int n1, n2, n3;
+  const int64_t *P1, *P2, *P3;
+  int64_t* row_ptr;
+  int32_t* col;
+};
+
+__device__ inline int band_lo(int i, int p) { return max(0, i - p); }
+__device__ inline int band_w(int i, int p, int n) { return min(n - 1, i + p) - max(0, i - p) + 1; }
+
+// row_ptr(i1,i2,i3) = P3(i3) N2 N1 + bw3(i3) (P2(i2) N1 + bw2(i2) P1(i1)).
+__global__ void k_row_ptr(PatternArgs a) {
+  int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  int64_t N = (int64_t)a.n1 * a.n2 * a.n3;
+  if (r > N) return;
+  int64_t N1 = a.P1[a.n1], N2 = a.P2[a.n2];
+  if (r == N) {
+    a.row_ptr[N] = a.P3[a.n3] * N2 * N1;
+    return;
+  }
+  int i1 = (int)(r % a.n1);
+  int i2 = (int)((r / a.n1) % a.n2);
+  int i3 = (int)(r / ((int64_t)a.n1 * a.n2));
+  a.row_ptr[r] = a.P3[i3] * N2 * N1 +
+                 (int64_t)band_w(i3, a.p, a.n3) * (a.P2[i2] * N1 + (int64_t)band_w(i2, a.p, a.n2) * a.P1[i1]);
+}
+
+// Column indices: one warp per row, ascending j1 + n1 (j2 + n2 j3).
+__global__ void k_cols(PatternArgs a) {
+  const int64_t N = (int64_t)a.n1 * a.n2 * a.n3;
+  const int lane = threadIdx.x & 31;
+  int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t r = warp; r < N; r += nwarps) {
+    int i1 = (int)(r % a.n1);
+    int i2 = (int)((r / a.n1) % a.n2);
+    int i3 = (int)(r / ((int64_t)a.n1 * a.n2));
+    int w1 = band_w(i1, a.p, a.n1), w2 = band_w(i2, a.p, a.n2), w3 = band_w(i3, a.p, a.n3);
+    int l1 = band_lo(i1, a.p), l2 = band_lo(i2, a.p), l3 = band_lo(i3, a.p);
+    int64_t base = a.row_ptr[r];
+    int cnt = w1 * w2 * w3;
+    for (int e = lane; e < cnt; e += 32) {
+      int t1 = e % w1, rest = e / w1;
+      int t2 = rest % w2, t3 = rest / w2;
+      a.col[base + e] = (int32_t)((l1 + t1) + (int64_t)a.n1 * ((l2 + t2) + (int64_t)a.n2 * (l3 + t3)));
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Coefficients. One block per (q3, tile of TQ2 q2-points, tile of TQ1 q1-points).
+// DF is sum-factorised over the tile: contract i3, then i2, then i1.
+constexpr int kCoefTQ1 = 32, kCoefTQ2 = 8;
+
+struct CoefArgs {
+  int p;
+  int n1, n2, n3, nq1, nq2, nq3;
+  const double* ctrl;
+  const double *bp1, *bp2, *bp3;
+  const int *f1, *f2, *f3;
+  double* coef;
+  int64_t nqp_total;
+  int* err;
+};
+
+__global__ void k_coef(CoefArgs a) {
+  extern __shared__ double sm[];
+  const int p = a.p, m = p + 1;
+  const int nt1 = (a.nq1 + kCoefTQ1 - 1) / kCoefTQ1;
+  int bid = blockIdx.x;
+  const int tq1 = bid % nt1;
+  bid /= nt1;
+  const int nt2 = (a.nq2 + kCoefTQ2 - 1) / kCoefTQ2;
+  const int tq2 = bid % nt2;
+  const int q3 = bid / nt2;
+  const int qa1 = tq1 * kCoefTQ1, qb1 = min(a.nq1, qa1 + kCoefTQ1);
+  const int qa2 = tq2 * kCoefTQ2, qb2 = min(a.nq2, qa2 + kCoefTQ2);
+  const int ia1 = a.f1[qa1], ib1 = a.f1[qb1 - 1] + p + 1;  // i1 window [ia1, ib1)
+  const int ia2 = a.f2[qa2], ib2 = a.f2[qb2 - 1] + p + 1;
+  const int W1 = ib1 - ia1, W2 = ib2 - ia2;
+  const int f3 = a.f3[q3];
+  double* X = sm;                       // [2][W2][W1][3]
+  double* Y = X + 2 * W2 * W1 * 3;      // [3][TQ2][W1][3]
+  const int nthr = blockDim.x;
+  // A: X[d3][i2][i1][r] = sum_t3 B3^{(d3)}(q3, t3) C[i1, i2, f3 + t3][r]
+  for (int e = threadIdx.x; e < 2 * W2 * W1 * 3; e += nthr) {
+    int rr = e % 3, i1 = (e / 3) % W1, i2 = (e / (3 * W1)) % W2, d3 = e / (3 * W1 * W2);
+    double acc = 0.0;
+    for (int t = 0; t < m; ++t) {
+      int64_t idx = ((int64_t)(f3 + t) * a.n2 + (ia2 + i2)) * a.n1 + (ia1 + i1);
+      acc = fma(a.bp3[((int64_t)d3 * a.nq3 + q3) * m + t], a.ctrl[idx * 3 + rr], acc);
+    }
+    X[e] = acc;
+  }
+  __syncthreads();
+  // B: Y[e][q2][i1][r], e = (d2,d3) in {(0,0), (1,0), (0,1)}
+  const int nq2t = qb2 - qa2;
+  for (int e = threadIdx.x; e < 3 * nq2t * W1 * 3; e += nthr) {
+    int rr = e % 3, i1 = (e / 3) % W1, q2l = (e / (3 * W1)) % nq2t, kind = e / (3 * W1 * nq2t);
+    int d2 = kind == 1, d3 = kind == 2;
+    int q2 = qa2 + q2l, f2 = a.f2[q2];
+    double acc = 0.0;
+    for (int t = 0; t < m; ++t)
+      acc = fma(a.bp2[((int64_t)d2 * a.nq2 + q2) * m + t], X[((d3 * W2 + (f2 + t - ia2)) * W1 + i1) * 3 + rr], acc);
+    Y[((kind * kCoefTQ2 + q2l) * W1 + i1) * 3 + rr] = acc;
+  }
+  __syncthreads();
+  const int nq1t = qb1 - qa1;
+  for (int e = threadIdx.x; e < nq2t * nq1t; e += nthr) {
+    int q1l = e % nq1t, q2l = e / nq1t;
+    int q1 = qa1 + q1l, q2 = qa2 + q2l;
+    int f1 = a.f1[q1];
+    double F[3][3];
+    for (int c = 0; c < 3; ++c) {
+      int d1 = c == 0;
+      const double* Yk = Y + ((c * kCoefTQ2 + q2l) * W1) * 3;
+      for (int rr = 0; rr < 3; ++rr) {
+        double acc = 0.0;
+        for (int t = 0; t < m; ++t)
+          acc = fma(a.bp1[((int64_t)d1 * a.nq1 + q1) * m + t], Yk[(f1 + t - ia1) * 3 + rr], acc);
+        F[rr][c] = acc;  // dF_r / dzeta_c
+      }
+    }
+    // adj = det * DF^{-1}: adj[l][k] = cofactor[k][l]
+    double adj[3][3];
+    adj[0][0] = F[1][1] * F[2][2] - F[1][2] * F[2][1];
+    adj[0][1] = F[0][2] * F[2][1] - F[0][1] * F[2][2];
+    adj[0][2] = F[0][1] * F[1][2] - F[0][2] * F[1][1];
+    adj[1][0] = F[1][2] * F[2][0] - F[1][0] * F[2][2];
+    adj[1][1] = F[0][0] * F[2][2] - F[0][2] * F[2][0];
+    adj[1][2] = F[0][2] * F[1][0] - F[0][0] * F[1][2];
+    adj[2][0] = F[1][0] * F[2][1] - F[1][1] * F[2][0];
+    adj[2][1] = F[0][1] * F[2][0] - F[0][0] * F[2][1];
+    adj[2][2] = F[0][0] * F[1][1] - F[0][1] * F[1][0];
+    double det = F[0][0] * adj[0][0] + F[0][1] * adj[1][0] + F[0][2] * adj[2][0];
+    if (!(det > 0.0) || !isfinite(det)) atomicOr(a.err, kErrBadGeometry);
+    double inv = 1.0 / det;
+    const int64_t qg = ((int64_t)q3 * a.nq2 + q2) * a.nq1 + q1;
+    const int L[6] = {0, 0, 0, 1, 1, 2}, Mi[6] = {0, 1, 2, 1, 2, 2};
+    for (int s = 0; s < 6; ++s) {
+      int l = L[s], mm = Mi[s];
+      double v = adj[l][0] * adj[mm][0] + adj[l][1] * adj[mm][1] + adj[l][2] * adj[mm][2];
+      a.coef[(int64_t)s * a.nqp_total + qg] = v * inv;
+    }
+    a.coef[6 * a.nqp_total + qg] = det;
+  }
+}
+
+static size_t coef_smem(int p) {
+  int W1 = kCoefTQ1 / 2 + p + 2, W2 = kCoefTQ2 / 2 + p + 2;
+  return sizeof(double) * (size_t)(2 * W2 * W1 * 3 + 3 * kCoefTQ2 * W1 * 3);
+}
+
+wq_status run_coefficients(wq_plan_s* pl, cudaStream_t s) {
+  CoefArgs a;
+  a.p = pl->p;
+  a.n1 = (int)pl->n[0];
+  a.n2 = (int)pl->n[1];
+  a.n3 = (int)pl->n[2];
+  a.nq1 = (int)pl->nqp[0];
+  a.nq2 = (int)pl->nqp[1];
+  a.nq3 = (int)pl->nqp[2];
+  a.ctrl = pl->ctrl;
+  a.bp1 = pl->dir[0].bp;
+  a.bp2 = pl->dir[1].bp;
+  a.bp3 = pl->dir[2].bp;
+  a.f1 = pl->dir[0].first;
+  a.f2 = pl->dir[1].first;
+  a.f3 = pl->dir[2].first;
+  a.coef = pl->coef;
+  a.nqp_total = pl->n_qp_total;
+  a.err = pl->err;
+  int64_t blocks = (int64_t)((a.nq1 + kCoefTQ1 - 1) / kCoefTQ1) * ((a.nq2 + kCoefTQ2 - 1) / kCoefTQ2) * a.nq3;
+  size_t smem = coef_smem(pl->p);
+  WQ_CUDA_TRY(cudaFuncSetAttribute(k_coef, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
+              "coefficient kernel attributes");
+  k_coef<<<(unsigned)blocks, 256, smem, s>>>(a);
+  count_launch();
+  WQ_CUDA_TRY(cudaGetLastError(), "coefficient kernel launch");
+  return WQ_OK;
+}
+
+wq_status run_setup(wq_plan_s* pl, cudaStream_t s, bool with_pattern) {
+  const int p = pl->p;
+  k_gauss<<<1, 32, 0, s>>>(pl->gauss, p + 1);
+  count_launch();
+  for (int l = 0; l < 3; ++l) {
+    DirArgs a = dir_args(pl, l);
+    DirData& d = pl->dir[l];
+    const int tb = 128;
+    k_points<<<(d.nqp + tb - 1) / tb, tb, 0, s>>>(a);
+    k_qranges<<<(d.n + tb - 1) / tb, tb, 0, s>>>(a);
+    size_t tab = (size_t)2 * d.n * pl->nq_max;
+    WQ_CUDA_TRY(cudaMemsetAsync(d.bt, 0, tab * sizeof(double), s), "table reset");
+    WQ_CUDA_TRY(cudaMemsetAsync(d.bt_dd, 0, tab * sizeof(dd), s), "table reset");
+    k_basis_points<<<(d.nqp + tb - 1) / tb, tb, 0, s>>>(a);
+    k_gauss_basis<<<(d.n_el * (p + 1) + tb - 1) / tb, tb, 0, s>>>(a);
+    k_integrals<<<(d.n * (2 * p + 1) + tb - 1) / tb, tb, 0, s>>>(a);
+    k_rules<<<dim3(d.n, 4), 32, 0, s>>>(a);
+    k_prefix<<<1, 32, 0, s>>>(a);
+    count_launch(7);
+  }
+  WQ_CUDA_TRY(cudaGetLastError(), "set-up kernels");
+  if (with_pattern) {
+    PatternArgs pa;
+    pa.p = p;
+    pa.n1 = (int)pl->n[0];
+    pa.n2 = (int)pl->n[1];
+    pa.n3 = (int)pl->n[2];
+    pa.P1 = pl->dir[0].prefix;
+    pa.P2 = pl->dir[1].prefix;
+    pa.P3 = pl->dir[2].prefix;
+    pa.row_ptr = pl->row_ptr;
+    pa.col = pl->col;
+    int64_t N = pl->n_rows;
+    k_row_ptr<<<(unsigned)((N + 1 + 255) / 256), 256, 0, s>>>(pa);
+    int dev_sms = 152;
+    cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, pl->device);
+    int64_t warps_needed = N;
+    int64_t blocks = (warps_needed + 7) / 8;
+    int64_t cap = (int64_t)dev_sms * 16;
+    if (blocks > cap) blocks = cap;
+    k_cols<<<(unsigned)blocks, 256, 0, s>>>(pa);
+    count_launch(2);
+    WQ_CUDA_TRY(cudaGetLastError(), "pattern kernels");
+  }
+  return run_coefficients(pl, s);
+}
+
+}  // namespace wq
+
+// ---------------------------------------------------------------------------
+// Host side of the plan.
+
+using wq::set_error;
+
+static bool knots_ok(const double* xi, int64_t len, int p, std::string* why) {
+  if (len < 2 * (p + 1) + 1) {
+    *why = "a knot vector needs at least two spans (length >= 2p+3)";
+    return false;
+  }
+  for (int64_t k = 0; k < len; ++k)
+    if (!std::isfinite(xi[k])) {
+      *why = "knots must be finite";
+      return false;
+    }
+  for (int k = 1; k <= p; ++k)
+    if (xi[k] != xi[0] || xi[len - 1 - k] != xi[len - 1]) {
+      *why = "end knots must repeat p+1 times (open knot vector)";
+      return false;
+    }
+  for (int64_t k = p; k < len - p - 1; ++k)
+    if (!(xi[k + 1] > xi[k])) {
+      *why = "interior knots must be simple and strictly increasing";
+      return false;
+    }
+  return true;
+}
+
+static void free_plan(wq_plan_s* pl) {
+  if (!pl) return;
+  for (int l = 0; l < 3; ++l) {
+    wq::DirData& d = pl->dir[l];
+    void* ptrs[] = {d.knots, d.x, d.x_dd, d.first, d.q0, d.nq, d.bt_dd, d.bt, d.bp, d.gb, d.integ, d.w, d.prefix};
+    for (void* q : ptrs)
+      if (q) cudaFree(q);
+  }
+  void* ptrs[] = {pl->ctrl, pl->coef, pl->row_ptr, pl->col, pl->gauss, pl->err};
+  for (void* q : ptrs)
+    if (q) cudaFree(q);
+  delete pl;
+}
+
+static wq_status dev_alloc(void** ptr, size_t bytes, const char* what) {
+  if (std::getenv("WQ_FAULT") && std::strcmp(std::getenv("WQ_FAULT"), "alloc") == 0)
+    return set_error(WQ_ERR_INJECTED, std::string("injected allocation failure: ") + what);
+  cudaError_t e = cudaMalloc(ptr, bytes ? bytes : 16);
+  if (e == cudaErrorMemoryAllocation) {
+    cudaGetLastError();
+    return set_error(WQ_ERR_OOM, std::string("device allocation failed: ") + what);
+  }
+  if (e != cudaSuccess) return wq::cuda_error(e, what);
+  return WQ_OK;
+}
+
+static wq_status read_error_word(wq_plan_s* pl, cudaStream_t s) {
+  int h = 0;
+  WQ_CUDA_TRY(cudaMemcpyAsync(&h, pl->err, sizeof(int), cudaMemcpyDeviceToHost, s), "error word read");
+  WQ_CUDA_TRY(cudaStreamSynchronize(s), "stream synchronize");
+  if (h) WQ_CUDA_TRY(cudaMemsetAsync(pl->err, 0, sizeof(int), s), "error word reset");
+  if (h & wq::kErrBadGeometry) return set_error(WQ_ERR_BAD_GEOMETRY, "det DF <= 0 or not finite at a quadrature point");
+  if (h & wq::kErrSingularRule) return set_error(WQ_ERR_SINGULAR_RULE, "a WQ rule system broke down");
+  if (h & wq::kErrTimeout) return set_error(WQ_ERR_TIMEOUT, "a bounded device wait gave up");
+  return WQ_OK;
+}
+
+extern "C" wq_status wq_plan_create(wq_plan_t* out, int d, int p, const int64_t n_knots[3],
+                                    const double* const h_knots[3], const double* h_ctrl, void* stream) {
+  if (!out || !n_knots || !h_knots || !h_ctrl) return set_error(WQ_ERR_INVALID_ARG, "NULL argument");
+  *out = nullptr;
+  if (d != 3) return set_error(WQ_ERR_UNSUPPORTED, "only d = 3 is supported");
+  if (p < 2 || p > wq::kMaxP) return set_error(WQ_ERR_INVALID_ARG, "degree must be in 2..8");
+  int64_t n[3];
+  for (int l = 0; l < 3; ++l) {
+    std::string why;
+    if (!h_knots[l]) return set_error(WQ_ERR_INVALID_ARG, "NULL knot vector");
+    if (!knots_ok(h_knots[l], n_knots[l], p, &why)) return set_error(WQ_ERR_INVALID_ARG, why);
+    n[l] = n_knots[l] - p - 1;
+  }
+  const int64_t N = n[0] * n[1] * n[2];
+  if (N > INT32_MAX) return set_error(WQ_ERR_UNSUPPORTED, "N_DOF must fit in int32 column indices");
+  for (int64_t k = 0; k < 3 * N; ++k)
+    if (!std::isfinite(h_ctrl[k])) return set_error(WQ_ERR_INVALID_ARG, "control points must be finite");
+  int dev = 0;
+  cudaError_t ce = cudaGetDevice(&dev);
+  if (ce != cudaSuccess) return wq::cuda_error(ce, "no CUDA device");
+  cudaStream_t s = (cudaStream_t)stream;
+
+  wq_plan_s* pl = new wq_plan_s();
+  pl->p = p;
+  pl->device = dev;
+  pl->n_rows = N;
+  int64_t nnz = 1;
+  int nqmax = 0;
+  for (int l = 0; l < 3; ++l) {
+    wq::DirData& dd = pl->dir[l];
+    dd.n = (int)n[l];
+    dd.n_el = (int)(n[l] - p);
+    dd.nqp = 2 * dd.n_el + 2 * p - 1;
+    pl->n[l] = n[l];
+    pl->nqp[l] = dd.nqp;
+    pl->nnz1[l] = 0;  // sum of the band widths |I_i| (= (2p+1) n - p(p+1) when n >= 2p+1)
+    for (int i = 0; i < dd.n; ++i) pl->nnz1[l] += std::min(dd.n - 1, i + p) - std::max(0, i - p) + 1;
+    nnz *= pl->nnz1[l];
+    for (int i = 0; i < dd.n; ++i) {  // |Q_i| from the same closed form as k_qranges
+      int lo = std::max(0, i - p), hi = std::min(dd.n_el, i + 1);
+      int qs = lo == 0 ? 0 : 2 * lo + p;
+      int qe = hi == dd.n_el ? dd.nqp - 1 : 2 * hi + p - 2;
+      nqmax = std::max(nqmax, qe - qs + 1);
+    }
+  }
+  pl->nnz = nnz;
+  pl->nq_max = nqmax;
+  pl->n_qp_total = pl->nqp[0] * pl->nqp[1] * pl->nqp[2];
+
+  wq_status st = WQ_OK;
+#define ALLOC(ptr, bytes, what)                                  \
+  do {                                                           \
+    st = dev_alloc((void**)&(ptr), (size_t)(bytes), what);       \
+    if (st != WQ_OK) {                                           \
+      free_plan(pl);                                             \
+      return st;                                                 \
+    }                                                            \
+  } while (0)
+  for (int l = 0; l < 3; ++l) {
+    wq::DirData& dd = pl->dir[l];
+    const int m = p + 1;
+    ALLOC(dd.knots, sizeof(double) * n_knots[l], "knots");
+    ALLOC(dd.x, sizeof(double) * dd.nqp, "points");
+    ALLOC(dd.x_dd, sizeof(wq::dd) * dd.nqp, "points");
+    ALLOC(dd.first, sizeof(int) * dd.nqp, "spans");
+    ALLOC(dd.q0, sizeof(int) * dd.n, "Q ranges");
+    ALLOC(dd.nq, sizeof(int) * dd.n, "Q ranges");
+    ALLOC(dd.bt_dd, sizeof(wq::dd) * 2 * dd.n * nqmax, "basis tables");
+    ALLOC(dd.bt, sizeof(double) * 2 * dd.n * nqmax, "basis tables");
+    ALLOC(dd.bp, sizeof(double) * 2 * dd.nqp * m, "basis tables");
+    ALLOC(dd.gb, sizeof(wq::dd) * dd.n_el * m * 2 * m, "Gauss basis");
+    ALLOC(dd.integ, sizeof(wq::dd) * 4 * dd.n * (2 * p + 1), "integrals");
+    ALLOC(dd.w, sizeof(double) * 4 * dd.n * nqmax, "rules");
+    ALLOC(dd.prefix, sizeof(int64_t) * (dd.n + 1), "band prefix");
+  }
+  ALLOC(pl->ctrl, sizeof(double) * 3 * N, "control points");
+  ALLOC(pl->coef, sizeof(double) * 7 * pl->n_qp_total, "coefficients");
+  ALLOC(pl->row_ptr, sizeof(int64_t) * (N + 1), "row_ptr");
+  ALLOC(pl->col, sizeof(int32_t) * nnz, "col");
+  ALLOC(pl->gauss, sizeof(wq::dd) * 2 * (p + 1), "Gauss rule");
+  ALLOC(pl->err, sizeof(int), "error word");
+#undef ALLOC
+  auto fail = [&](wq_status code) {
+    free_plan(pl);
+    return code;
+  };
+  for (int l = 0; l < 3; ++l) {
+    cudaError_t e = cudaMemcpyAsync(pl->dir[l].knots, h_knots[l], sizeof(double) * n_knots[l],
+                                    cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return fail(wq::cuda_error(e, "knot copy"));
+  }
+  cudaError_t e = cudaMemcpyAsync(pl->ctrl, h_ctrl, sizeof(double) * 3 * N, cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return fail(wq::cuda_error(e, "control point copy"));
+  e = cudaMemsetAsync(pl->err, 0, sizeof(int), s);
+  if (e != cudaSuccess) return fail(wq::cuda_error(e, "error word reset"));
+  st = wq::run_setup(pl, s, true);
+  if (st != WQ_OK) return fail(st);
+  st = read_error_word(pl, s);
+  if (st != WQ_OK) return fail(st);
+  *out = pl;
+  return WQ_OK;
+}
+
+extern "C" wq_status wq_plan_destroy(wq_plan_t plan) {
+  free_plan(plan);
+  return WQ_OK;
+}
+
+extern "C" wq_status wq_plan_info(wq_plan_t plan, int* p, int64_t n[3], int64_t n_qp[3], int64_t* n_rows,
+                                  int64_t* nnz) {
+  if (!plan) return set_error(WQ_ERR_INVALID_ARG, "NULL plan");
+  if (p) *p = plan->p;
+  for (int l = 0; l < 3; ++l) {
+    if (n) n[l] = plan->n[l];
+    if (n_qp) n_qp[l] = plan->nqp[l];
+  }
+  if (n_rows) *n_rows = plan->n_rows;
+  if (nnz) *nnz = plan->nnz;
+  return WQ_OK;
+}
+
+extern "C" wq_status wq_plan_pattern(wq_plan_t plan, const int64_t** d_row_ptr, const int32_t** d_col) {
+  if (!plan) return set_error(WQ_ERR_INVALID_ARG, "NULL plan");
+  if (d_row_ptr) *d_row_ptr = plan->row_ptr;
+  if (d_col) *d_col = plan->col;
+  return WQ_OK;
+}
+
+static wq_status copy_ctrl(wq_plan_t plan, const double* ctrl, int on_device, cudaStream_t s) {
+  if (!ctrl) return WQ_OK;
+  cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  WQ_CUDA_TRY(cudaMemcpyAsync(plan->ctrl, ctrl, sizeof(double) * 3 * plan->n_rows, kind, s), "control point copy");
+  return WQ_OK;
+}
+
+extern "C" wq_status wq_plan_set_geometry(wq_plan_t plan, const double* ctrl, int ctrl_on_device, void* stream) {
+  if (!plan || !ctrl) return set_error(WQ_ERR_INVALID_ARG, "NULL argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  wq_status st = copy_ctrl(plan, ctrl, ctrl_on_device, s);
+  if (st != WQ_OK) return st;
+  return wq::run_coefficients(plan, s);
+}
+
+extern "C" wq_status wq_plan_refresh(wq_plan_t plan, const double* ctrl, int ctrl_on_device, void* stream) {
+  if (!plan) return set_error(WQ_ERR_INVALID_ARG, "NULL plan");
+  cudaStream_t s = (cudaStream_t)stream;
+  wq_status st = copy_ctrl(plan, ctrl, ctrl_on_device, s);
+  if (st != WQ_OK) return st;
+  return wq::run_setup(plan, s, true);
+}
+
+extern "C" wq_status wq_sync_check(wq_plan_t plan, void* stream) {
+  if (!plan) return set_error(WQ_ERR_INVALID_ARG, "NULL plan");
+  return read_error_word(plan, (cudaStream_t)stream);
+}
+
+extern "C" wq_status wq_get_nq_max(wq_plan_t plan, int* nq_max) {
+  if (!plan || !nq_max) return set_error(WQ_ERR_INVALID_ARG, "NULL argument");
+  *nq_max = plan->nq_max;
+  return WQ_OK;
+}
+
+extern "C" wq_status wq_get_points(wq_plan_t plan, int dir, double* h_x) {
+  if (!plan || !h_x || dir < 0 || dir > 2) return set_error(WQ_ERR_INVALID_ARG, "bad argument");
+  WQ_CUDA_TRY(cudaDeviceSynchronize(), "synchronize");
+  WQ_CUDA_TRY(cudaMemcpy(h_x, plan->dir[dir].x, sizeof(double) * plan->nqp[dir], cudaMemcpyDeviceToHost),
+              "points copy");
+  return WQ_OK;
+}
+
+extern "C" wq_status wq_get_rules(wq_plan_t plan, int dir, int a, int b, double* h_w, int32_t* h_q0,
+                                  int32_t* h_nq) {
+  if (!plan || dir < 0 || dir > 2 || a < 0 || a > 1 || b < 0 || b > 1)
+    return set_error(WQ_ERR_INVALID_ARG, "bad argument");
+  const wq::DirData& d = plan->dir[dir];
+  WQ_CUDA_TRY(cudaDeviceSynchronize(), "synchronize");
+  if (h_w)
+    WQ_CUDA_TRY(cudaMemcpy(h_w, d.w + (size_t)(2 * a + b) * d.n * plan->nq_max,
+                           sizeof(double) * d.n * plan->nq_max, cudaMemcpyDeviceToHost),
+                "rules copy");
+  if (h_q0) WQ_CUDA_TRY(cudaMemcpy(h_q0, d.q0, sizeof(int) * d.n, cudaMemcpyDeviceToHost), "rules copy");
+  if (h_nq) WQ_CUDA_TRY(cudaMemcpy(h_nq, d.nq, sizeof(int) * d.n, cudaMemcpyDeviceToHost), "rules copy");
+  return WQ_OK;
+}
+
+extern "C" wq_status wq_get_coefficients(wq_plan_t plan, double* h_coef) {
+  if (!plan || !h_coef) return set_error(WQ_ERR_INVALID_ARG, "NULL argument");
+  WQ_CUDA_TRY(cudaDeviceSynchronize(), "synchronize");
+  WQ_CUDA_TRY(cudaMemcpy(h_coef, plan->coef, sizeof(double) * 7 * plan->n_qp_total, cudaMemcpyDeviceToHost),
+              "coefficient copy");
+  return WQ_OK;
+}

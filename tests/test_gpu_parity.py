@@ -1,0 +1,233 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+FP64 bar: every value within 1e-12 of its row's largest |entry| (relative), CSR
+pattern bit-exact. Small meshes are checked on every row; the full-size
+workloads on seeded sampled rows that include all 27 boundary/interior classes.
+"""
+import os
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle import Oracle3D, rows_c  # noqa: E402
+from wq_synth import (affine_cube, graded_breaks, perturbed_cube, random_field, sample_rows,  # noqa: E402
+                      workload_p4_64, workload_small, workload_sweep)
+
+TOL_F64 = 1e-12
+THREADS = max(1, min(16, os.cpu_count() or 1))
+
+
+@pytest.fixture(scope="module")
+def wq():
+    import paper_1605_01238_gb300 as wq
+    from paper_1605_01238_gb300 import build
+    build.build()
+    wq.load()
+    return wq
+
+
+def row_ptr_reference(orc):
+    bw = [np.array([len(I) for I in d.I], dtype=np.int64) for d in orc.dirs]
+    counts = np.kron(bw[2], np.kron(bw[1], bw[0]))
+    return np.concatenate([[0], np.cumsum(counts)])
+
+
+def gather_rows(vals, rp, rows):
+    idx = np.concatenate([np.arange(rp[r], rp[r + 1]) for r in rows])
+    return vals[torch.as_tensor(idx, device=vals.device)].cpu().numpy()
+
+
+def check_rows(orc, plan, vals, which, rows, tol=TOL_F64):
+    rp_d, col_d = plan.pattern()
+    rp = rp_d.cpu().numpy()
+    np.testing.assert_array_equal(rp, row_ptr_reference(orc))
+    got_all = gather_rows(vals, rp, rows)
+    cols_all = gather_rows(col_d, rp, rows)
+    ref = rows_c(orc, rows, which, threads=THREADS)
+    off, worst = 0, 0.0
+    for r, rv in zip(rows, ref):
+        k = len(rv)
+        np.testing.assert_array_equal(cols_all[off:off + k], orc.row_cols(int(r)))
+        got = got_all[off:off + k].astype(np.float64)
+        err = np.abs(got - rv).max() / np.abs(rv).max()
+        worst = max(worst, err)
+        off += k
+    assert worst <= tol, f"{which}: worst row-relative error {worst:.3e} > {tol:.1e}"
+    return worst
+
+
+def make(wq, patch, kappa=None):
+    plan = wq.Plan(patch.p, patch.knots, patch.ctrl)
+    orc = Oracle3D(patch.p, patch.knots, patch.ctrl, kappa=kappa)
+    return plan, orc
+
+
+# --- small meshes, every row -------------------------------------------------------
+
+SMALL = [
+    ("p2_16", lambda: workload_small()),
+    ("p2_2x2x2", lambda: perturbed_cube(2, (2, 2, 2), seed=3)),
+    ("p3_2x3x7", lambda: perturbed_cube(3, (2, 3, 7), seed=4)),
+    ("p4_3x9x5", lambda: perturbed_cube(4, (3, 9, 5), seed=5)),
+    ("p5_6x2x4", lambda: perturbed_cube(5, (6, 2, 4), seed=6)),
+    ("p3_graded", lambda: perturbed_cube(3, (6, 5, 7), seed=7,
+                                         breaks=[graded_breaks(e, seed=40 + k) for k, e in enumerate((6, 5, 7))])),
+    ("p2_ragged_37x5x3", lambda: perturbed_cube(2, (37, 5, 3), seed=8)),
+]
+
+
+@pytest.mark.parametrize("name,factory", SMALL, ids=[s[0] for s in SMALL])
+def test_every_row_matches_oracle(wq, name, factory):
+    patch = factory()
+    plan, orc = make(wq, patch)
+    S = plan.stiffness()
+    M = plan.mass()
+    torch.cuda.synchronize()
+    plan.sync_check()
+    rows = np.arange(plan.n_rows)
+    check_rows(orc, plan, S, "stiffness", rows)
+    check_rows(orc, plan, M, "mass", rows)
+    rp, col = plan.pattern()
+    assert int(rp[-1]) == plan.nnz == int(np.prod([sum(len(I) for I in d.I) for d in orc.dirs]))
+
+
+def test_kappa_field(wq):
+    patch = perturbed_cube(2, (5, 6, 4), seed=9)
+    plan = wq.Plan(patch.p, patch.knots, patch.ctrl)
+    kappa = random_field(int(np.prod(plan.n_qp)), seed=77, kind="positive")
+    orc = Oracle3D(patch.p, patch.knots, patch.ctrl, kappa=kappa)
+    kd = torch.as_tensor(kappa, device="cuda")
+    S = plan.stiffness(kappa=kd)
+    M = plan.mass(kappa=kd)
+    torch.cuda.synchronize()
+    rows = np.arange(plan.n_rows)
+    check_rows(orc, plan, S, "stiffness", rows)
+    check_rows(orc, plan, M, "mass", rows)
+
+
+# --- univariate data and coefficients ------------------------------------------------
+
+@pytest.mark.parametrize("p,nel", [(2, 16), (4, 11), (6, 9), (8, 12)])
+def test_points_and_rules_match_oracle(wq, p, nel):
+    patch = perturbed_cube(p, (nel, 3, 2), seed=10)
+    plan, orc = make(wq, patch)
+    d = orc.dirs[0]
+    x = plan.points(0)
+    np.testing.assert_allclose(x, d.x, rtol=2.3e-16, atol=0)
+    for a in (0, 1):
+        for b in (0, 1):
+            w, q0, nq = plan.rules(0, a, b)
+            for i in range(d.n):
+                Q = d.Q[i]
+                assert q0[i] == Q[0] and nq[i] == len(Q)
+                ref = d.W[a, b, i, Q]
+                err = np.abs(w[i, :nq[i]] - ref).max() / np.abs(ref).max()
+                assert err <= 1e-14, f"rule ({a},{b}) i={i}: {err:.2e}"
+                assert np.all(w[i, nq[i]:] == 0.0)
+
+
+def test_coefficients_match_oracle(wq):
+    patch = perturbed_cube(3, (7, 5, 6), seed=11)
+    plan, orc = make(wq, patch)
+    c = plan.coefficients()
+    scale = np.abs(orc.coef).reshape(7, -1).max(1)
+    err = (np.abs(c - orc.coef).reshape(7, -1).max(1) / scale)
+    assert np.all(err <= 1e-13), err
+
+
+def test_affine_map_gives_galerkin_and_bitexact_pattern(wq):
+    from oracle import galerkin_dense
+    A = np.array([[1.2, 0.3, 0.1], [-0.2, 0.8, 0.25], [0.15, -0.1, 1.05]])
+    patch = affine_cube(3, (3, 2, 4), A, np.array([0.3, 0.2, 0.1]))
+    plan = wq.Plan(patch.p, patch.knots, patch.ctrl)
+    S = plan.csr(plan.stiffness()).to_dense().cpu().numpy()
+    M = plan.csr(plan.mass()).to_dense().cpu().numpy()
+    S_g, M_g = galerkin_dense(3, patch.knots, patch.ctrl)
+    assert np.abs(S - S_g).max() <= 1e-12 * np.abs(S_g).max()
+    assert np.abs(M - M_g).max() <= 1e-12 * np.abs(M_g).max()
+
+
+# --- full-size workloads, sampled rows -------------------------------------------------
+
+def test_p4_64_sampled_rows(wq):
+    patch = workload_p4_64()
+    plan, orc = make(wq, patch)
+    S = plan.stiffness()
+    torch.cuda.synchronize()
+    plan.sync_check()
+    rows = sample_rows(plan.n, plan.p, 160, seed=2024)
+    check_rows(orc, plan, S, "stiffness", rows)
+    M = plan.mass()
+    torch.cuda.synchronize()
+    check_rows(orc, plan, M, "mass", rows[:64])
+
+
+@pytest.mark.parametrize("p,count", [(2, 96), (3, 96), (5, 64), (6, 40), (8, 16)])
+def test_degree_sweep_sampled_rows(wq, p, count):
+    patch = workload_sweep(p)
+    plan, orc = make(wq, patch)
+    S = plan.stiffness()
+    torch.cuda.synchronize()
+    plan.sync_check()
+    rows = sample_rows(plan.n, plan.p, count, seed=3000 + p)
+    check_rows(orc, plan, S, "stiffness", rows)
+    del S
+    torch.cuda.empty_cache()
+
+
+# --- reduced precision: error report ------------------------------------------------------
+
+@pytest.mark.parametrize("dtype", ["float32", "float64"])
+def test_fp32_contractions_error(wq, dtype):
+    patch = perturbed_cube(4, (12, 10, 9), seed=12)
+    plan, orc = make(wq, patch)
+    S = plan.stiffness(precision="fp32", dtype=getattr(torch, dtype))
+    torch.cuda.synchronize()
+    rows = sample_rows(plan.n, plan.p, 120, seed=5)
+    worst = check_rows(orc, plan, S, "stiffness", rows, tol=2e-5)
+    print(f"fp32 contractions, {dtype} values: worst row-relative error {worst:.3e}")
+
+
+# --- geometry updates, refresh, host end-to-end ------------------------------------------------
+
+def test_set_geometry_and_refresh(wq):
+    a = perturbed_cube(3, (6, 5, 4), seed=13)
+    b = perturbed_cube(3, (6, 5, 4), seed=14)
+    plan = wq.Plan(a.p, a.knots, a.ctrl)
+    plan.set_geometry(torch.as_tensor(b.ctrl, device="cuda"))
+    S = plan.stiffness()
+    torch.cuda.synchronize()
+    orc_b = Oracle3D(b.p, b.knots, b.ctrl)
+    rows = np.arange(plan.n_rows)
+    check_rows(orc_b, plan, S, "stiffness", rows)
+    plan.refresh(a.ctrl)
+    S2 = plan.stiffness()
+    torch.cuda.synchronize()
+    check_rows(Oracle3D(a.p, a.knots, a.ctrl), plan, S2, "stiffness", rows)
+
+
+def test_host_end_to_end_matches_device_path(wq):
+    patch = perturbed_cube(2, (7, 6, 5), seed=15)
+    plan = wq.Plan(patch.p, patch.knots, patch.ctrl)
+    d_vals = torch.empty(plan.nnz, dtype=torch.float64, device="cuda")
+    h_vals = torch.empty(plan.nnz, dtype=torch.float64).pin_memory()
+    plan.assemble_host("stiffness", patch.ctrl.reshape(-1).copy(), d_vals, h_vals)
+    ref = plan.stiffness()
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(h_vals.numpy(), ref.cpu().numpy())
+
+
+def test_inverted_geometry_is_reported(wq):
+    patch = perturbed_cube(2, (3, 3, 3), seed=16, amp=0.0)
+    ctrl = patch.ctrl.copy()
+    ctrl[:, 0] = -ctrl[:, 0]                      # mirror: det DF < 0 everywhere
+    with pytest.raises(wq.WqError) as e:
+        wq.Plan(2, patch.knots, ctrl)
+    assert e.value.status == 4
+    ok = wq.Plan(2, patch.knots, patch.ctrl)      # the context stays usable
+    ok.stiffness()
+    torch.cuda.synchronize()
+    ok.sync_check()
