@@ -374,18 +374,56 @@ def exact_integrals(knot_vector, p: int, ng: int) -> np.ndarray:
 COEF_LM = ((0, 0), (0, 1), (0, 2), (1, 1), (1, 2), (2, 2))
 
 
-def jacobians(dirs: list, ctrl: np.ndarray) -> np.ndarray:
-    """DF at every point of the tensor grid: array (nqp3, nqp2, nqp1, 3, 3),
-    DF[r, c] = sum_i C_i[r] d/dzeta_c B_i, by einsum over the dense univariate tables."""
+def greville_exact(knot_vector, p: int) -> list:
+    """Greville abscissae g_i = (xi_{i+1} + ... + xi_{i+p}) / p as exact rationals."""
+    xi = [Fraction(float(v)) for v in knot_vector]
+    n = len(xi) - p - 1
+    return [sum(xi[i + 1:i + p + 1], Fraction(0)) / p for i in range(n)]
+
+
+def control_offsets(dirs: list, ctrl: np.ndarray) -> np.ndarray:
+    """C_i - g_i, g_i = (g_{1,i1}, g_{2,i2}, g_{3,i3}) the Greville point of i:
+    array (n3, n2, n1, 3). Each Greville abscissa is split exactly into
+    hi + lo doubles; C - hi is formed exactly by two-sum, and the result is
+    rounded once more (within one ulp of the exact difference)."""
     n1, n2, n3 = (d.n for d in dirs)
     C = np.asarray(ctrl, dtype=np.float64).reshape(n3, n2, n1, 3)
+    out = np.empty_like(C)
+    shapes = [(1, 1, n1), (1, n2, 1), (n3, 1, 1)]
+    for r, d in enumerate(dirs):
+        g = greville_exact(d.xi, d.p)
+        hi = np.array([float(v) for v in g])
+        lo = np.array([float(v - Fraction(float(v))) for v in g])
+        hi, lo = hi.reshape(shapes[r]), lo.reshape(shapes[r])
+        c = C[..., r]
+        s = c - hi                                   # two-sum: s + e = c - hi exactly
+        bb = s - c
+        e = (c - (s - bb)) + (-hi - bb)
+        out[..., r] = s + (e - lo)
+    return out
+
+
+def jacobians(dirs: list, ctrl: np.ndarray) -> np.ndarray:
+    """DF at every point of the tensor grid: array (nqp3, nqp2, nqp1, 3, 3),
+    DF[r, c] = d/dzeta_c of F_r, F = sum_i C_i B_i (Section 3).
+
+    B-splines reproduce linear functions with the Greville points as
+    coefficients, zeta = sum_i g_i B_i(zeta), so F(zeta) = zeta + sum_i (C_i - g_i) B_i(zeta)
+    and DF = I + sum_i (C_i - g_i) x grad B_i: the same matrix, without summing the
+    O(1/h) terms C_i x grad B_i that cancel to O(1) (their rounding would reach
+    the stiffness entries amplified by the rules' conditioning at high degree).
+    The sums are einsums over the dense univariate tables."""
+    D = control_offsets(dirs, ctrl)
     B = [d.B for d in dirs]                          # (2, n, nqp) each
     out = np.empty((dirs[2].nqp, dirs[1].nqp, dirs[0].nqp, 3, 3))
     for c in range(3):
         D1 = B[0][1 if c == 0 else 0]
         D2 = B[1][1 if c == 1 else 0]
         D3 = B[2][1 if c == 2 else 0]
-        out[..., :, c] = np.einsum("kjir,ia,jb,kc->cbar", C, D1, D2, D3, optimize=True)
+        out[..., :, c] = np.einsum("kjir,ia,jb,kc->cbar", D, D1, D2, D3, optimize=True)
+    out[..., 0, 0] += 1.0
+    out[..., 1, 1] += 1.0
+    out[..., 2, 2] += 1.0
     return out
 
 

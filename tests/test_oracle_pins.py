@@ -326,3 +326,18 @@ def test_c_rows_match_python_rows(which):
     for r, g in zip(rows, got):
         ref = orc.row_values(int(r), which)
         np.testing.assert_allclose(g, ref, rtol=0, atol=1e-14 * np.abs(ref).max())
+
+
+def test_greville_points_reproduce_linear_functions():
+    # zeta = sum_i g_i B_i(zeta): the identity behind DF = I + sum (C_i - g_i) grad B_i
+    for p in (2, 4, 7):
+        kv = open_knot_vector(graded_breaks(6, seed=p), p)
+        g = np.array([float(v) for v in wo.greville_exact(kv, p)])
+        x = np.linspace(0, 1, 41)
+        np.testing.assert_allclose(wo.bspline_all(kv, p, x, 0) @ g, x, atol=1e-15)
+        np.testing.assert_allclose(wo.bspline_all(kv, p, x, 1) @ g, 1.0, atol=1e-12)
+    patch = perturbed_cube(3, (4, 3, 5), seed=0, amp=0.0)
+    orc_dirs = [wo.Direction(k, 3) for k in patch.knots]
+    assert np.abs(wo.control_offsets(orc_dirs, patch.ctrl)).max() <= 2.3e-16   # float Greville net: 1 ulp
+    J = wo.jacobians(orc_dirs, patch.ctrl)
+    np.testing.assert_allclose(J, np.broadcast_to(np.eye(3), J.shape), atol=1e-15)
