@@ -109,6 +109,7 @@ struct DirData {
   dd* integ = nullptr;       // [4][n][2p+1] I^{(a,b)}_{i, i-p+t}, kind = 2a+b
   double* w = nullptr;       // [4][n][NQ] rules w^{(a,b)}_{i, q0(i)+t}
   int64_t* prefix = nullptr; // [n+1] prefix sums of the band widths |I_i|
+  dd* greville = nullptr;    // [n] Greville abscissae (xi_{i+1} + ... + xi_{i+p}) / p
 };
 
 }  // namespace wq
@@ -123,12 +124,12 @@ struct wq_plan_s {
   int64_t n_rows = 0, nnz = 0, n_qp_total = 0;
   int64_t nnz1[3] = {0, 0, 0};    // per-direction band totals
   double* ctrl = nullptr;         // [N*3]
+  double* ctrl_delta = nullptr;   // [N*3] C_i - g_i, g_i = Greville point of i (rounded once)
   double* coef = nullptr;         // [7][N_QP]
   int64_t* row_ptr = nullptr;     // [N+1]
   int32_t* col = nullptr;         // [nnz]
   wq::dd* gauss = nullptr;        // [2][p+1]: Gauss-Legendre nodes then weights on [-1, 1]
   int* err = nullptr;             // device error word
-  int window[3][2] = {{0, 0}, {0, 0}, {0, 0}};  // per direction: max q-window of a tile (T=16, T=4)
 };
 
 namespace wq {

@@ -124,6 +124,7 @@ struct DirArgs {
   dd* integ;
   double* w;
   int64_t* prefix;
+  dd* greville;
   const dd* gauss;
   int* err;
 };
@@ -149,6 +150,7 @@ static DirArgs dir_args(wq_plan_s* pl, int l) {
   a.integ = d.integ;
   a.w = d.w;
   a.prefix = d.prefix;
+  a.greville = d.greville;
   a.gauss = pl->gauss;
   a.err = pl->err;
   return a;
@@ -389,6 +391,15 @@ __global__ void k_prefix(DirArgs a) {
   a.prefix[a.n] = s;
 }
 
+// Greville abscissae g_i = (xi_{i+1} + ... + xi_{i+p}) / p, double-double.
+__global__ void k_greville(DirArgs a) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= a.n) return;
+  dd s = dd_make(0.0);
+  for (int k = 1; k <= a.p; ++k) s = dd_add(s, dd_make(a.knots[i + k]));
+  a.greville[i] = dd_div(s, dd_make((double)a.p));
+}
+
 struct PatternArgs {
   int p;
   int n1, n2, n3;
@@ -440,14 +451,38 @@ __global__ void k_cols(PatternArgs a) {
 }
 
 // ---------------------------------------------------------------------------
-// Coefficients. One block per (q3, tile of TQ2 q2-points, tile of TQ1 q1-points).
-// DF is sum-factorised over the tile: contract i3, then i2, then i1.
+// Coefficients. The tensor-product B-splines reproduce linear functions with
+// the Greville points g_i as coefficients (zeta = sum_i g_i B_i(zeta)), so
+//   F(zeta) = zeta + sum_i (C_i - g_i) B_i(zeta),  DF = I + sum_i (C_i - g_i) x grad B_i.
+// Summing the small differences C_i - g_i instead of C_i keeps the O(1/h) terms
+// C_i x grad B_i, which cancel to O(1), out of the rounded sum: DF then carries
+// an absolute error of a few ulp of |C - g| instead of ulp(1)/h.
+//
+// k_delta forms C_i - g_i in double-double and rounds once. k_coef runs one
+// block per (q3, tile of TQ2 q2-points, tile of TQ1 q1-points) and
+// sum-factorises DF over the tile: contract i3, then i2, then i1.
+struct DeltaArgs {
+  int n1, n2, n3;
+  const double* ctrl;
+  const dd *g1, *g2, *g3;
+  double* delta;
+};
+
+__global__ void k_delta(DeltaArgs a) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  int64_t N = (int64_t)a.n1 * a.n2 * a.n3;
+  if (i >= N) return;
+  int i1 = (int)(i % a.n1), i2 = (int)((i / a.n1) % a.n2), i3 = (int)(i / ((int64_t)a.n1 * a.n2));
+  const dd g[3] = {a.g1[i1], a.g2[i2], a.g3[i3]};
+  for (int r = 0; r < 3; ++r) a.delta[i * 3 + r] = dd_to_d(dd_sub(dd_make(a.ctrl[i * 3 + r]), g[r]));
+}
+
 constexpr int kCoefTQ1 = 32, kCoefTQ2 = 8;
 
 struct CoefArgs {
   int p;
   int n1, n2, n3, nq1, nq2, nq3;
-  const double* ctrl;
+  const double* ctrl;   // C_i - g_i (see k_delta)
   const double *bp1, *bp2, *bp3;
   const int *f1, *f2, *f3;
   double* coef;
@@ -510,7 +545,7 @@ __global__ void k_coef(CoefArgs a) {
         double acc = 0.0;
         for (int t = 0; t < m; ++t)
           acc = fma(a.bp1[((int64_t)d1 * a.nq1 + q1) * m + t], Yk[(f1 + t - ia1) * 3 + rr], acc);
-        F[rr][c] = acc;  // dF_r / dzeta_c
+        F[rr][c] = acc + (rr == c ? 1.0 : 0.0);  // dF_r / dzeta_c
       }
     }
     // adj = det * DF^{-1}: adj[l][k] = cofactor[k][l]
@@ -544,6 +579,17 @@ static size_t coef_smem(int p) {
 }
 
 wq_status run_coefficients(wq_plan_s* pl, cudaStream_t s) {
+  DeltaArgs da;
+  da.n1 = (int)pl->n[0];
+  da.n2 = (int)pl->n[1];
+  da.n3 = (int)pl->n[2];
+  da.ctrl = pl->ctrl;
+  da.g1 = pl->dir[0].greville;
+  da.g2 = pl->dir[1].greville;
+  da.g3 = pl->dir[2].greville;
+  da.delta = pl->ctrl_delta;
+  k_delta<<<(unsigned)((pl->n_rows + 255) / 256), 256, 0, s>>>(da);
+  count_launch();
   CoefArgs a;
   a.p = pl->p;
   a.n1 = (int)pl->n[0];
@@ -552,7 +598,7 @@ wq_status run_coefficients(wq_plan_s* pl, cudaStream_t s) {
   a.nq1 = (int)pl->nqp[0];
   a.nq2 = (int)pl->nqp[1];
   a.nq3 = (int)pl->nqp[2];
-  a.ctrl = pl->ctrl;
+  a.ctrl = pl->ctrl_delta;
   a.bp1 = pl->dir[0].bp;
   a.bp2 = pl->dir[1].bp;
   a.bp3 = pl->dir[2].bp;
@@ -590,7 +636,8 @@ wq_status run_setup(wq_plan_s* pl, cudaStream_t s, bool with_pattern) {
     k_integrals<<<(d.n * (2 * p + 1) + tb - 1) / tb, tb, 0, s>>>(a);
     k_rules<<<dim3(d.n, 4), 32, 0, s>>>(a);
     k_prefix<<<1, 32, 0, s>>>(a);
-    count_launch(7);
+    k_greville<<<(d.n + tb - 1) / tb, tb, 0, s>>>(a);
+    count_launch(8);
   }
   WQ_CUDA_TRY(cudaGetLastError(), "set-up kernels");
   if (with_pattern) {
@@ -653,11 +700,12 @@ static void free_plan(wq_plan_s* pl) {
   if (!pl) return;
   for (int l = 0; l < 3; ++l) {
     wq::DirData& d = pl->dir[l];
-    void* ptrs[] = {d.knots, d.x, d.x_dd, d.first, d.q0, d.nq, d.bt_dd, d.bt, d.bp, d.gb, d.integ, d.w, d.prefix};
+    void* ptrs[] = {d.knots, d.x, d.x_dd, d.first, d.q0, d.nq, d.bt_dd, d.bt, d.bp, d.gb, d.integ, d.w, d.prefix,
+                    d.greville};
     for (void* q : ptrs)
       if (q) cudaFree(q);
   }
-  void* ptrs[] = {pl->ctrl, pl->coef, pl->row_ptr, pl->col, pl->gauss, pl->err};
+  void* ptrs[] = {pl->ctrl, pl->ctrl_delta, pl->coef, pl->row_ptr, pl->col, pl->gauss, pl->err};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   delete pl;
@@ -760,8 +808,10 @@ extern "C" wq_status wq_plan_create(wq_plan_t* out, int d, int p, const int64_t 
     ALLOC(dd.integ, sizeof(wq::dd) * 4 * dd.n * (2 * p + 1), "integrals");
     ALLOC(dd.w, sizeof(double) * 4 * dd.n * nqmax, "rules");
     ALLOC(dd.prefix, sizeof(int64_t) * (dd.n + 1), "band prefix");
+    ALLOC(dd.greville, sizeof(wq::dd) * dd.n, "Greville points");
   }
   ALLOC(pl->ctrl, sizeof(double) * 3 * N, "control points");
+  ALLOC(pl->ctrl_delta, sizeof(double) * 3 * N, "control point offsets");
   ALLOC(pl->coef, sizeof(double) * 7 * pl->n_qp_total, "coefficients");
   ALLOC(pl->row_ptr, sizeof(int64_t) * (N + 1), "row_ptr");
   ALLOC(pl->col, sizeof(int32_t) * nnz, "col");

@@ -17,6 +17,12 @@ from wq_synth import (affine_cube, graded_breaks, perturbed_cube, random_field, 
                       workload_p4_64, workload_small, workload_sweep)
 
 TOL_F64 = 1e-12
+# p = 8: stiffness entries amplify relative perturbations of the coefficients c_lm
+# by A ~ 3e3 (tests/test_oracle_pins.py::test_high_degree_amplification measures it
+# on the CPU). Two independent FP64 evaluations of c_lm differ by a few ulp, so the
+# entries of two correct implementations differ by ~A * 4 ulp ~ 1.3e-12; the bar
+# for p = 8 is 10 ulp * A = 5e-12. Every p <= 6 case keeps 1e-12.
+TOL_F64_P8 = 5e-12
 THREADS = max(1, min(16, os.cpu_count() or 1))
 
 
@@ -173,7 +179,7 @@ def test_degree_sweep_sampled_rows(wq, p, count):
     torch.cuda.synchronize()
     plan.sync_check()
     rows = sample_rows(plan.n, plan.p, count, seed=3000 + p)
-    check_rows(orc, plan, S, "stiffness", rows)
+    check_rows(orc, plan, S, "stiffness", rows, tol=TOL_F64_P8 if p == 8 else TOL_F64)
     del S
     torch.cuda.empty_cache()
 
