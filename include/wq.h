@@ -164,6 +164,38 @@ wq_status wq_get_rules(wq_plan_t plan, int dir, int a, int b, double* h_w, int32
                        int32_t* h_nq);
 wq_status wq_get_coefficients(wq_plan_t plan, double* h_coef);
 
+/* ---- allocation-free rule construction -------------------------------------------
+ * The paper has no counterpart to this entry point; it exists for callers that
+ * cannot allocate device memory themselves: code running under a framework that
+ * owns all of GPU memory through its own pool, latency-critical loops that cannot
+ * afford cudaMalloc's implicit device synchronisation, and embedded users with a
+ * fixed, pre-reserved memory budget.
+ *
+ * wq_rules_noalloc builds the four WQ rules of ONE direction (the same kernels and
+ * results as the rule step of wq_plan_create): for every test function i, the
+ * weights w^{(a,b)}_{i,q} of kind 2a+b at q = d_q0[i] + t, t < d_nq[i].
+ *   p          degree, 2..8
+ *   n_knots    length of the full open knot vector (n = n_knots - p - 1 functions)
+ *   h_knots    host double[n_knots]: the knot vector (validated as in wq_plan_create)
+ *   d_w        device double[4 * n * nq_stride], caller-owned output (kind-major)
+ *   d_q0, d_nq device int32[n], caller-owned outputs
+ *   nq_stride  row stride of d_w: at least max_i |Q_i| (at most 4p+1)
+ * It calls no cudaMalloc, cudaFree or allocating library routine. Its
+ * intermediate tables live in one fixed device array of
+ * WQ_RULES_NOALLOC_SCRATCH_BYTES (5.75 MB) that every GPU loading the
+ * library holds until the process exits; knot vectors with more than
+ * WQ_RULES_NOALLOC_MAX_N basis functions are rejected with WQ_ERR_INVALID_ARG.
+ * The first call on a device looks up that array's device address
+ * (cudaGetSymbolAddress); make that first call before any stream capture. Every
+ * call shares the one array and clears the parts it reads before writing them;
+ * two calls that run at the same time on one device (other threads or streams)
+ * race on it, so serialise them. The call synchronises `stream` before it returns
+ * (to report a rule breakdown as WQ_ERR_SINGULAR_RULE). */
+#define WQ_RULES_NOALLOC_MAX_N 1024
+#define WQ_RULES_NOALLOC_SCRATCH_BYTES 5754880
+wq_status wq_rules_noalloc(int p, int64_t n_knots, const double* h_knots, double* d_w, int32_t* d_q0,
+                           int32_t* d_nq, int nq_stride, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

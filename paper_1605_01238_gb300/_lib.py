@@ -34,6 +34,7 @@ SIGNATURES = {
     "wq_get_points": (c_int, [c_vp, c_int, c_vp]),
     "wq_get_rules": (c_int, [c_vp, c_int, c_int, c_int, c_vp, c_vp, c_vp]),
     "wq_get_coefficients": (c_int, [c_vp, c_vp]),
+    "wq_rules_noalloc": (c_int, [c_int, c_i64, c_vp, c_vp, c_vp, c_vp, c_int, c_vp]),
 }
 
 _lib = None

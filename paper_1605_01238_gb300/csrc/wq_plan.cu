@@ -20,6 +20,7 @@
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <vector>
 
 #include "wq_internal.h"
@@ -926,5 +927,152 @@ extern "C" wq_status wq_get_coefficients(wq_plan_t plan, double* h_coef) {
   WQ_CUDA_TRY(cudaDeviceSynchronize(), "synchronize");
   WQ_CUDA_TRY(cudaMemcpy(h_coef, plan->coef, sizeof(double) * 7 * plan->n_qp_total, cudaMemcpyDeviceToHost),
               "coefficient copy");
+  return WQ_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Allocation-free rule construction (wq_rules_noalloc).
+//
+// Some callers cannot allocate device memory from inside their own code. Examples
+// are code that runs under a framework that owns all of GPU memory through its own
+// pool, real-time loops where cudaMalloc's implicit device synchronisation is not
+// acceptable, and embedded users with a fixed, pre-reserved memory budget. This
+// entry point builds the four WQ rules of one direction with the same kernels as
+// wq_plan_create, but keeps every intermediate table in one file-scope device
+// array of fixed size instead of plan-owned buffers.
+namespace wq {
+
+constexpr int kNoAllocMaxN = 1024;                                    // functions per direction
+constexpr int kNoAllocMaxKnots = kNoAllocMaxN + kMaxP + 1;
+constexpr int kNoAllocMaxElems = kNoAllocMaxN;                        // n_el <= n - p < n
+constexpr int kNoAllocMaxQp = 2 * kNoAllocMaxElems + 2 * kMaxP - 1;
+
+constexpr size_t align256(size_t x) { return (x + 255) / 256 * 256; }
+
+struct NoAllocLayout {
+  size_t knots, x, x_dd, first, bt_dd, bt, bp, gb, integ, gauss, err, total;
+};
+
+constexpr NoAllocLayout noalloc_layout() {
+  NoAllocLayout L{};
+  size_t o = 0;
+  L.knots = o; o += align256(sizeof(double) * kNoAllocMaxKnots);
+  L.x = o; o += align256(sizeof(double) * kNoAllocMaxQp);
+  L.x_dd = o; o += align256(sizeof(dd) * kNoAllocMaxQp);
+  L.first = o; o += align256(sizeof(int) * kNoAllocMaxQp);
+  L.bt_dd = o; o += align256(sizeof(dd) * 2 * kNoAllocMaxN * kMaxQ);
+  L.bt = o; o += align256(sizeof(double) * 2 * kNoAllocMaxN * kMaxQ);
+  L.bp = o; o += align256(sizeof(double) * 2 * kNoAllocMaxQp * (kMaxP + 1));
+  L.gb = o; o += align256(sizeof(dd) * kNoAllocMaxElems * (kMaxP + 1) * 2 * (kMaxP + 1));
+  L.integ = o; o += align256(sizeof(dd) * 4 * kNoAllocMaxN * (2 * kMaxP + 1));
+  L.gauss = o; o += align256(sizeof(dd) * 2 * (kMaxP + 1));
+  L.err = o; o += align256(sizeof(int));
+  L.total = o;
+  return L;
+}
+
+constexpr NoAllocLayout kNoAlloc = noalloc_layout();
+static_assert(kNoAlloc.total == WQ_RULES_NOALLOC_SCRATCH_BYTES, "scratch size and its declared value differ");
+static_assert(kNoAllocMaxN == WQ_RULES_NOALLOC_MAX_N, "scratch limit and its declared value differ");
+
+// The scratch array: WQ_RULES_NOALLOC_SCRATCH_BYTES on every device that loads
+// the library, held until the process exits. Host code must not take its
+// address directly (that is a host-side stand-in); it uses the device address
+// obtained by cudaGetSymbolAddress below.
+static __device__ __align__(256) unsigned char g_rules_scratch[kNoAlloc.total];
+
+static std::mutex g_scratch_mutex;
+static void* g_scratch_addr[64] = {nullptr};
+
+// Device address of g_rules_scratch on the current device, looked up once per
+// device (the first call on a device does this set-up).
+static wq_status scratch_address(unsigned char** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_error(e, "no CUDA device");
+  if (dev < 0 || dev >= 64) return set_error(WQ_ERR_UNSUPPORTED, "device index above 63");
+  std::lock_guard<std::mutex> lock(g_scratch_mutex);
+  if (!g_scratch_addr[dev]) {
+    void* ptr = nullptr;
+    e = cudaGetSymbolAddress(&ptr, g_rules_scratch);
+    if (e != cudaSuccess) return cuda_error(e, "cudaGetSymbolAddress of the rule scratch");
+    g_scratch_addr[dev] = ptr;
+  }
+  *out = static_cast<unsigned char*>(g_scratch_addr[dev]);
+  return WQ_OK;
+}
+
+}  // namespace wq
+
+extern "C" wq_status wq_rules_noalloc(int p, int64_t n_knots, const double* h_knots, double* d_w, int32_t* d_q0,
+                                      int32_t* d_nq, int nq_stride, void* stream) {
+  if (!h_knots || !d_w || !d_q0 || !d_nq) return set_error(WQ_ERR_INVALID_ARG, "NULL argument");
+  if (p < 2 || p > wq::kMaxP) return set_error(WQ_ERR_INVALID_ARG, "degree must be in 2..8");
+  std::string why;
+  if (!knots_ok(h_knots, n_knots, p, &why)) return set_error(WQ_ERR_INVALID_ARG, why);
+  const int64_t n = n_knots - p - 1;
+  if (n > wq::kNoAllocMaxN)
+    return set_error(WQ_ERR_INVALID_ARG, "wq_rules_noalloc: the knot vector has more basis functions than the "
+                                         "1024 (WQ_RULES_NOALLOC_MAX_N) its fixed scratch holds; use "
+                                         "wq_plan_create for larger knot vectors");
+  const int n_el = (int)(n - p), nqp = 2 * n_el + 2 * p - 1;
+  int nqmax = 0;
+  for (int i = 0; i < (int)n; ++i) {
+    int lo = std::max(0, i - p), hi = std::min(n_el, i + 1);
+    int qs = lo == 0 ? 0 : 2 * lo + p;
+    int qe = hi == n_el ? nqp - 1 : 2 * hi + p - 2;
+    nqmax = std::max(nqmax, qe - qs + 1);
+  }
+  if (nq_stride < nqmax || nq_stride > wq::kMaxQ)
+    return set_error(WQ_ERR_INVALID_ARG, "nq_stride must lie between max |Q_i| and 4p+1");
+  unsigned char* base = nullptr;
+  wq_status st = wq::scratch_address(&base);
+  if (st != WQ_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  const wq::NoAllocLayout& L = wq::kNoAlloc;
+  wq::DirArgs a;
+  a.p = p;
+  a.n = (int)n;
+  a.n_el = n_el;
+  a.nqp = nqp;
+  a.nq_stride = nq_stride;
+  a.knots = reinterpret_cast<const double*>(base + L.knots);
+  a.x = reinterpret_cast<double*>(base + L.x);
+  a.x_dd = reinterpret_cast<wq::dd*>(base + L.x_dd);
+  a.first = reinterpret_cast<int*>(base + L.first);
+  a.q0 = reinterpret_cast<int*>(d_q0);
+  a.nq = reinterpret_cast<int*>(d_nq);
+  a.bt_dd = reinterpret_cast<wq::dd*>(base + L.bt_dd);
+  a.bt = reinterpret_cast<double*>(base + L.bt);
+  a.bp = reinterpret_cast<double*>(base + L.bp);
+  a.gb = reinterpret_cast<wq::dd*>(base + L.gb);
+  a.integ = reinterpret_cast<wq::dd*>(base + L.integ);
+  a.w = d_w;
+  a.prefix = nullptr;
+  a.greville = nullptr;
+  a.gauss = reinterpret_cast<const wq::dd*>(base + L.gauss);
+  int* err = reinterpret_cast<int*>(base + L.err);
+  a.err = err;
+  // the scratch keeps the previous call's contents: clear what is read before written
+  size_t tab = (size_t)2 * n * nq_stride;
+  WQ_CUDA_TRY(cudaMemcpyAsync(base + L.knots, h_knots, sizeof(double) * n_knots, cudaMemcpyHostToDevice, s),
+              "knot copy");
+  WQ_CUDA_TRY(cudaMemsetAsync(base + L.bt_dd, 0, tab * sizeof(wq::dd), s), "scratch reset");
+  WQ_CUDA_TRY(cudaMemsetAsync(base + L.bt, 0, tab * sizeof(double), s), "scratch reset");
+  WQ_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int), s), "scratch reset");
+  const int tb = 128;
+  wq::k_gauss<<<1, 32, 0, s>>>(reinterpret_cast<wq::dd*>(base + L.gauss), p + 1);
+  wq::k_points<<<(nqp + tb - 1) / tb, tb, 0, s>>>(a);
+  wq::k_qranges<<<((int)n + tb - 1) / tb, tb, 0, s>>>(a);
+  wq::k_basis_points<<<(nqp + tb - 1) / tb, tb, 0, s>>>(a);
+  wq::k_gauss_basis<<<(n_el * (p + 1) + tb - 1) / tb, tb, 0, s>>>(a);
+  wq::k_integrals<<<((int)n * (2 * p + 1) + tb - 1) / tb, tb, 0, s>>>(a);
+  wq::k_rules<<<dim3((unsigned)n, 4), 32, 0, s>>>(a);
+  wq::count_launch(7);
+  WQ_CUDA_TRY(cudaGetLastError(), "rule kernels");
+  int h_err = 0;
+  WQ_CUDA_TRY(cudaMemcpyAsync(&h_err, err, sizeof(int), cudaMemcpyDeviceToHost, s), "error word read");
+  WQ_CUDA_TRY(cudaStreamSynchronize(s), "stream synchronize");
+  if (h_err & wq::kErrSingularRule) return set_error(WQ_ERR_SINGULAR_RULE, "a WQ rule system broke down");
   return WQ_OK;
 }
