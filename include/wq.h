@@ -107,11 +107,13 @@ wq_status wq_plan_pattern(wq_plan_t plan, const int64_t** d_row_ptr, const int32
 wq_status wq_plan_set_geometry(wq_plan_t plan, const double* ctrl, int ctrl_on_device,
                                void* stream);
 
-/* Re-runs every set-up kernel of the plan in place on `stream` (points, tables,
- * integrals, rules, CSR pattern and coefficients), without allocating or
- * synchronising: the whole path from knots and control points to a matrix is
- * then wq_plan_refresh + wq_assemble_*. ctrl as in wq_plan_set_geometry, or
- * NULL to keep the plan's current control points. */
+/* Re-runs in place on `stream` every set-up kernel that depends on the knots or
+ * the control points (points, tables, integrals, rules, CSR pattern and
+ * coefficients; the Gauss-Legendre rule depends on p only and is computed once
+ * by wq_plan_create), without allocating or synchronising: the whole path from
+ * knots and control points to a matrix is then wq_plan_refresh + wq_assemble_*.
+ * ctrl as in wq_plan_set_geometry, or NULL to keep the plan's current control
+ * points. */
 wq_status wq_plan_refresh(wq_plan_t plan, const double* ctrl, int ctrl_on_device, void* stream);
 
 /* ---- assembly ---------------------------------------------------------------

@@ -200,21 +200,33 @@ __global__ void __launch_bounds__(256) k_assemble(AsmArgs A) {
         const int k2 = MASS ? 0 : 2 * (l == 1) + (m == 1);
         const double* cs = A.coef + (int64_t)slot * A.nqp_total;
         __syncthreads();  // t3s free, h2s zeroed
-        // stage 3: contract q3
-        for (int e = tid; e < W1 * W2; e += nth) {
-          const int q1l = e % W1, q2l = e / W1;
-          const int64_t base = (int64_t)(qw2 + q2l) * A.nqp1 + (qw1 + q1l);
-          Real acc = (Real)0;
-          const Real* a3 = a3s + k3 * NQ;
+        // stage 3: contract q3; two independent items per thread
+        const Real* a3 = a3s + k3 * NQ;
+        for (int e0 = tid; e0 < W1 * W2; e0 += 2 * nth) {
+          const int e1 = e0 + nth;
+          const bool two = e1 < W1 * W2;
+          const int64_t base0 = (int64_t)(qw2 + e0 / W1) * A.nqp1 + (qw1 + e0 % W1);
+          const int64_t base1 = two ? (int64_t)(qw2 + e1 / W1) * A.nqp1 + (qw1 + e1 % W1) : base0;
+          const double* c0 = cs + (int64_t)lo3 * plane + base0;
+          const double* c1 = cs + (int64_t)lo3 * plane + base1;
+          Real acc0 = (Real)0, acc1 = (Real)0;
           if (A.kappa) {
+            const double* k0 = A.kappa + (int64_t)lo3 * plane + base0;
+            const double* k1 = A.kappa + (int64_t)lo3 * plane + base1;
+#pragma unroll 4
             for (int q = 0; q < n3o; ++q) {
-              const int64_t idx = (int64_t)(lo3 + q) * plane + base;
-              acc = fmaT<Real>(a3[q], (Real)(cs[idx] * A.kappa[idx]), acc);
+              acc0 = fmaT<Real>(a3[q], (Real)(c0[q * plane] * k0[q * plane]), acc0);
+              acc1 = fmaT<Real>(a3[q], (Real)(c1[q * plane] * k1[q * plane]), acc1);
             }
           } else {
-            for (int q = 0; q < n3o; ++q) acc = fmaT<Real>(a3[q], (Real)cs[(int64_t)(lo3 + q) * plane + base], acc);
+#pragma unroll 4
+            for (int q = 0; q < n3o; ++q) {
+              acc0 = fmaT<Real>(a3[q], (Real)c0[q * plane], acc0);
+              acc1 = fmaT<Real>(a3[q], (Real)c1[q * plane], acc1);
+            }
           }
-          t3s[e] = acc;
+          t3s[e0] = acc0;
+          if (two) t3s[e1] = acc1;
         }
         __syncthreads();
         // stage 2a: fold the direction-2 test weights of this term into H2
@@ -227,66 +239,110 @@ __global__ void __launch_bounds__(256) k_assemble(AsmArgs A) {
         }
       }
       __syncthreads();
-      // stage 2b: contract q2 against the trial B-splines of direction 2
-      for (int e = tid; e < T2 * BW * W1; e += nth) {
-        const int q1l = e % W1, r = e / W1, tt2 = r % BW, il = r / BW;
-        const int i2 = i2a + il, j2 = i2 - P + tt2;
-        if (j2 < 0 || j2 >= n2) continue;
-        const int il2 = i2 - j2a, jl2 = j2 - j2a;
-        const int qi = q0j2[il2], qj = q0j2[jl2];
-        const int lo = max(qi, qj), hi = min(qi + nqj2[il2], qj + nqj2[jl2]);
-        Real acc = (Real)0;
-        const Real* bb = b2s + (b2 * J2M + jl2) * NQ;
-        const Real* hh = h2s + il * NQ * W1 + q1l;
-        for (int q = lo; q < hi; ++q) acc = fmaT<Real>(bb[q - qj], hh[(q - qi) * W1], acc);
-        Real* gp = gs + ((grp * T2 + il) * BW + tt2) * W1 + q1l;
-        *gp += acc;
+      // stage 2b: contract q2 against the trial B-splines of direction 2. One item
+      // per (q1, i2, half of the band): the q2 loop runs outside, the j2 outputs of
+      // the half are independent accumulators.
+      {
+        constexpr int HB = P + 1;  // outputs per half: tt2 in [0, P] or [P+1, 2P]
+        for (int e = tid; e < T2 * 2 * W1; e += nth) {
+          const int q1l = e % W1, r = e / W1, half = r & 1, il = r >> 1;
+          const int i2 = i2a + il, il2 = i2 - j2a;
+          const int qi = q0j2[il2], ni = nqj2[il2];
+          int lo[HB], hi[HB], jl[HB];
+          Real acc[HB];
+#pragma unroll
+          for (int k = 0; k < HB; ++k) {
+            const int tt2 = half * (P + 1) + k;
+            const int j2 = i2 - P + tt2;
+            acc[k] = (Real)0;
+            if (tt2 < BW && j2 >= 0 && j2 < n2) {
+              const int jj = j2 - j2a;
+              jl[k] = jj;
+              lo[k] = max(qi, q0j2[jj]);
+              hi[k] = min(qi + ni, q0j2[jj] + nqj2[jj]);
+            } else {
+              jl[k] = 0;
+              lo[k] = 1 << 30;
+              hi[k] = -(1 << 30);
+            }
+          }
+          const Real* hh = h2s + il * NQ * W1 + q1l;
+          const Real* bb = b2s + b2 * J2M * NQ;
+          for (int t = 0; t < ni; ++t) {
+            const int q = qi + t;
+            const Real hv = hh[t * W1];
+#pragma unroll
+            for (int k = 0; k < HB; ++k)
+              if (q >= lo[k] && q < hi[k]) acc[k] = fmaT<Real>(bb[jl[k] * NQ + q - q0j2[jl[k]]], hv, acc[k]);
+          }
+#pragma unroll
+          for (int k = 0; k < HB; ++k) {
+            const int tt2 = half * (P + 1) + k;
+            if (hi[k] > lo[k]) gs[((grp * T2 + il) * BW + tt2) * W1 + q1l] += acc[k];
+          }
+        }
       }
       __syncthreads();
     }
 
-    // stage 1: contract q1 and store
+    // stage 1: contract q1 and store. The q1 loop runs outside; the 2p+1 outputs
+    // of the row (one per j1) are independent accumulators.
     const int jl3 = j3 - jlo3;
     for (int e = tid; e < T1 * T2 * BW; e += nth) {
       const int il1 = e % T1, r = e / T1, tt2 = r % BW, il2 = r / BW;
       const int i1 = i1a + il1, i2 = i2a + il2, j2 = i2 - P + tt2;
       if (j2 < 0 || j2 >= n2) continue;
       const int qi1 = q0j1[i1 - j1a], ni1 = nqj1[i1 - j1a];
-      Real h0[MAXQ], h1[MAXQ];
-      const Real* g0 = gs + ((0 * T2 + il2) * BW + tt2) * W1;
-      for (int t = 0; t < ni1; ++t) {
-        const int q = qi1 + t - qw1;
-        if (MASS) {
-          h0[t] = w1s[il1 * NQ + t] * g0[q];
+      int lo[BW], hi[BW], qj[BW];
+      Real s[BW];
+#pragma unroll
+      for (int tt1 = 0; tt1 < BW; ++tt1) {
+        const int j1 = i1 - P + tt1;
+        s[tt1] = (Real)0;
+        if (j1 >= 0 && j1 < n1) {
+          qj[tt1] = q0j1[j1 - j1a];
+          lo[tt1] = max(qi1, qj[tt1]);
+          hi[tt1] = min(qi1 + ni1, qj[tt1] + nqj1[j1 - j1a]);
         } else {
-          const int gstride = T2 * BW * W1;
-          const Real* wk = w1s + il1 * NQ + t;
+          qj[tt1] = 0;
+          lo[tt1] = 1 << 30;
+          hi[tt1] = -(1 << 30);
+        }
+      }
+      const int gstride = T2 * BW * W1;
+      const Real* g0 = gs + (il2 * BW + tt2) * W1;   // group 0; group g at + g * gstride
+      const Real* wk = w1s + il1 * NQ;               // kind 0; kind k at + k * T1M * NQ
+      const int jrow0 = i1 - P - j1a;                // b1s row of tt1 = 0 (may be < 0)
+      for (int q = qi1; q < qi1 + ni1; ++q) {
+        const int gq = q - qw1, wq = q - qi1;
+        Real h0, h1 = (Real)0;
+        if (MASS) {
+          h0 = wk[wq] * g0[gq];
+        } else {
           // groups g = 2a+b: h_b = w^{(0,b)} G_{(0,b)} + w^{(1,b)} G_{(1,b)}
-          h0[t] = fmaT<Real>(wk[0 * A.T1M * NQ], g0[q], wk[2 * A.T1M * NQ] * g0[q + 2 * gstride]);
-          h1[t] = fmaT<Real>(wk[1 * A.T1M * NQ], g0[q + gstride], wk[3 * A.T1M * NQ] * g0[q + 3 * gstride]);
+          h0 = fmaT<Real>(wk[wq], g0[gq], wk[wq + 2 * A.T1M * NQ] * g0[gq + 2 * gstride]);
+          h1 = fmaT<Real>(wk[wq + A.T1M * NQ], g0[gq + gstride], wk[wq + 3 * A.T1M * NQ] * g0[gq + 3 * gstride]);
+        }
+#pragma unroll
+        for (int tt1 = 0; tt1 < BW; ++tt1) {
+          if (q >= lo[tt1] && q < hi[tt1]) {
+            const int idx = (jrow0 + tt1) * NQ + q - qj[tt1];
+            if (MASS)
+              s[tt1] = fmaT<Real>(b1s[idx], h0, s[tt1]);
+            else
+              s[tt1] = fmaT<Real>(b1s[idx + J1M * NQ], h1, fmaT<Real>(b1s[idx], h0, s[tt1]));
+          }
         }
       }
       const int64_t row = P3i * N2 * N1 +
                           (int64_t)bw3 * (A.d[1].prefix[i2] * N1 + (int64_t)band_w(i2, P, n2) * A.d[0].prefix[i1]);
       const int bw1 = band_w(i1, P, n1), bw2 = band_w(i2, P, n2);
       const int jlo1 = band_lo(i1, P), jlo2 = band_lo(i2, P);
-      OutT* out = vals + row + ((int64_t)jl3 * bw2 + (j2 - jlo2)) * bw1;
+      const int64_t base = row + ((int64_t)jl3 * bw2 + (j2 - jlo2)) * bw1 - jlo1;
 #pragma unroll
       for (int tt1 = 0; tt1 < BW; ++tt1) {
         const int j1 = i1 - P + tt1;
-        if (j1 < 0 || j1 >= n1) continue;
-        const int qj = q0j1[j1 - j1a];
-        const int lo = max(qi1, qj), hi = min(qi1 + ni1, qj + nqj1[j1 - j1a]);
-        const Real* bb0 = b1s + (j1 - j1a) * NQ;
-        Real s = (Real)0;
-        if (MASS) {
-          for (int q = lo; q < hi; ++q) s = fmaT<Real>(bb0[q - qj], h0[q - qi1], s);
-        } else {
-          const Real* bb1 = bb0 + J1M * NQ;
-          for (int q = lo; q < hi; ++q)
-            s = fmaT<Real>(bb1[q - qj], h1[q - qi1], fmaT<Real>(bb0[q - qj], h0[q - qi1], s));
-        }
-        out[j1 - jlo1] = (OutT)s;
+        if (j1 >= 0 && j1 < n1) vals[base + j1] = (OutT)s[tt1];
       }
     }
   }

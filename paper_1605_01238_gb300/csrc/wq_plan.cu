@@ -130,6 +130,12 @@ struct DirArgs {
   int* err;
 };
 
+// The three directions of a plan, one launch for all of them (blockIdx.y, or
+// blockIdx.z for k_rules, selects the direction; gridDim covers the largest).
+struct DirArgs3 {
+  DirArgs d[3];
+};
+
 static DirArgs dir_args(wq_plan_s* pl, int l) {
   DirData& d = pl->dir[l];
   DirArgs a;
@@ -159,7 +165,8 @@ static DirArgs dir_args(wq_plan_s* pl, int l) {
 
 // Points: p+1 equally spaced points strictly inside each boundary span,
 // x = a + k (b - a)/(p + 2), k = 1..p+1; knots and midpoints elsewhere.
-__global__ void k_points(DirArgs a) {
+__global__ void k_points(DirArgs3 A) {
+  const DirArgs& a = A.d[blockIdx.y];
   int q = blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= a.nqp) return;
   const double* chi = a.knots + a.p;  // distinct knots chi_0..chi_{n_el}
@@ -189,7 +196,8 @@ __global__ void k_points(DirArgs a) {
 }
 
 // Q_i = points strictly inside (chi_{max(0,i-p)}, chi_{min(n_el,i+1)}).
-__global__ void k_qranges(DirArgs a) {
+__global__ void k_qranges(DirArgs3 A) {
+  const DirArgs& a = A.d[blockIdx.y];
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= a.n) return;
   int lo = max(0, i - a.p), hi = min(a.n_el, i + 1);
@@ -199,7 +207,8 @@ __global__ void k_qranges(DirArgs a) {
   a.nq[i] = qe - qs + 1;
 }
 
-__global__ void k_basis_points(DirArgs a) {
+__global__ void k_basis_points(DirArgs3 A) {
+  const DirArgs& a = A.d[blockIdx.y];
   int q = blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= a.nqp) return;
   const int p = a.p;
@@ -223,7 +232,8 @@ __global__ void k_basis_points(DirArgs a) {
 }
 
 // Basis at the p+1 Gauss points of every span: gb[span][g][b][t].
-__global__ void k_gauss_basis(DirArgs a) {
+__global__ void k_gauss_basis(DirArgs3 A) {
+  const DirArgs& a = A.d[blockIdx.y];
   int id = blockIdx.x * blockDim.x + threadIdx.x;
   const int p = a.p, m = p + 1;
   if (id >= a.n_el * m) return;
@@ -244,7 +254,8 @@ __global__ void k_gauss_basis(DirArgs a) {
 }
 
 // I^{(a,b)}_{i,j} for j = i - p + t, all four kinds, by Gauss on the common spans.
-__global__ void k_integrals(DirArgs a) {
+__global__ void k_integrals(DirArgs3 A) {
+  const DirArgs& a = A.d[blockIdx.y];
   int id = blockIdx.x * blockDim.x + threadIdx.x;
   const int p = a.p, m = p + 1, bw = 2 * p + 1;
   if (id >= a.n * bw) return;
@@ -279,8 +290,10 @@ __global__ void k_integrals(DirArgs a) {
 // b = 1 the rows of M sum to zero and r is consistent; the rank-one term
 // sigma u u^T with u = D^{-1} 1 (the left null vector of the scaled matrix)
 // makes the system definite without changing w.
-__global__ void k_rules(DirArgs a) {
+__global__ void k_rules(DirArgs3 A) {
+  const DirArgs& a = A.d[blockIdx.z];
   const int i = blockIdx.x, kind = blockIdx.y;
+  if (i >= a.n) return;
   const int ka = kind >> 1, kb = kind & 1;
   const int lane = threadIdx.x;
   const int p = a.p, bw = 2 * p + 1;
@@ -382,7 +395,8 @@ __global__ void k_rules(DirArgs a) {
 }
 
 // Prefix sums of the band widths |I_i| = min(n-1, i+p) - max(0, i-p) + 1.
-__global__ void k_prefix(DirArgs a) {
+__global__ void k_prefix(DirArgs3 A) {
+  const DirArgs& a = A.d[blockIdx.y];
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   int64_t s = 0;
   for (int i = 0; i < a.n; ++i) {
@@ -393,7 +407,8 @@ __global__ void k_prefix(DirArgs a) {
 }
 
 // Greville abscissae g_i = (xi_{i+1} + ... + xi_{i+p}) / p, double-double.
-__global__ void k_greville(DirArgs a) {
+__global__ void k_greville(DirArgs3 A) {
+  const DirArgs& a = A.d[blockIdx.y];
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= a.n) return;
   dd s = dd_make(0.0);
@@ -429,7 +444,9 @@ __global__ void k_row_ptr(PatternArgs a) {
                  (int64_t)band_w(i3, a.p, a.n3) * (a.P2[i2] * N1 + (int64_t)band_w(i2, a.p, a.n2) * a.P1[i1]);
 }
 
-// Column indices: one warp per row, ascending j1 + n1 (j2 + n2 j3).
+// Column indices: one warp per row, ascending j1 + n1 (j2 + n2 j3). Each lane
+// walks its entries e = lane, lane + 32, ... keeping (t1, t2, t3) up to date
+// by carries instead of dividing every index.
 __global__ void k_cols(PatternArgs a) {
   const int64_t N = (int64_t)a.n1 * a.n2 * a.n3;
   const int lane = threadIdx.x & 31;
@@ -441,12 +458,20 @@ __global__ void k_cols(PatternArgs a) {
     int i3 = (int)(r / ((int64_t)a.n1 * a.n2));
     int w1 = band_w(i1, a.p, a.n1), w2 = band_w(i2, a.p, a.n2), w3 = band_w(i3, a.p, a.n3);
     int l1 = band_lo(i1, a.p), l2 = band_lo(i2, a.p), l3 = band_lo(i3, a.p);
-    int64_t base = a.row_ptr[r];
-    int cnt = w1 * w2 * w3;
+    int32_t* out = a.col + a.row_ptr[r];
+    const int cnt = w1 * w2 * w3;
+    int t1 = lane % w1, rest = lane / w1;
+    int t2 = rest % w2, t3 = rest / w2;
+    const int s1 = 32 % w1, c1 = 32 / w1;        // step of 32 entries: +s1 in t1, +c1 carried to t2
+    const int s2 = c1 % w2, c2 = c1 / w2;
     for (int e = lane; e < cnt; e += 32) {
-      int t1 = e % w1, rest = e / w1;
-      int t2 = rest % w2, t3 = rest / w2;
-      a.col[base + e] = (int32_t)((l1 + t1) + (int64_t)a.n1 * ((l2 + t2) + (int64_t)a.n2 * (l3 + t3)));
+      out[e] = (int32_t)((l1 + t1) + (int64_t)a.n1 * ((l2 + t2) + (int64_t)a.n2 * (l3 + t3)));
+      t1 += s1;
+      int k2 = s2, k3 = c2;
+      if (t1 >= w1) { t1 -= w1; ++k2; }
+      t2 += k2;
+      while (t2 >= w2) { t2 -= w2; ++k3; }
+      t3 += k3;
     }
   }
 }
@@ -621,25 +646,28 @@ wq_status run_coefficients(wq_plan_s* pl, cudaStream_t s) {
 
 wq_status run_setup(wq_plan_s* pl, cudaStream_t s, bool with_pattern) {
   const int p = pl->p;
-  k_gauss<<<1, 32, 0, s>>>(pl->gauss, p + 1);
-  count_launch();
+  DirArgs3 A;
+  int max_n = 0, max_qp = 0, max_el = 0;
   for (int l = 0; l < 3; ++l) {
-    DirArgs a = dir_args(pl, l);
+    A.d[l] = dir_args(pl, l);
     DirData& d = pl->dir[l];
-    const int tb = 128;
-    k_points<<<(d.nqp + tb - 1) / tb, tb, 0, s>>>(a);
-    k_qranges<<<(d.n + tb - 1) / tb, tb, 0, s>>>(a);
+    max_n = std::max(max_n, d.n);
+    max_qp = std::max(max_qp, d.nqp);
+    max_el = std::max(max_el, d.n_el);
     size_t tab = (size_t)2 * d.n * pl->nq_max;
     WQ_CUDA_TRY(cudaMemsetAsync(d.bt, 0, tab * sizeof(double), s), "table reset");
     WQ_CUDA_TRY(cudaMemsetAsync(d.bt_dd, 0, tab * sizeof(dd), s), "table reset");
-    k_basis_points<<<(d.nqp + tb - 1) / tb, tb, 0, s>>>(a);
-    k_gauss_basis<<<(d.n_el * (p + 1) + tb - 1) / tb, tb, 0, s>>>(a);
-    k_integrals<<<(d.n * (2 * p + 1) + tb - 1) / tb, tb, 0, s>>>(a);
-    k_rules<<<dim3(d.n, 4), 32, 0, s>>>(a);
-    k_prefix<<<1, 32, 0, s>>>(a);
-    k_greville<<<(d.n + tb - 1) / tb, tb, 0, s>>>(a);
-    count_launch(8);
   }
+  const int tb = 128;
+  k_points<<<dim3((max_qp + tb - 1) / tb, 3), tb, 0, s>>>(A);
+  k_qranges<<<dim3((max_n + tb - 1) / tb, 3), tb, 0, s>>>(A);
+  k_basis_points<<<dim3((max_qp + tb - 1) / tb, 3), tb, 0, s>>>(A);
+  k_gauss_basis<<<dim3((max_el * (p + 1) + tb - 1) / tb, 3), tb, 0, s>>>(A);
+  k_integrals<<<dim3((max_n * (2 * p + 1) + tb - 1) / tb, 3), tb, 0, s>>>(A);
+  k_rules<<<dim3(max_n, 4, 3), 32, 0, s>>>(A);
+  k_prefix<<<dim3(1, 3), 32, 0, s>>>(A);
+  k_greville<<<dim3((max_n + tb - 1) / tb, 3), tb, 0, s>>>(A);
+  count_launch(8);
   WQ_CUDA_TRY(cudaGetLastError(), "set-up kernels");
   if (with_pattern) {
     PatternArgs pa;
@@ -832,6 +860,9 @@ extern "C" wq_status wq_plan_create(wq_plan_t* out, int d, int p, const int64_t 
   if (e != cudaSuccess) return fail(wq::cuda_error(e, "control point copy"));
   e = cudaMemsetAsync(pl->err, 0, sizeof(int), s);
   if (e != cudaSuccess) return fail(wq::cuda_error(e, "error word reset"));
+  // the Gauss-Legendre rule depends on p only: computed once per plan
+  wq::k_gauss<<<1, 32, 0, s>>>(pl->gauss, p + 1);
+  wq::count_launch();
   st = wq::run_setup(pl, s, true);
   if (st != WQ_OK) return fail(st);
   st = read_error_word(pl, s);
@@ -1061,13 +1092,15 @@ extern "C" wq_status wq_rules_noalloc(int p, int64_t n_knots, const double* h_kn
   WQ_CUDA_TRY(cudaMemsetAsync(base + L.bt, 0, tab * sizeof(double), s), "scratch reset");
   WQ_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int), s), "scratch reset");
   const int tb = 128;
+  wq::DirArgs3 A;
+  A.d[0] = a;
   wq::k_gauss<<<1, 32, 0, s>>>(reinterpret_cast<wq::dd*>(base + L.gauss), p + 1);
-  wq::k_points<<<(nqp + tb - 1) / tb, tb, 0, s>>>(a);
-  wq::k_qranges<<<((int)n + tb - 1) / tb, tb, 0, s>>>(a);
-  wq::k_basis_points<<<(nqp + tb - 1) / tb, tb, 0, s>>>(a);
-  wq::k_gauss_basis<<<(n_el * (p + 1) + tb - 1) / tb, tb, 0, s>>>(a);
-  wq::k_integrals<<<((int)n * (2 * p + 1) + tb - 1) / tb, tb, 0, s>>>(a);
-  wq::k_rules<<<dim3((unsigned)n, 4), 32, 0, s>>>(a);
+  wq::k_points<<<(nqp + tb - 1) / tb, tb, 0, s>>>(A);
+  wq::k_qranges<<<((int)n + tb - 1) / tb, tb, 0, s>>>(A);
+  wq::k_basis_points<<<(nqp + tb - 1) / tb, tb, 0, s>>>(A);
+  wq::k_gauss_basis<<<(n_el * (p + 1) + tb - 1) / tb, tb, 0, s>>>(A);
+  wq::k_integrals<<<((int)n * (2 * p + 1) + tb - 1) / tb, tb, 0, s>>>(A);
+  wq::k_rules<<<dim3((unsigned)n, 4, 1), 32, 0, s>>>(A);
   wq::count_launch(7);
   WQ_CUDA_TRY(cudaGetLastError(), "rule kernels");
   int h_err = 0;
