@@ -162,6 +162,39 @@ def cpu_oracle_sample(patch, seconds: float, seed: int, which: str = "stiffness"
             "setup_seconds": setup_s}
 
 
+def run_batch_variant(wq, torch, stream, count: int = 64):
+    """64 seeded cubes (n_el in [8, 48]^3, p in {2, 3, 4, 5}), stiffness + mass, one
+    persistent graph-captured launch, tiles from the autotuner."""
+    from paper_1605_01238_gb300 import tune
+    from wq_synth import workload_batch
+    tiles = {int(k): tuple(v) for k, v in tune.tune(degrees=(2, 3, 4, 5), cache=None).items()}
+    patches = workload_batch(count)
+    plans = [wq.Plan(pt.p, pt.knots, pt.ctrl) for pt in patches]
+    tune.apply_tiles(plans, tiles)
+    S = [torch.empty(pl.nnz, dtype=torch.float64, device="cuda") for pl in plans]
+    M = [torch.empty(pl.nnz, dtype=torch.float64, device="cuda") for pl in plans]
+    batch = wq.Batch(plans, stiffness=S, mass=M)
+    batch.launch()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 3
+    a.record(stream)
+    for _ in range(reps):
+        batch.launch()
+    b.record(stream)
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b) / reps
+    out = {"patches": count, "nnz_written": batch.nnz_total, "work_items": batch.n_items, "grid": batch.grid,
+           "ms_per_launch": ms, "nnz_per_s": batch.nnz_total / (ms * 1e-3), "tiles": {str(k): v for k, v in tiles.items()},
+           "note": "stiffness + mass of every patch, FP64, one graph launch"}
+    batch.close()
+    for pl in plans:
+        pl.close()
+    del S, M
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_reference(args):
     """--impl reference: the CPU oracle, as it stands, on the machine's host cores."""
     rank = int(os.environ.get("RANK", "0"))
@@ -286,6 +319,7 @@ def run_ours(args):
     f32_f64_ms = timed(lambda: plan.stiffness(out=vals, precision="fp32"))
     refresh_ms = timed(lambda: plan.refresh(ctrl_d))
     del vals32
+    batch_line = run_batch_variant(wq, torch, stream) if args.batch else None
 
     # end to end through the C ABI with host buffers (pinned)
     h_ctrl = torch.as_tensor(patch.ctrl.reshape(-1)).pin_memory()
@@ -330,6 +364,7 @@ def run_ours(args):
                                "mass_fp64_assembly_only": nnz / (mass_ms * 1e-3),
                                "stiffness_fp32_f32vals": nnz / (f32_ms * 1e-3),
                                "stiffness_fp32_f64vals": nnz / (f32_f64_ms * 1e-3)},
+        "batch": batch_line,
         "e2e": {"value": world * nnz / e2e_s, "unit": "nnz/s", "h2d_bytes_per_step": 8 * 3 * N,
                 "d2h_bytes_per_step": 8 * nnz,
                 "call": "wq_assemble_host: H2D control points, refresh, assemble, D2H values"},
@@ -362,6 +397,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--p", type=int, default=4, help="degree (default: the p=4 workload)")
     ap.add_argument("--nel", type=int, default=64, help="elements per direction (default 64)")
+    ap.add_argument("--no-batch", dest="batch", action="store_false",
+                    help="skip the 64-patch batched launch variant")
     ap.add_argument("--steps-only", action="store_true",
                     help="time the steps only (no variants, e2e or CPU baseline); for profiler captures")
     args = ap.parse_args()

@@ -130,6 +130,14 @@ wq_status wq_assemble_stiffness(wq_plan_t plan, const double* d_kappa, void* d_v
 wq_status wq_assemble_mass(wq_plan_t plan, const double* d_kappa, void* d_vals,
                            int value_dtype, int precision, void* stream);
 
+/* Tile extents of the assembly kernels: each block assembles at most t1 x t2
+ * rows in directions 1 x 2 for one i3 (the three mode products of
+ * Eq. (sumfactorization) share their intermediates inside a tile). t1 = t2 = 0
+ * restores the defaults (16 x 4); otherwise 1 <= t1, t2 <= 64. A tile that does
+ * not fit in shared memory makes the assembly calls return WQ_ERR_UNSUPPORTED.
+ * The autotuner (paper_1605_01238_gb300/tune.py) picks them per degree. */
+wq_status wq_plan_set_tiles(wq_plan_t plan, int t1, int t2);
+
 /* End-to-end call with host buffers: copies h_ctrl (NULL = keep) to the device,
  * refreshes the plan, assembles S (which = 0) or M (which = 1) in FP64 into the
  * caller's device staging array d_vals (nnz doubles) and copies the values to
@@ -137,6 +145,28 @@ wq_status wq_assemble_mass(wq_plan_t plan, const double* d_kappa, void* d_vals,
  * after `stream` has finished the copy back. */
 wq_status wq_assemble_host(wq_plan_t plan, int which, const double* h_ctrl, double* d_vals,
                            double* h_vals, void* stream);
+
+/* ---- batched assembly --------------------------------------------------------
+ * Many patches of different size and degree assembled by one persistent kernel
+ * launch, captured once in a CUDA graph (a memset of the work counter and the
+ * kernel). The paper treats a single patch; rows of different patches are as
+ * independent as rows of one patch (Section 1 notes that every row can be
+ * computed on its own), so all (patch, matrix, tile) work items share one queue,
+ * ordered longest first.
+ *   plans        count plans (they must outlive the batch; wq_plan_refresh and
+ *                wq_plan_set_geometry update them in place and stay valid)
+ *   d_stiffness  NULL or count device pointers (FP64, nnz of each plan; a NULL
+ *                entry skips that patch's stiffness matrix)
+ *   d_mass       same for the mass matrices
+ * Each plan's tile extents (wq_plan_set_tiles) are read at creation. The outputs
+ * are fixed at creation; wq_batch_launch replays the graph on `stream`. */
+typedef struct wq_batch_s* wq_batch_t;
+wq_status wq_batch_create(wq_batch_t* batch, int count, const wq_plan_t* plans, void* const* d_stiffness,
+                          void* const* d_mass, void* stream);
+wq_status wq_batch_launch(wq_batch_t batch, void* stream);
+/* Work items, total nonzeros written per launch and the persistent grid size. */
+wq_status wq_batch_info(wq_batch_t batch, int64_t* n_items, int64_t* nnz_total, int* grid);
+wq_status wq_batch_destroy(wq_batch_t batch);
 
 /* ---- errors and bookkeeping --------------------------------------------------- */
 

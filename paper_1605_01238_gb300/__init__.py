@@ -15,7 +15,7 @@ import numpy as np
 
 from ._lib import WqError, check, load
 
-__all__ = ["Plan", "WqError", "launch_count", "load", "VALUES_F64", "VALUES_F32", "PREC_FP64", "PREC_FP32"]
+__all__ = ["Plan", "Batch", "WqError", "launch_count", "load", "VALUES_F64", "VALUES_F32", "PREC_FP64", "PREC_FP32"]
 
 VALUES_F64, VALUES_F32 = 0, 1
 PREC_FP64, PREC_FP32 = 0, 1
@@ -147,6 +147,10 @@ class Plan:
                 ptr, on_dev = arr.ctypes.data, 0
         check(load().wq_plan_refresh(self._h, ctypes.c_void_p(ptr), on_dev, _stream(stream)))
 
+    def set_tiles(self, t1: int = 0, t2: int = 0) -> None:
+        """Assembly tile extents in directions 1 and 2 (0, 0 = defaults)."""
+        check(load().wq_plan_set_tiles(self._h, int(t1), int(t2)))
+
     # -- assembly
     def _assemble(self, fn, kappa, out, dtype, precision, stream):
         torch = _torch()
@@ -217,3 +221,51 @@ class Plan:
         out = np.empty((7, self.n_qp[2], self.n_qp[1], self.n_qp[0]))
         check(load().wq_get_coefficients(self._h, ctypes.c_void_p(out.ctypes.data)))
         return out
+
+
+class Batch:
+    """Many plans assembled by one persistent, graph-captured launch (wq_batch_create).
+
+    stiffness / mass: None, or one CUDA float64 tensor (nnz of that plan) or None
+    per plan. The plans and tensors must stay alive as long as the batch."""
+
+    def __init__(self, plans, stiffness=None, mass=None, stream=None):
+        torch = _torch()
+        self.plans = list(plans)
+        count = len(self.plans)
+        self._keep = []
+
+        def ptrs(outs):
+            if outs is None:
+                return None
+            arr = (ctypes.c_void_p * count)()
+            for k, (pl, t) in enumerate(zip(self.plans, outs)):
+                arr[k] = None if t is None else _dev_ptr(t, torch.float64, pl.nnz, "batch output")
+            self._keep.append(outs)
+            return arr
+
+        handles = (ctypes.c_void_p * count)(*[pl.handle.value for pl in self.plans])
+        s_arr, m_arr = ptrs(stiffness), ptrs(mass)
+        h = ctypes.c_void_p()
+        check(load().wq_batch_create(ctypes.byref(h), count, ctypes.cast(handles, ctypes.c_void_p),
+                                     ctypes.cast(s_arr, ctypes.c_void_p) if s_arr is not None else None,
+                                     ctypes.cast(m_arr, ctypes.c_void_p) if m_arr is not None else None,
+                                     _stream(stream)))
+        self._h = h
+        n_items, nnz, grid = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int()
+        check(load().wq_batch_info(h, ctypes.byref(n_items), ctypes.byref(nnz), ctypes.byref(grid)))
+        self.n_items, self.nnz_total, self.grid = n_items.value, nnz.value, grid.value
+
+    def launch(self, stream=None) -> None:
+        check(load().wq_batch_launch(self._h, _stream(stream)))
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            load().wq_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -25,6 +25,7 @@
 // run over the intersection of the two supports). Values go straight to their
 // CSR position: row_ptr is closed form in the band prefix sums.
 #include <algorithm>
+#include <vector>
 
 #include "wq_internal.h"
 
@@ -48,6 +49,7 @@ struct AsmArgs {
   int nqp1, nqp2;
   void* vals;
   int nt1, nt2;          // tiles per direction 1, 2
+  int T1, T2;            // target tile extents (TileSplit)
   int T1M, T2M;          // largest tile extents
   int W1M, W2M;          // largest point windows of a tile
 };
@@ -58,6 +60,35 @@ __constant__ int kTermL[9] = {0, 0, 0, 1, 2, 1, 2, 1, 2};
 __constant__ int kTermM[9] = {0, 1, 2, 0, 0, 1, 1, 2, 2};
 __constant__ int kClassStart[7] = {0, 1, 2, 3, 5, 7, 9};
 __constant__ int kSlot[3][3] = {{0, 1, 2}, {1, 3, 4}, {2, 4, 5}};
+
+// Tiles of one direction: rows [0, p+1) and [n-p-1, n) have irregular point sets
+// (their supports reach a boundary span); rows in between are regular:
+// Q_i = [2i - p, 2i + p]. Each of the three segments is split into tiles of at
+// most T rows, so a tile is either wholly regular or wholly boundary. When the
+// regular segment is empty the whole range is one boundary segment.
+struct TileSplit {
+  int n, p, T;
+  __host__ __device__ int seg_count(int len) const { return len > 0 ? (len + T - 1) / T : 0; }
+  __host__ __device__ bool has_mid() const { return n - p - 1 > p + 1; }
+  __host__ __device__ int count() const {
+    if (!has_mid()) return seg_count(n);
+    return 2 * seg_count(p + 1) + seg_count(n - 2 * (p + 1));
+  }
+  // bounds [a, b) of tile t and whether its rows are regular
+  __host__ __device__ void tile(int t, int* a, int* b, bool* regular) const {
+    int lo, len, k, m;
+    if (!has_mid()) {
+      lo = 0; len = n; m = seg_count(n); k = t; *regular = false;
+    } else {
+      const int nb = seg_count(p + 1), nm = seg_count(n - 2 * (p + 1));
+      if (t < nb) { lo = 0; len = p + 1; m = nb; k = t; *regular = false; }
+      else if (t < nb + nm) { lo = p + 1; len = n - 2 * (p + 1); m = nm; k = t - nb; *regular = true; }
+      else { lo = n - p - 1; len = p + 1; m = nb; k = t - nb - nm; *regular = false; }
+    }
+    *a = lo + (int)((int64_t)k * len / m);
+    *b = lo + (int)((int64_t)(k + 1) * len / m);
+  }
+};
 
 __device__ __forceinline__ int band_lo(int i, int p) { return i - p > 0 ? i - p : 0; }
 __device__ __forceinline__ int band_w(int i, int p, int n) { return min(n - 1, i + p) - band_lo(i, p) + 1; }
@@ -92,28 +123,98 @@ __host__ __device__ inline SmemLayout smem_layout(int NQ, int T1M, int T2M, int 
   return L;
 }
 
+
+// Stage 2b for one item (q1, i2) of a regular direction-2 tile: the 2P+1 outputs
+// j2 = i2 - P + tt2 share the row's 2P+1 points; the (t, tt2) pattern is static.
+template <int P, typename Real>
+__device__ __forceinline__ void stage2b_regular(const Real* h2s, const Real* b2s, Real* gs, const int* q0j2, int il,
+                                                int q1l, int i2a, int j2a, int NQ, int J2M, int W1, int T2, int b2,
+                                                int grp) {
+  constexpr int BW = 2 * P + 1;
+  const int i2 = i2a + il;
+  const int qi = q0j2[i2 - j2a];
+  const Real* hh = h2s + il * NQ * W1 + q1l;
+  int brow[BW];
+  Real acc[BW];
+#pragma unroll
+  for (int tt2 = 0; tt2 < BW; ++tt2) {
+    const int jl = i2 - P + tt2 - j2a;
+    brow[tt2] = (b2 * J2M + jl) * NQ + qi - q0j2[jl];
+    acc[tt2] = (Real)0;
+  }
+#pragma unroll
+  for (int t = 0; t <= 2 * P; ++t) {
+    const Real hv = hh[t * W1];
+#pragma unroll
+    for (int tt2 = 0; tt2 < BW; ++tt2)
+      if (t >= 2 * tt2 - 2 * P && t <= 2 * tt2) acc[tt2] = fmaT<Real>(b2s[brow[tt2] + t], hv, acc[tt2]);
+  }
+  Real* g = gs + (grp * T2 + il) * BW * W1 + q1l;
+#pragma unroll
+  for (int tt2 = 0; tt2 < BW; ++tt2) g[tt2 * W1] += acc[tt2];
+}
+
+// Stage 1 for one (row i1, column block) of a regular direction-1 tile: the row's
+// 2P+1 points t, the 2P+1 outputs j1 = i1 - P + tt1, pattern t in [2 tt1 - 2P, 2 tt1].
 template <int P, bool MASS, typename Real, typename OutT>
-__global__ void __launch_bounds__(256) k_assemble(AsmArgs A) {
+__device__ __forceinline__ void stage1_regular(const Real* g0, const Real* wk, const Real* b1s, const int* q0j1,
+                                               OutT* out, int i1, int j1a, int gq0, int qi1, int NQ, int J1M,
+                                               int T1M, int gstride) {
+  constexpr int BW = 2 * P + 1;
+  int brow[BW];
+  Real s[BW];
+#pragma unroll
+  for (int tt1 = 0; tt1 < BW; ++tt1) {
+    const int jl = i1 - P + tt1 - j1a;
+    brow[tt1] = jl * NQ + qi1 - q0j1[jl];
+    s[tt1] = (Real)0;
+  }
+#pragma unroll
+  for (int t = 0; t <= 2 * P; ++t) {
+    const int gq = gq0 + t;
+    Real h0, h1 = (Real)0;
+    if (MASS) {
+      h0 = wk[t] * g0[gq];
+    } else {
+      h0 = fmaT<Real>(wk[t], g0[gq], wk[t + 2 * T1M * NQ] * g0[gq + 2 * gstride]);
+      h1 = fmaT<Real>(wk[t + T1M * NQ], g0[gq + gstride], wk[t + 3 * T1M * NQ] * g0[gq + 3 * gstride]);
+    }
+#pragma unroll
+    for (int tt1 = 0; tt1 < BW; ++tt1) {
+      if (t >= 2 * tt1 - 2 * P && t <= 2 * tt1) {
+        if (MASS)
+          s[tt1] = fmaT<Real>(b1s[brow[tt1] + t], h0, s[tt1]);
+        else
+          s[tt1] = fmaT<Real>(b1s[brow[tt1] + J1M * NQ + t], h1, fmaT<Real>(b1s[brow[tt1] + t], h0, s[tt1]));
+      }
+    }
+  }
+#pragma unroll
+  for (int tt1 = 0; tt1 < BW; ++tt1) out[i1 - P + tt1] = (OutT)s[tt1];
+}
+
+// One tile (tile1, tile2, i3) of one matrix: the body shared by the per-plan
+// kernel and the persistent batch kernel. smem_raw holds the tile's tables and
+// intermediates (layout from smem_layout); all threads of the block take part.
+template <int P, bool MASS, typename Real, typename OutT>
+__device__ __forceinline__ void assemble_tile(const AsmArgs& A, int tile1, int tile2, int i3,
+                                              unsigned char* smem_raw) {
   constexpr int BW = 2 * P + 1;
   constexpr int NK = MASS ? 1 : 4;   // weight kinds held per direction
   constexpr int NB = MASS ? 1 : 2;   // trial derivative orders
   constexpr int NG = MASS ? 1 : 4;   // stage-1 groups (a1, b1)
   constexpr int NCLASS = MASS ? 1 : 6;
   constexpr int MAXQ = 4 * P + 1;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
   Real* sm = reinterpret_cast<Real*>(smem_raw);
   const int NQ = A.NQ;
   const SmemLayout L = smem_layout<P, MASS>(NQ, A.T1M, A.T2M, A.W1M, A.W2M);
   int* si = reinterpret_cast<int*>(sm + L.total_real);
 
   const int n1 = A.d[0].n, n2 = A.d[1].n, n3 = A.d[2].n;
-  int bid = blockIdx.x;
-  const int tile1 = bid % A.nt1;
-  bid /= A.nt1;
-  const int tile2 = bid % A.nt2;
-  const int i3 = bid / A.nt2;
-  const int i1a = (int)((int64_t)tile1 * n1 / A.nt1), i1b = (int)((int64_t)(tile1 + 1) * n1 / A.nt1);
-  const int i2a = (int)((int64_t)tile2 * n2 / A.nt2), i2b = (int)((int64_t)(tile2 + 1) * n2 / A.nt2);
+  int i1a, i1b, i2a, i2b;
+  bool reg1, reg2;
+  TileSplit{n1, P, A.T1}.tile(tile1, &i1a, &i1b, &reg1);
+  TileSplit{n2, P, A.T2}.tile(tile2, &i2a, &i2b, &reg2);
   const int T1 = i1b - i1a, T2 = i2b - i2a;
   const int j1a = band_lo(i1a, P), j1b = min(n1 - 1, i1b - 1 + P), J1 = j1b - j1a + 1;
   const int j2a = band_lo(i2a, P), j2b = min(n2 - 1, i2b - 1 + P), J2 = j2b - j2a + 1;
@@ -200,151 +301,196 @@ __global__ void __launch_bounds__(256) k_assemble(AsmArgs A) {
         const int k2 = MASS ? 0 : 2 * (l == 1) + (m == 1);
         const double* cs = A.coef + (int64_t)slot * A.nqp_total;
         __syncthreads();  // t3s free, h2s zeroed
-        // stage 3: contract q3; two independent items per thread
+        // stage 3: contract q3; a thread takes its items two at a time when it has two
         const Real* a3 = a3s + k3 * NQ;
         for (int e0 = tid; e0 < W1 * W2; e0 += 2 * nth) {
           const int e1 = e0 + nth;
-          const bool two = e1 < W1 * W2;
           const int64_t base0 = (int64_t)(qw2 + e0 / W1) * A.nqp1 + (qw1 + e0 % W1);
-          const int64_t base1 = two ? (int64_t)(qw2 + e1 / W1) * A.nqp1 + (qw1 + e1 % W1) : base0;
           const double* c0 = cs + (int64_t)lo3 * plane + base0;
-          const double* c1 = cs + (int64_t)lo3 * plane + base1;
-          Real acc0 = (Real)0, acc1 = (Real)0;
-          if (A.kappa) {
-            const double* k0 = A.kappa + (int64_t)lo3 * plane + base0;
-            const double* k1 = A.kappa + (int64_t)lo3 * plane + base1;
+          const double* k0 = A.kappa ? A.kappa + (int64_t)lo3 * plane + base0 : nullptr;
+          Real acc0 = (Real)0;
+          if (e1 < W1 * W2) {
+            const int64_t base1 = (int64_t)(qw2 + e1 / W1) * A.nqp1 + (qw1 + e1 % W1);
+            const double* c1 = cs + (int64_t)lo3 * plane + base1;
+            Real acc1 = (Real)0;
+            if (k0) {
+              const double* k1 = A.kappa + (int64_t)lo3 * plane + base1;
 #pragma unroll 4
-            for (int q = 0; q < n3o; ++q) {
-              acc0 = fmaT<Real>(a3[q], (Real)(c0[q * plane] * k0[q * plane]), acc0);
-              acc1 = fmaT<Real>(a3[q], (Real)(c1[q * plane] * k1[q * plane]), acc1);
+              for (int q = 0; q < n3o; ++q) {
+                acc0 = fmaT<Real>(a3[q], (Real)(c0[q * plane] * k0[q * plane]), acc0);
+                acc1 = fmaT<Real>(a3[q], (Real)(c1[q * plane] * k1[q * plane]), acc1);
+              }
+            } else {
+#pragma unroll 4
+              for (int q = 0; q < n3o; ++q) {
+                acc0 = fmaT<Real>(a3[q], (Real)c0[q * plane], acc0);
+                acc1 = fmaT<Real>(a3[q], (Real)c1[q * plane], acc1);
+              }
             }
+            t3s[e1] = acc1;
+          } else if (k0) {
+#pragma unroll 4
+            for (int q = 0; q < n3o; ++q) acc0 = fmaT<Real>(a3[q], (Real)(c0[q * plane] * k0[q * plane]), acc0);
           } else {
 #pragma unroll 4
-            for (int q = 0; q < n3o; ++q) {
-              acc0 = fmaT<Real>(a3[q], (Real)c0[q * plane], acc0);
-              acc1 = fmaT<Real>(a3[q], (Real)c1[q * plane], acc1);
-            }
+            for (int q = 0; q < n3o; ++q) acc0 = fmaT<Real>(a3[q], (Real)c0[q * plane], acc0);
           }
           t3s[e0] = acc0;
-          if (two) t3s[e1] = acc1;
         }
         __syncthreads();
         // stage 2a: fold the direction-2 test weights of this term into H2
-        for (int e = tid; e < T2 * NQ * W1; e += nth) {
-          const int q1l = e % W1, r = e / W1, t = r % NQ, il = r / NQ;
-          const int jl = i2a + il - j2a;
-          if (t >= nqj2[jl]) continue;
-          const int q2 = q0j2[jl] + t;
-          h2s[e] = fmaT<Real>(w2s[(k2 * A.T2M + il) * NQ + t], t3s[(q2 - qw2) * W1 + q1l], h2s[e]);
+        if (reg2) {
+          constexpr int NR = 2 * P + 1;  // |Q_i2| of regular rows; q2 - qw2 = 2 il + t
+          for (int e = tid; e < T2 * NR * W1; e += nth) {
+            const int q1l = e % W1, r = e / W1, t = r % NR, il = r / NR;
+            Real* hp = h2s + (il * NQ + t) * W1 + q1l;
+            *hp = fmaT<Real>(w2s[(k2 * A.T2M + il) * NQ + t], t3s[(2 * il + t) * W1 + q1l], *hp);
+          }
+        } else {
+          for (int e = tid; e < T2 * NQ * W1; e += nth) {
+            const int q1l = e % W1, r = e / W1, t = r % NQ, il = r / NQ;
+            const int jl = i2a + il - j2a;
+            if (t >= nqj2[jl]) continue;
+            const int q2 = q0j2[jl] + t;
+            h2s[e] = fmaT<Real>(w2s[(k2 * A.T2M + il) * NQ + t], t3s[(q2 - qw2) * W1 + q1l], h2s[e]);
+          }
         }
       }
       __syncthreads();
-      // stage 2b: contract q2 against the trial B-splines of direction 2. One item
-      // per (q1, i2, half of the band): the q2 loop runs outside, the j2 outputs of
-      // the half are independent accumulators.
-      {
-        constexpr int HB = P + 1;  // outputs per half: tt2 in [0, P] or [P+1, 2P]
-        for (int e = tid; e < T2 * 2 * W1; e += nth) {
-          const int q1l = e % W1, r = e / W1, half = r & 1, il = r >> 1;
-          const int i2 = i2a + il, il2 = i2 - j2a;
-          const int qi = q0j2[il2], ni = nqj2[il2];
-          int lo[HB], hi[HB], jl[HB];
-          Real acc[HB];
-#pragma unroll
-          for (int k = 0; k < HB; ++k) {
-            const int tt2 = half * (P + 1) + k;
-            const int j2 = i2 - P + tt2;
-            acc[k] = (Real)0;
-            if (tt2 < BW && j2 >= 0 && j2 < n2) {
-              const int jj = j2 - j2a;
-              jl[k] = jj;
-              lo[k] = max(qi, q0j2[jj]);
-              hi[k] = min(qi + ni, q0j2[jj] + nqj2[jj]);
-            } else {
-              jl[k] = 0;
-              lo[k] = 1 << 30;
-              hi[k] = -(1 << 30);
-            }
-          }
+      // stage 2b: contract q2 against the trial B-splines of direction 2.
+      if (reg2) {
+        // regular rows: t = q2 - q0(i2) in [0, 2P]; j2 = i2 - P + tt2 meets the row at
+        // t in [2 tt2 - 2P, 2 tt2] n [0, 2P], a pattern fixed at compile time. One item
+        // per (q1, i2) with the 2P+1 outputs j2 as independent accumulators.
+        for (int e = tid; e < T2 * W1; e += nth)
+          stage2b_regular<P, Real>(h2s, b2s, gs, q0j2, e / W1, e % W1, i2a, j2a, NQ, J2M, W1, T2, b2, grp);
+      } else {
+        for (int e = tid; e < T2 * BW * W1; e += nth) {
+          const int q1l = e % W1, r = e / W1, tt2 = r % BW, il = r / BW;
+          const int i2 = i2a + il, j2 = i2 - P + tt2;
+          if (j2 < 0 || j2 >= n2) continue;
+          const int il2 = i2 - j2a, jl2 = j2 - j2a;
+          const int qi = q0j2[il2], qj = q0j2[jl2];
+          const int lo = max(qi, qj), hi = min(qi + nqj2[il2], qj + nqj2[jl2]);
+          Real acc = (Real)0;
+          const Real* bb = b2s + (b2 * J2M + jl2) * NQ;
           const Real* hh = h2s + il * NQ * W1 + q1l;
-          const Real* bb = b2s + b2 * J2M * NQ;
-          for (int t = 0; t < ni; ++t) {
-            const int q = qi + t;
-            const Real hv = hh[t * W1];
-#pragma unroll
-            for (int k = 0; k < HB; ++k)
-              if (q >= lo[k] && q < hi[k]) acc[k] = fmaT<Real>(bb[jl[k] * NQ + q - q0j2[jl[k]]], hv, acc[k]);
-          }
-#pragma unroll
-          for (int k = 0; k < HB; ++k) {
-            const int tt2 = half * (P + 1) + k;
-            if (hi[k] > lo[k]) gs[((grp * T2 + il) * BW + tt2) * W1 + q1l] += acc[k];
-          }
+          for (int q = lo; q < hi; ++q) acc = fmaT<Real>(bb[q - qj], hh[(q - qi) * W1], acc);
+          gs[((grp * T2 + il) * BW + tt2) * W1 + q1l] += acc;
         }
       }
       __syncthreads();
     }
 
-    // stage 1: contract q1 and store. The q1 loop runs outside; the 2p+1 outputs
-    // of the row (one per j1) are independent accumulators.
+    // stage 1: contract q1 and store.
     const int jl3 = j3 - jlo3;
     for (int e = tid; e < T1 * T2 * BW; e += nth) {
       const int il1 = e % T1, r = e / T1, tt2 = r % BW, il2 = r / BW;
       const int i1 = i1a + il1, i2 = i2a + il2, j2 = i2 - P + tt2;
       if (j2 < 0 || j2 >= n2) continue;
-      const int qi1 = q0j1[i1 - j1a], ni1 = nqj1[i1 - j1a];
-      int lo[BW], hi[BW], qj[BW];
-      Real s[BW];
-#pragma unroll
-      for (int tt1 = 0; tt1 < BW; ++tt1) {
-        const int j1 = i1 - P + tt1;
-        s[tt1] = (Real)0;
-        if (j1 >= 0 && j1 < n1) {
-          qj[tt1] = q0j1[j1 - j1a];
-          lo[tt1] = max(qi1, qj[tt1]);
-          hi[tt1] = min(qi1 + ni1, qj[tt1] + nqj1[j1 - j1a]);
-        } else {
-          qj[tt1] = 0;
-          lo[tt1] = 1 << 30;
-          hi[tt1] = -(1 << 30);
-        }
-      }
-      const int gstride = T2 * BW * W1;
-      const Real* g0 = gs + (il2 * BW + tt2) * W1;   // group 0; group g at + g * gstride
-      const Real* wk = w1s + il1 * NQ;               // kind 0; kind k at + k * T1M * NQ
-      const int jrow0 = i1 - P - j1a;                // b1s row of tt1 = 0 (may be < 0)
-      for (int q = qi1; q < qi1 + ni1; ++q) {
-        const int gq = q - qw1, wq = q - qi1;
-        Real h0, h1 = (Real)0;
-        if (MASS) {
-          h0 = wk[wq] * g0[gq];
-        } else {
-          // groups g = 2a+b: h_b = w^{(0,b)} G_{(0,b)} + w^{(1,b)} G_{(1,b)}
-          h0 = fmaT<Real>(wk[wq], g0[gq], wk[wq + 2 * A.T1M * NQ] * g0[gq + 2 * gstride]);
-          h1 = fmaT<Real>(wk[wq + A.T1M * NQ], g0[gq + gstride], wk[wq + 3 * A.T1M * NQ] * g0[gq + 3 * gstride]);
-        }
-#pragma unroll
-        for (int tt1 = 0; tt1 < BW; ++tt1) {
-          if (q >= lo[tt1] && q < hi[tt1]) {
-            const int idx = (jrow0 + tt1) * NQ + q - qj[tt1];
-            if (MASS)
-              s[tt1] = fmaT<Real>(b1s[idx], h0, s[tt1]);
-            else
-              s[tt1] = fmaT<Real>(b1s[idx + J1M * NQ], h1, fmaT<Real>(b1s[idx], h0, s[tt1]));
-          }
-        }
-      }
       const int64_t row = P3i * N2 * N1 +
                           (int64_t)bw3 * (A.d[1].prefix[i2] * N1 + (int64_t)band_w(i2, P, n2) * A.d[0].prefix[i1]);
       const int bw1 = band_w(i1, P, n1), bw2 = band_w(i2, P, n2);
       const int jlo1 = band_lo(i1, P), jlo2 = band_lo(i2, P);
       const int64_t base = row + ((int64_t)jl3 * bw2 + (j2 - jlo2)) * bw1 - jlo1;
+      const int gstride = T2 * BW * W1;
+      const Real* g0 = gs + (il2 * BW + tt2) * W1;   // group 0; group g at + g * gstride
+      const Real* wk = w1s + il1 * NQ;               // kind 0; kind k at + k * T1M * NQ
+      const int qi1 = q0j1[i1 - j1a];
+      if (reg1) {
+        stage1_regular<P, MASS, Real, OutT>(g0, wk, b1s, q0j1, vals + base, i1, j1a, qi1 - qw1, qi1,
+                                            NQ, J1M, A.T1M, gstride);
+      } else {
+        const int ni1 = nqj1[i1 - j1a];
+        Real h0[MAXQ], h1[MAXQ];
+        for (int t = 0; t < ni1; ++t) {
+          const int gq = qi1 + t - qw1;
+          if (MASS) {
+            h0[t] = wk[t] * g0[gq];
+          } else {
+            h0[t] = fmaT<Real>(wk[t], g0[gq], wk[t + 2 * A.T1M * NQ] * g0[gq + 2 * gstride]);
+            h1[t] = fmaT<Real>(wk[t + A.T1M * NQ], g0[gq + gstride], wk[t + 3 * A.T1M * NQ] * g0[gq + 3 * gstride]);
+          }
+        }
 #pragma unroll
-      for (int tt1 = 0; tt1 < BW; ++tt1) {
-        const int j1 = i1 - P + tt1;
-        if (j1 >= 0 && j1 < n1) vals[base + j1] = (OutT)s[tt1];
+        for (int tt1 = 0; tt1 < BW; ++tt1) {
+          const int j1 = i1 - P + tt1;
+          if (j1 < 0 || j1 >= n1) continue;
+          const int qj = q0j1[j1 - j1a];
+          const int lo = max(qi1, qj), hi = min(qi1 + ni1, qj + nqj1[j1 - j1a]);
+          const Real* bb0 = b1s + (j1 - j1a) * NQ;
+          Real s = (Real)0;
+          if (MASS) {
+            for (int q = lo; q < hi; ++q) s = fmaT<Real>(bb0[q - qj], h0[q - qi1], s);
+          } else {
+            const Real* bb1 = bb0 + J1M * NQ;
+            for (int q = lo; q < hi; ++q)
+              s = fmaT<Real>(bb1[q - qj], h1[q - qi1], fmaT<Real>(bb0[q - qj], h0[q - qi1], s));
+          }
+          vals[base + j1] = (OutT)s;
+        }
       }
     }
+  }
+}
+
+
+template <int P, bool MASS, typename Real, typename OutT>
+__global__ void __launch_bounds__(256) k_assemble(AsmArgs A) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  int bid = blockIdx.x;
+  const int tile1 = bid % A.nt1;
+  bid /= A.nt1;
+  const int tile2 = bid % A.nt2;
+  const int i3 = bid / A.nt2;
+  assemble_tile<P, MASS, Real, OutT>(A, tile1, tile2, i3, smem_raw);
+}
+
+// ---------------------------------------------------------------------------
+// Batched assembly: many patches of different size and degree, stiffness and/or
+// mass, in one persistent launch. Work items (job, tile1, tile2, i3) are taken in
+// order from an atomic counter (the host sorts them longest first); no block
+// ever waits on another, so the loop ends when the list is exhausted.
+struct BatchJob {
+  AsmArgs A;
+  int p;
+  int mass;
+};
+
+struct BatchItem {
+  int job, tile1, tile2, i3;
+};
+
+template <bool MASS>
+__device__ __forceinline__ void batch_dispatch(const BatchJob& J, const BatchItem& it, unsigned char* smem) {
+  switch (J.p) {
+    case 2: assemble_tile<2, MASS, double, double>(J.A, it.tile1, it.tile2, it.i3, smem); break;
+    case 3: assemble_tile<3, MASS, double, double>(J.A, it.tile1, it.tile2, it.i3, smem); break;
+    case 4: assemble_tile<4, MASS, double, double>(J.A, it.tile1, it.tile2, it.i3, smem); break;
+    case 5: assemble_tile<5, MASS, double, double>(J.A, it.tile1, it.tile2, it.i3, smem); break;
+    case 6: assemble_tile<6, MASS, double, double>(J.A, it.tile1, it.tile2, it.i3, smem); break;
+    case 7: assemble_tile<7, MASS, double, double>(J.A, it.tile1, it.tile2, it.i3, smem); break;
+    case 8: assemble_tile<8, MASS, double, double>(J.A, it.tile1, it.tile2, it.i3, smem); break;
+  }
+}
+
+__global__ void __launch_bounds__(256) k_assemble_batch(const BatchJob* jobs, const BatchItem* items, int n_items,
+                                                        unsigned int* counter) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int next;
+  for (;;) {
+    if (threadIdx.x == 0) next = (int)atomicAdd(counter, 1u);
+    __syncthreads();
+    const int k = next;
+    __syncthreads();  // every thread has read `next` before thread 0 overwrites it
+    if (k >= n_items) break;
+    const BatchItem it = items[k];
+    const BatchJob& J = jobs[it.job];
+    if (J.mass)
+      batch_dispatch<true>(J, it, smem_raw);
+    else
+      batch_dispatch<false>(J, it, smem_raw);
+    __syncthreads();  // shared memory is reused by the next item
   }
 }
 
@@ -355,32 +501,38 @@ static void q_range_host(int i, int p, int n_el, int nqp, int* qs, int* qe) {
   *qe = hi == n_el ? nqp - 1 : 2 * hi + p - 2;
 }
 
-static int max_window(const wq_plan_s* pl, int l, int nt) {
+static void tile_extents(const wq_plan_s* pl, int l, int T, int* count, int* max_rows, int* max_win) {
   const int n = (int)pl->n[l], p = pl->p, ne = n - p, nqp = (int)pl->nqp[l];
-  int best = 0;
-  for (int t = 0; t < nt; ++t) {
-    int a = (int)((int64_t)t * n / nt), b = (int)((int64_t)(t + 1) * n / nt);
+  TileSplit ts{n, p, T};
+  *count = ts.count();
+  *max_rows = 0;
+  *max_win = 0;
+  for (int t = 0; t < *count; ++t) {
+    int a, b;
+    bool reg;
+    ts.tile(t, &a, &b, &reg);
     if (b <= a) continue;
     int qs0, qe0, qs1, qe1;
     q_range_host(a, p, ne, nqp, &qs0, &qe0);
     q_range_host(b - 1, p, ne, nqp, &qs1, &qe1);
-    best = std::max(best, qe1 - qs0 + 1);
+    *max_rows = std::max(*max_rows, b - a);
+    *max_win = std::max(*max_win, qe1 - qs0 + 1);
   }
-  return best;
 }
 
 struct TileChoice {
   int t1, t2;
 };
 
-static TileChoice tiles_for(int p) {
-  (void)p;
+static TileChoice tiles_for(const wq_plan_s* pl) {
+  if (pl->tile[0] > 0 && pl->tile[1] > 0) return TileChoice{pl->tile[0], pl->tile[1]};
   return TileChoice{16, 4};
 }
 
-template <int P, bool MASS, typename Real, typename OutT>
-static wq_status launch_t(wq_plan_s* pl, const double* kappa, void* vals, cudaStream_t s) {
-  AsmArgs A;
+// Kernel arguments, tile counts and shared-memory size of one matrix of one plan.
+template <int P, bool MASS, typename Real>
+static size_t make_args(wq_plan_s* pl, const double* kappa, void* vals, AsmArgs* out) {
+  AsmArgs& A = *out;
   for (int l = 0; l < 3; ++l) {
     A.d[l].n = pl->dir[l].n;
     A.d[l].q0 = pl->dir[l].q0;
@@ -396,16 +548,20 @@ static wq_status launch_t(wq_plan_s* pl, const double* kappa, void* vals, cudaSt
   A.nqp1 = (int)pl->nqp[0];
   A.nqp2 = (int)pl->nqp[1];
   A.vals = vals;
-  TileChoice tc = tiles_for(P);
-  const int n1 = (int)pl->n[0], n2 = (int)pl->n[1], n3 = (int)pl->n[2];
-  A.nt1 = (n1 + tc.t1 - 1) / tc.t1;
-  A.nt2 = (n2 + tc.t2 - 1) / tc.t2;
-  A.T1M = (n1 + A.nt1 - 1) / A.nt1;
-  A.T2M = (n2 + A.nt2 - 1) / A.nt2;
-  A.W1M = max_window(pl, 0, A.nt1);
-  A.W2M = max_window(pl, 1, A.nt2);
+  TileChoice tc = tiles_for(pl);
+  A.T1 = tc.t1;
+  A.T2 = tc.t2;
+  tile_extents(pl, 0, tc.t1, &A.nt1, &A.T1M, &A.W1M);
+  tile_extents(pl, 1, tc.t2, &A.nt2, &A.T2M, &A.W2M);
   SmemLayout L = smem_layout<P, MASS>(A.NQ, A.T1M, A.T2M, A.W1M, A.W2M);
-  size_t smem = sizeof(Real) * (size_t)L.total_real + sizeof(int) * (size_t)L.ints + 16;
+  return sizeof(Real) * (size_t)L.total_real + sizeof(int) * (size_t)L.ints + 16;
+}
+
+template <int P, bool MASS, typename Real, typename OutT>
+static wq_status launch_t(wq_plan_s* pl, const double* kappa, void* vals, cudaStream_t s) {
+  AsmArgs A;
+  size_t smem = make_args<P, MASS, Real>(pl, kappa, vals, &A);
+  const int n3 = (int)pl->n[2];
   if (smem > 227 * 1024) return set_error(WQ_ERR_UNSUPPORTED, "tile does not fit in shared memory");
   auto kern = k_assemble<P, MASS, Real, OutT>;
   WQ_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
@@ -461,6 +617,15 @@ static wq_status assemble(wq_plan_t plan, bool mass, const double* kappa, void* 
   return set_error(WQ_ERR_UNSUPPORTED, "unknown precision");
 }
 
+extern "C" wq_status wq_plan_set_tiles(wq_plan_t plan, int t1, int t2) {
+  if (!plan) return set_error(WQ_ERR_INVALID_ARG, "NULL plan");
+  if (t1 < 0 || t2 < 0 || t1 > 64 || t2 > 64 || (t1 == 0) != (t2 == 0))
+    return set_error(WQ_ERR_INVALID_ARG, "tile extents must both be 0 (default) or in 1..64");
+  plan->tile[0] = t1;
+  plan->tile[1] = t2;
+  return WQ_OK;
+}
+
 extern "C" wq_status wq_assemble_stiffness(wq_plan_t plan, const double* d_kappa, void* d_vals, int value_dtype,
                                            int precision, void* stream) {
   return assemble(plan, false, d_kappa, d_vals, value_dtype, precision, stream);
@@ -481,5 +646,163 @@ extern "C" wq_status wq_assemble_host(wq_plan_t plan, int which, const double* h
   if (st != WQ_OK) return st;
   WQ_CUDA_TRY(cudaMemcpyAsync(h_vals, d_vals, sizeof(double) * plan->nnz, cudaMemcpyDeviceToHost, s), "value copy");
   WQ_CUDA_TRY(cudaStreamSynchronize(s), "stream synchronize");
+  return WQ_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Batch host side.
+
+namespace wq {
+
+template <bool MASS>
+static size_t job_args(wq_plan_s* pl, void* vals, AsmArgs* A) {
+  switch (pl->p) {
+    case 2: return make_args<2, MASS, double>(pl, nullptr, vals, A);
+    case 3: return make_args<3, MASS, double>(pl, nullptr, vals, A);
+    case 4: return make_args<4, MASS, double>(pl, nullptr, vals, A);
+    case 5: return make_args<5, MASS, double>(pl, nullptr, vals, A);
+    case 6: return make_args<6, MASS, double>(pl, nullptr, vals, A);
+    case 7: return make_args<7, MASS, double>(pl, nullptr, vals, A);
+    default: return make_args<8, MASS, double>(pl, nullptr, vals, A);
+  }
+}
+
+}  // namespace wq
+
+struct wq_batch_s {
+  int device = 0;
+  wq::BatchJob* jobs = nullptr;
+  wq::BatchItem* items = nullptr;
+  unsigned int* counter = nullptr;
+  int n_items = 0;
+  int grid = 0;
+  size_t smem = 0;
+  int64_t nnz_total = 0;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+};
+
+static void free_batch(wq_batch_s* b) {
+  if (!b) return;
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  if (b->jobs) cudaFree(b->jobs);
+  if (b->items) cudaFree(b->items);
+  if (b->counter) cudaFree(b->counter);
+  delete b;
+}
+
+extern "C" wq_status wq_batch_create(wq_batch_t* out, int count, const wq_plan_t* plans, void* const* d_stiffness,
+                                     void* const* d_mass, void* stream) {
+  (void)stream;
+  if (!out || count <= 0 || !plans) return set_error(WQ_ERR_INVALID_ARG, "bad batch arguments");
+  *out = nullptr;
+  std::vector<wq::BatchJob> jobs;
+  std::vector<wq::BatchItem> items;
+  std::vector<double> cost;
+  size_t smem = 0;
+  int64_t nnz_total = 0;
+  for (int k = 0; k < count; ++k) {
+    wq_plan_s* pl = plans[k];
+    if (!pl) return set_error(WQ_ERR_INVALID_ARG, "NULL plan in batch");
+    for (int mass = 0; mass < 2; ++mass) {
+      void* vals = mass ? (d_mass ? d_mass[k] : nullptr) : (d_stiffness ? d_stiffness[k] : nullptr);
+      if (!vals) continue;
+      wq::BatchJob J;
+      J.p = pl->p;
+      J.mass = mass;
+      size_t need = mass ? wq::job_args<true>(pl, vals, &J.A) : wq::job_args<false>(pl, vals, &J.A);
+      if (need > 227 * 1024) return set_error(WQ_ERR_UNSUPPORTED, "a batch tile does not fit in shared memory");
+      smem = std::max(smem, need);
+      const int job = (int)jobs.size();
+      jobs.push_back(J);
+      nnz_total += pl->nnz;
+      // per-row work ~ nnz per row x multiply-adds per nonzero (stiffness ~ 3x mass)
+      const double b = 2.0 * pl->p + 1.0;
+      const double row_cost = b * b * b * (mass ? 1.0 : 3.0) * (4.0 + b);
+      wq::TileSplit t1{(int)pl->n[0], pl->p, J.A.T1}, t2{(int)pl->n[1], pl->p, J.A.T2};
+      for (int a = 0; a < J.A.nt1; ++a) {
+        int a0, a1;
+        bool r;
+        t1.tile(a, &a0, &a1, &r);
+        for (int c = 0; c < J.A.nt2; ++c) {
+          int c0, c1;
+          t2.tile(c, &c0, &c1, &r);
+          for (int i3 = 0; i3 < (int)pl->n[2]; ++i3) {
+            items.push_back(wq::BatchItem{job, a, c, i3});
+            cost.push_back(row_cost * (a1 - a0) * (c1 - c0));
+          }
+        }
+      }
+    }
+  }
+  if (jobs.empty()) return set_error(WQ_ERR_INVALID_ARG, "the batch has no output arrays");
+  // longest first
+  std::vector<int> order(items.size());
+  for (size_t i = 0; i < order.size(); ++i) order[i] = (int)i;
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return cost[x] > cost[y]; });
+  std::vector<wq::BatchItem> sorted(items.size());
+  for (size_t i = 0; i < order.size(); ++i) sorted[i] = items[order[i]];
+
+  wq_batch_s* b = new wq_batch_s();
+  cudaGetDevice(&b->device);
+  b->n_items = (int)sorted.size();
+  b->smem = smem;
+  b->nnz_total = nnz_total;
+  auto fail = [&](cudaError_t e, const char* what) {
+    free_batch(b);
+    return wq::cuda_error(e, what);
+  };
+  cudaError_t e = cudaMalloc(&b->jobs, sizeof(wq::BatchJob) * jobs.size());
+  if (e == cudaSuccess) e = cudaMalloc(&b->items, sizeof(wq::BatchItem) * sorted.size());
+  if (e == cudaSuccess) e = cudaMalloc(&b->counter, sizeof(unsigned int));
+  if (e != cudaSuccess) return fail(e, "batch allocation");
+  e = cudaMemcpy(b->jobs, jobs.data(), sizeof(wq::BatchJob) * jobs.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(b->items, sorted.data(), sizeof(wq::BatchItem) * sorted.size(), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return fail(e, "batch upload");
+  e = cudaFuncSetAttribute(wq::k_assemble_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return fail(e, "batch kernel attributes");
+  int per_sm = 0, sms = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, wq::k_assemble_batch, 256, smem);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device);
+  if (e != cudaSuccess) return fail(e, "batch occupancy");
+  b->grid = std::max(1, per_sm) * sms;
+  // one graph: reset the work counter, then the persistent kernel
+  cudaStream_t cs = nullptr;
+  e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+  if (e != cudaSuccess) return fail(e, "capture stream");
+  e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) e = cudaMemsetAsync(b->counter, 0, sizeof(unsigned int), cs);
+  if (e == cudaSuccess) {
+    wq::k_assemble_batch<<<b->grid, 256, smem, cs>>>(b->jobs, b->items, b->n_items, b->counter);
+    e = cudaGetLastError();
+  }
+  cudaError_t e2 = cudaStreamEndCapture(cs, &b->graph);
+  if (e == cudaSuccess) e = e2;
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, b->graph, 0);
+  cudaStreamDestroy(cs);
+  if (e != cudaSuccess) return fail(e, "batch graph capture");
+  *out = b;
+  return WQ_OK;
+}
+
+extern "C" wq_status wq_batch_launch(wq_batch_t batch, void* stream) {
+  if (!batch) return set_error(WQ_ERR_INVALID_ARG, "NULL batch");
+  WQ_CUDA_TRY(cudaGraphLaunch(batch->exec, (cudaStream_t)stream), "batch graph launch");
+  wq::count_launch();
+  return WQ_OK;
+}
+
+extern "C" wq_status wq_batch_info(wq_batch_t batch, int64_t* n_items, int64_t* nnz_total, int* grid) {
+  if (!batch) return set_error(WQ_ERR_INVALID_ARG, "NULL batch");
+  if (n_items) *n_items = batch->n_items;
+  if (nnz_total) *nnz_total = batch->nnz_total;
+  if (grid) *grid = batch->grid;
+  return WQ_OK;
+}
+
+extern "C" wq_status wq_batch_destroy(wq_batch_t batch) {
+  free_batch(batch);
   return WQ_OK;
 }

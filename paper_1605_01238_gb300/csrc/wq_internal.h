@@ -130,6 +130,7 @@ struct wq_plan_s {
   int32_t* col = nullptr;         // [nnz]
   wq::dd* gauss = nullptr;        // [2][p+1]: Gauss-Legendre nodes then weights on [-1, 1]
   int* err = nullptr;             // device error word
+  int tile[2] = {0, 0};           // assembly tile extents in directions 1, 2 (0 = default)
 };
 
 namespace wq {
