@@ -146,6 +146,28 @@ wq_status wq_plan_set_tiles(wq_plan_t plan, int t1, int t2);
 wq_status wq_assemble_host(wq_plan_t plan, int which, const double* h_ctrl, double* d_vals,
                            double* h_vals, void* stream);
 
+/* ---- adjoint ------------------------------------------------------------------
+ * J = lambda^T S u (which = 1), lambda^T M u (which = 2) or both (which = 3), for
+ * the plan's current geometry and the coefficient field kappa, and its gradients
+ * with respect to kappa and to the control points. Matrix-free: with the WQ
+ * entries of Eq. (stiff) / Eq. (Mass_approx) written out,
+ *   J = sum_q kappa(q) [ sum_{lm} c_lm(q) Lam_lm(q) U_m(q) + c(q) Lam_0(q) U_0(q) ],
+ * U_m the m-th parametric derivative of u_h = sum_j u_j B_j at the points and
+ * Lam_lm = sum_i lambda_i prod_k w^{(delta_kl, delta_km)}_{k,i_k,q_k}, both by sum
+ * factorisation; dJ/dkappa is pointwise and dJ/dC follows the chain rule through
+ * c_lm = det DF (DF^{-1} DF^{-T})_lm (Eq. (coef_stiff)) and
+ * DF = sum_i C_i x grad B_i. The paper has no adjoint; this is its derivative.
+ *   d_kappa       NULL (kappa = 1) or device double[N_QP]
+ *   d_lambda, d_u device double[N_DOF]
+ *   h_J           NULL or host double: J (the call then synchronises `stream`)
+ *   d_grad_kappa  NULL or device double[N_QP]
+ *   d_grad_ctrl   NULL or device double[N_DOF*3] (xyz interleaved)
+ * The first call allocates about (32 N_QP + 9 N_QP) doubles of plan-owned scratch;
+ * later calls allocate nothing. It recomputes the coefficients (wq_plan_set_geometry
+ * state) before the contractions. */
+wq_status wq_adjoint(wq_plan_t plan, int which, const double* d_kappa, const double* d_lambda,
+                     const double* d_u, double* h_J, double* d_grad_kappa, double* d_grad_ctrl, void* stream);
+
 /* ---- batched assembly --------------------------------------------------------
  * Many patches of different size and degree assembled by one persistent kernel
  * launch, captured once in a CUDA graph (a memset of the work counter and the

@@ -576,3 +576,70 @@ def cardinal_bspline(m: int, x) -> np.ndarray:
                 acc += (-1) ** k * math.comb(m + 1, k) * (xv - k) ** m
         out[idx] = float(acc / math.factorial(m))
     return out
+
+
+# ---------------------------------------------------------------------------
+# Adjoint of the bilinear forms (derivative of the WQ matrices; the paper has no
+# adjoint). J = lambda^T A u with A = S, M or S + M assembled with kappa at the
+# points; the gradients follow from writing the WQ entries out point by point.
+
+def adjoint_fields(orc: "Oracle3D", lam: np.ndarray, u: np.ndarray) -> tuple:
+    """U[m] (m = 0 value, 1..3 parametric derivatives of sum_j u_j B_j) and
+    Lam[t] (t = 3l + m: sum_i lambda_i prod_k w^{(delta_kl, delta_km)}_{k,i_k}; t = 9:
+    the (0,0) rules) at every point, arrays (nqp3, nqp2, nqp1), by einsum over the
+    dense univariate tables."""
+    n1, n2, n3 = orc.n
+    L3 = np.asarray(lam, dtype=np.float64).reshape(n3, n2, n1)
+    U3 = np.asarray(u, dtype=np.float64).reshape(n3, n2, n1)
+    d = orc.dirs
+    U = []
+    for m in range(4):
+        der = [int(k == m - 1) for k in range(3)]
+        U.append(np.einsum("kji,ia,jb,kc->cba", U3, d[0].B[der[0]], d[1].B[der[1]], d[2].B[der[2]], optimize=True))
+    Lam = []
+    for t in range(10):
+        if t < 9:
+            l, m = divmod(t, 3)
+            kinds = [(int(k == l), int(k == m)) for k in range(3)]
+        else:
+            kinds = [(0, 0)] * 3
+        W = [d[k].W[kinds[k][0], kinds[k][1]] for k in range(3)]     # (n, nqp)
+        Lam.append(np.einsum("kji,ia,jb,kc->cba", L3, W[0], W[1], W[2], optimize=True))
+    return U, Lam
+
+
+def adjoint(orc: "Oracle3D", lam, u, which: str = "stiffness", kappa=None) -> tuple:
+    """(J, dJ/dkappa (nqp3, nqp2, nqp1), dJ/dC (N_DOF, 3)) for the oracle's geometry.
+    orc.coef must hold the coefficients without kappa (kappa is passed here)."""
+    U, Lam = adjoint_fields(orc, lam, u)
+    kap = np.ones(orc.coef.shape[1:]) if kappa is None else np.asarray(kappa, dtype=np.float64).reshape(orc.coef.shape[1:])
+    gk = np.zeros(orc.coef.shape[1:])
+    Kb = np.zeros(orc.coef.shape[1:] + (3, 3))
+    cb = np.zeros(orc.coef.shape[1:])
+    if which in ("stiffness", "both"):
+        for l in range(3):
+            for m in range(3):
+                lu = Lam[3 * l + m] * U[m + 1]
+                gk += orc.coef[coef_index(l, m)] * lu
+                Kb[..., l, m] = kap * lu
+    if which in ("mass", "both"):
+        lu = Lam[9] * U[0]
+        gk += orc.coef[6] * lu
+        cb = kap * lu
+    J = float(np.sum(kap * gk))
+    G = jacobians(orc.dirs, orc.ctrl)
+    det = np.linalg.det(G)
+    Gi = np.linalg.inv(G)
+    GiT = np.swapaxes(Gi, -1, -2)
+    P = Gi @ GiT
+    KP = np.einsum("...ij,...ij->...", Kb, P)
+    Ks = Kb + np.swapaxes(Kb, -1, -2)
+    Gbar = det[..., None, None] * ((KP + cb)[..., None, None] * GiT - GiT @ Ks @ P)
+    n1, n2, n3 = orc.n
+    d = orc.dirs
+    gc = np.zeros((n3, n2, n1, 3))
+    for c in range(3):
+        der = [int(k == c) for k in range(3)]
+        gc += np.einsum("cbar,ia,jb,kc->kjir", Gbar[..., :, c], d[0].B[der[0]], d[1].B[der[1]], d[2].B[der[2]],
+                        optimize=True)
+    return J, gk, gc.reshape(-1, 3)

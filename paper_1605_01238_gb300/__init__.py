@@ -15,7 +15,7 @@ import numpy as np
 
 from ._lib import WqError, check, load
 
-__all__ = ["Plan", "Batch", "WqError", "launch_count", "load", "VALUES_F64", "VALUES_F32", "PREC_FP64", "PREC_FP32"]
+__all__ = ["Plan", "Batch", "bilinear", "WqError", "launch_count", "load", "VALUES_F64", "VALUES_F32", "PREC_FP64", "PREC_FP32"]
 
 VALUES_F64, VALUES_F32 = 0, 1
 PREC_FP64, PREC_FP32 = 0, 1
@@ -197,6 +197,24 @@ class Plan:
         check(load().wq_assemble_host(self._h, 1 if which == "mass" else 0, ctypes.c_void_p(cp),
                                       ctypes.c_void_p(vp), ctypes.c_void_p(hp), _stream(stream)))
 
+    def adjoint(self, lam, u, kappa=None, which: str = "stiffness", grad_kappa: bool = True,
+                grad_ctrl: bool = True, stream=None):
+        """(J, dJ/dkappa or None, dJ/dC or None) for J = lam^T A u, A = S, M or S+M
+        (which = "stiffness", "mass", "both"); wq_adjoint."""
+        torch = _torch()
+        w = {"stiffness": 1, "mass": 2, "both": 3}[which]
+        lp = _dev_ptr(lam, torch.float64, self.n_rows, "lam")
+        up = _dev_ptr(u, torch.float64, self.n_rows, "u")
+        nqp = int(np.prod(self.n_qp))
+        kp = None if kappa is None else _dev_ptr(kappa, torch.float64, nqp, "kappa")
+        gk = torch.empty(nqp, dtype=torch.float64, device="cuda") if grad_kappa else None
+        gc = torch.empty(self.n_rows * 3, dtype=torch.float64, device="cuda") if grad_ctrl else None
+        J = ctypes.c_double()
+        check(load().wq_adjoint(self._h, w, ctypes.c_void_p(kp), ctypes.c_void_p(lp), ctypes.c_void_p(up),
+                                ctypes.byref(J), ctypes.c_void_p(None if gk is None else gk.data_ptr()),
+                                ctypes.c_void_p(None if gc is None else gc.data_ptr()), _stream(stream)))
+        return J.value, gk, (None if gc is None else gc.view(self.n_rows, 3))
+
     def sync_check(self, stream=None) -> None:
         check(load().wq_sync_check(self._h, _stream(stream)))
 
@@ -269,3 +287,42 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+def _bilinear_function():
+    torch = _torch()
+
+    class _Bilinear(torch.autograd.Function):
+        """J = lam^T A(ctrl, kappa) u with the hand-written adjoint as backward."""
+
+        @staticmethod
+        def forward(ctx, ctrl, kappa, plan, lam, u, which):
+            plan.set_geometry(ctrl.detach().reshape(-1).contiguous())
+            want_k = kappa is not None and ctx.needs_input_grad[1]
+            J, gk, gc = plan.adjoint(lam, u, None if kappa is None else kappa.detach().contiguous(), which,
+                                     grad_kappa=want_k, grad_ctrl=ctx.needs_input_grad[0])
+            ctx.save_for_backward(gc if gc is not None else torch.empty(0), gk if gk is not None else torch.empty(0))
+            ctx.has = (gc is not None, gk is not None)
+            return torch.tensor(J, dtype=torch.float64, device=ctrl.device)
+
+        @staticmethod
+        def backward(ctx, grad_out):
+            gc, gk = ctx.saved_tensors
+            g_ctrl = grad_out * gc if ctx.has[0] else None
+            g_kappa = grad_out * gk if ctx.has[1] else None
+            return g_ctrl, g_kappa, None, None, None, None
+
+    return _Bilinear
+
+
+_BILINEAR = None
+
+
+def bilinear(plan, ctrl, lam, u, kappa=None, which: str = "stiffness"):
+    """Differentiable J = lam^T A u for the plan's mesh with control points `ctrl`
+    ((N_DOF, 3) CUDA float64) and coefficient field `kappa` (CUDA float64 over the
+    points, or None); gradients flow to ctrl and kappa through wq_adjoint."""
+    global _BILINEAR
+    if _BILINEAR is None:
+        _BILINEAR = _bilinear_function()
+    return _BILINEAR.apply(ctrl, kappa, plan, lam, u, which)

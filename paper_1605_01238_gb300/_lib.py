@@ -34,6 +34,7 @@ SIGNATURES = {
     "wq_get_points": (c_int, [c_vp, c_int, c_vp]),
     "wq_get_rules": (c_int, [c_vp, c_int, c_int, c_int, c_vp, c_vp, c_vp]),
     "wq_get_coefficients": (c_int, [c_vp, c_vp]),
+    "wq_adjoint": (c_int, [c_vp, c_int, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp]),
     "wq_batch_create": (c_int, [ctypes.POINTER(c_vp), c_int, c_vp, c_vp, c_vp, c_vp]),
     "wq_batch_launch": (c_int, [c_vp, c_vp]),
     "wq_batch_info": (c_int, [c_vp, ctypes.POINTER(c_i64), ctypes.POINTER(c_i64), ctypes.POINTER(c_int)]),

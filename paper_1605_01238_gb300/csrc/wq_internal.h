@@ -131,6 +131,8 @@ struct wq_plan_s {
   wq::dd* gauss = nullptr;        // [2][p+1]: Gauss-Legendre nodes then weights on [-1, 1]
   int* err = nullptr;             // device error word
   int tile[2] = {0, 0};           // assembly tile extents in directions 1, 2 (0 = default)
+  double* jac = nullptr;          // [9][N_QP] DF at the points (allocated by the first wq_adjoint)
+  double* adj_scratch = nullptr;  // adjoint fields (allocated by the first wq_adjoint)
 };
 
 namespace wq {
@@ -142,7 +144,7 @@ void count_launch(int k = 1);
 
 // Plan-building steps (wq_plan.cu).
 wq_status run_setup(wq_plan_s* pl, cudaStream_t s, bool with_pattern);
-wq_status run_coefficients(wq_plan_s* pl, cudaStream_t s);
+wq_status run_coefficients(wq_plan_s* pl, cudaStream_t s, double* jac = nullptr);
 
 // Assembly launches (wq_assemble.cu).
 wq_status launch_assemble_f64(wq_plan_s* pl, bool mass, const double* kappa, double* vals,

@@ -512,6 +512,7 @@ struct CoefArgs {
   const double *bp1, *bp2, *bp3;
   const int *f1, *f2, *f3;
   double* coef;
+  double* jac;  // NULL, or [9][N_QP]: DF_{rc} at (3r + c)
   int64_t nqp_total;
   int* err;
 };
@@ -574,6 +575,10 @@ __global__ void k_coef(CoefArgs a) {
         F[rr][c] = acc + (rr == c ? 1.0 : 0.0);  // dF_r / dzeta_c
       }
     }
+    const int64_t qg = ((int64_t)q3 * a.nq2 + q2) * a.nq1 + q1;
+    if (a.jac)
+      for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < 3; ++c) a.jac[(3 * r + c) * a.nqp_total + qg] = F[r][c];
     // adj = det * DF^{-1}: adj[l][k] = cofactor[k][l]
     double adj[3][3];
     adj[0][0] = F[1][1] * F[2][2] - F[1][2] * F[2][1];
@@ -588,7 +593,6 @@ __global__ void k_coef(CoefArgs a) {
     double det = F[0][0] * adj[0][0] + F[0][1] * adj[1][0] + F[0][2] * adj[2][0];
     if (!(det > 0.0) || !isfinite(det)) atomicOr(a.err, kErrBadGeometry);
     double inv = 1.0 / det;
-    const int64_t qg = ((int64_t)q3 * a.nq2 + q2) * a.nq1 + q1;
     const int L[6] = {0, 0, 0, 1, 1, 2}, Mi[6] = {0, 1, 2, 1, 2, 2};
     for (int s = 0; s < 6; ++s) {
       int l = L[s], mm = Mi[s];
@@ -604,7 +608,7 @@ static size_t coef_smem(int p) {
   return sizeof(double) * (size_t)(2 * W2 * W1 * 3 + 3 * kCoefTQ2 * W1 * 3);
 }
 
-wq_status run_coefficients(wq_plan_s* pl, cudaStream_t s) {
+wq_status run_coefficients(wq_plan_s* pl, cudaStream_t s, double* jac) {
   DeltaArgs da;
   da.n1 = (int)pl->n[0];
   da.n2 = (int)pl->n[1];
@@ -632,6 +636,7 @@ wq_status run_coefficients(wq_plan_s* pl, cudaStream_t s) {
   a.f2 = pl->dir[1].first;
   a.f3 = pl->dir[2].first;
   a.coef = pl->coef;
+  a.jac = jac;
   a.nqp_total = pl->n_qp_total;
   a.err = pl->err;
   int64_t blocks = (int64_t)((a.nq1 + kCoefTQ1 - 1) / kCoefTQ1) * ((a.nq2 + kCoefTQ2 - 1) / kCoefTQ2) * a.nq3;
@@ -734,7 +739,8 @@ static void free_plan(wq_plan_s* pl) {
     for (void* q : ptrs)
       if (q) cudaFree(q);
   }
-  void* ptrs[] = {pl->ctrl, pl->ctrl_delta, pl->coef, pl->row_ptr, pl->col, pl->gauss, pl->err};
+  void* ptrs[] = {pl->ctrl, pl->ctrl_delta, pl->coef, pl->row_ptr, pl->col, pl->gauss, pl->err, pl->jac,
+                  pl->adj_scratch};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   delete pl;
