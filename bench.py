@@ -47,21 +47,45 @@ def fp64_peak_tflops(sm_max_mhz: float) -> float:
     return 152 * 2 * 2 * sm_max_mhz * 1e6 / 1e12
 
 
-def stiffness_flops_per_nnz(p: int) -> float:
-    """FLOPs per nonzero of the halo-free sum factorisation the kernel implements
-    (each multiply or fused multiply-add counted as 2 flops), interior rows."""
-    b = 2 * p + 1
-    o = 2 * p * p + 2 * p + 1            # sum over j of |Q_i n Q_j| (structural zeros skipped)
-    stage1 = (4 * b + 2 * o) / b
-    stage2 = 2 * (9 * b + 6 * o) / b ** 2
-    stage3 = 4 * 9 * o / b ** 3
-    return 2 * (stage1 + stage2 + stage3)
+def _dir_census(n: int, p: int):
+    """Per direction: number of points, |Q_i|, sum_j |Q_i n Q_j| and band widths (Section 3
+    sets, with the point grid of the Remark on the choice of points)."""
+    ne = n - p
+    nqp = 2 * ne + 2 * p - 1
+
+    def qr(i):
+        lo, hi = max(0, i - p), min(ne, i + 1)
+        qs = 0 if lo == 0 else 2 * lo + p
+        qe = nqp - 1 if hi == ne else 2 * hi + p - 2
+        return qs, qe + 1
+    Q = [qr(i) for i in range(n)]
+    nq = [b - a for a, b in Q]
+    ov = [sum(max(0, min(Q[i][1], Q[j][1]) - max(Q[i][0], Q[j][0]))
+              for j in range(max(0, i - p), min(n, i + p + 1))) for i in range(n)]
+    bw = [min(n - 1, i + p) - max(0, i - p) + 1 for i in range(n)]
+    return nqp, nq, ov, bw
 
 
-def mass_flops_per_nnz(p: int) -> float:
-    b = 2 * p + 1
-    o = 2 * p * p + 2 * p + 1
-    return 2 * ((b + o) / b + 2 * (b + o) / b ** 2 + 4 * o / b ** 3)
+def algorithmic_flops(n: tuple, p: int, mass: bool = False) -> float:
+    """FP64 flops of one assembly by the sum factorisation of Eq. (sumfactorization)
+    with test weights folded in and structural zeros skipped, every intermediate
+    computed once (each multiply or multiply-add counted as 2 flops), for this mesh
+    (boundary rows included):
+      stage 3: 9 sum_{i3} sum_{j3} |Q_i3 n Q_j3|                per (q1, q2)
+      stage 2: 9 |Q_i2| + 6 sum_{j2} |Q_i2 n Q_j2|              per (q1, i2, i3, j3)
+      stage 1: 4 |Q_i1| + 2 sum_{j1} |Q_i1 n Q_j1|              per (i1, i2, j2, i3, j3)
+    (mass: one term, one class, one group)."""
+    d1, d2, d3 = (_dir_census(nl, p) for nl in n)
+    nnz1 = [sum(d[3]) for d in (d1, d2, d3)]
+    if mass:
+        s3 = d1[0] * d2[0] * sum(d3[2])
+        s2 = d1[0] * nnz1[2] * sum(a + b for a, b in zip(d2[1], d2[2]))
+        s1 = nnz1[1] * nnz1[2] * sum(a + b for a, b in zip(d1[1], d1[2]))
+    else:
+        s3 = d1[0] * d2[0] * 9 * sum(d3[2])
+        s2 = d1[0] * nnz1[2] * sum(9 * a + 6 * b for a, b in zip(d2[1], d2[2]))
+        s1 = nnz1[1] * nnz1[2] * sum(4 * a + 2 * b for a, b in zip(d1[1], d1[2]))
+    return 2.0 * (s1 + s2 + s3)
 
 
 class ClockSampler:
@@ -250,6 +274,7 @@ def run_ours(args):
         perturbed_cube(args.p, args.nel, seed=1605 + 1)
     p = patch.p
     plan = wq.Plan(p, patch.knots, patch.ctrl)
+    plan.set_algorithm(args.algo)
     nnz, N = plan.nnz, plan.n_rows
     ctrl_d = torch.as_tensor(patch.ctrl.reshape(-1), device="cuda")
     vals = torch.empty(nnz, dtype=torch.float64, device="cuda")
@@ -294,7 +319,7 @@ def run_ours(args):
     if args.steps_only:
         if rank == 0:
             print(json.dumps({"metric": METRIC, "value": value, "unit": "nnz/s", "ms_per_step": ms_step,
-                              "assembly_ms": kernel_ms, "p": p, "n_el": args.nel, "nnz": nnz,
+                              "assembly_ms": kernel_ms, "p": p, "n_el": args.nel, "nnz": nnz, "algo": args.algo,
                               "gpu_launches": int(launches)}), flush=True)
         plan.close()
         if dist is not None:
@@ -317,6 +342,11 @@ def run_ours(args):
     vals32 = torch.empty(nnz, dtype=torch.float32, device="cuda")
     f32_ms = timed(lambda: plan.stiffness(out=vals32, dtype=torch.float32, precision="fp32"))
     f32_f64_ms = timed(lambda: plan.stiffness(out=vals, precision="fp32"))
+    plan.set_algorithm("staged")
+    f32s_ms = timed(lambda: plan.stiffness(out=vals32, dtype=torch.float32, precision="fp32"))
+    plan.set_algorithm("fused")
+    f64f_ms = timed(lambda: plan.stiffness(out=vals))
+    plan.set_algorithm(args.algo)
     refresh_ms = timed(lambda: plan.refresh(ctrl_d))
     del vals32
     batch_line = run_batch_variant(wq, torch, stream) if args.batch else None
@@ -334,9 +364,10 @@ def run_ours(args):
     e2e_s = max_over_ranks(dist, e2e_s)
 
     pk, pk_kind = peaks()
-    fpn = stiffness_flops_per_nnz(p)
+    flops = algorithmic_flops(plan.n, p)
+    fpn = flops / nnz
     peak_tf = fp64_peak_tflops(pk.get("sm_max_mhz", 2070.0))
-    achieved_tf = fpn * nnz / (kernel_ms * 1e-3) / 1e12
+    achieved_tf = flops / (kernel_ms * 1e-3) / 1e12
     hbm = pk["hbm_gbs"]
     write_gbs = 8.0 * nnz / (ms_step * 1e-3) / 1e9
     line = {
@@ -352,18 +383,23 @@ def run_ours(args):
                    "parallelism": f"{world} independent patches, one per GPU"},
         "roofline": {"bound": "alu", "achieved": achieved_tf, "peak": peak_tf, "unit": "TFLOP/s",
                      "frac": achieved_tf / peak_tf, "traffic": None,
-                     "kernel": f"k_assemble<{p},stiffness,fp64>",
-                     "note": f"FP64 FMA pipe: {fpn:.1f} algorithmic flop/nnz; peak = 152 SMs x 2 DFMA/clk "
+                     "kernel": f"k_assemble<{p},stiffness,fp64> ({args.algo})",
+                     "flops_per_launch": flops,
+                     "note": f"FP64 FMA pipe: {fpn:.1f} algorithmic flop/nnz (exact census of the factorisation "
+                             f"for this mesh); peak = 152 SMs x 2 DFMA/clk "
                              f"x {pk.get('sm_max_mhz', 2070.0):.0f} MHz (derived; a DFMA probe measured "
                              "1.20 TFLOP/s)"},
         "hbm_write": {"achieved_gbs": write_gbs, "peak_gbs": hbm, "frac": write_gbs / hbm,
                       "peak_kind": f"{pk_kind} copy bandwidth"},
         "breakdown_ms": {"assembly": kernel_ms, "refresh": refresh_ms, "mass_fp64": mass_ms,
-                         "stiffness_fp32_f32vals": f32_ms, "stiffness_fp32_f64vals": f32_f64_ms},
+                         "stiffness_fp32_f32vals": f32_ms, "stiffness_fp32_f64vals": f32_f64_ms,
+                         "stiffness_fp32_f32vals_staged": f32s_ms, "stiffness_fp64_fused": f64f_ms},
         "variants_nnz_per_s": {"stiffness_fp64_assembly_only": nnz / (kernel_ms * 1e-3),
                                "mass_fp64_assembly_only": nnz / (mass_ms * 1e-3),
                                "stiffness_fp32_f32vals": nnz / (f32_ms * 1e-3),
-                               "stiffness_fp32_f64vals": nnz / (f32_f64_ms * 1e-3)},
+                               "stiffness_fp32_f64vals": nnz / (f32_f64_ms * 1e-3),
+                               "stiffness_fp32_f32vals_staged": nnz / (f32s_ms * 1e-3),
+                               "stiffness_fp64_fused_assembly_only": nnz / (f64f_ms * 1e-3)},
         "batch": batch_line,
         "e2e": {"value": world * nnz / e2e_s, "unit": "nnz/s", "h2d_bytes_per_step": 8 * 3 * N,
                 "d2h_bytes_per_step": 8 * nnz,
@@ -397,6 +433,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--p", type=int, default=4, help="degree (default: the p=4 workload)")
     ap.add_argument("--nel", type=int, default=64, help="elements per direction (default 64)")
+    ap.add_argument("--algo", default="auto", choices=["auto", "fused", "staged"],
+                    help="assembly algorithm: one fused kernel, or three staged kernels")
     ap.add_argument("--no-batch", dest="batch", action="store_false",
                     help="skip the 64-patch batched launch variant")
     ap.add_argument("--steps-only", action="store_true",

@@ -130,6 +130,20 @@ wq_status wq_assemble_stiffness(wq_plan_t plan, const double* d_kappa, void* d_v
 wq_status wq_assemble_mass(wq_plan_t plan, const double* d_kappa, void* d_vals,
                            int value_dtype, int precision, void* stream);
 
+/* Assembly algorithm of a plan.
+ *   WQ_ALGO_FUSED  one kernel: each block runs the three mode products of
+ *                  Eq. (sumfactorization) for a tile of rows in shared memory
+ *                  (intermediates of neighbouring tiles overlap and are recomputed)
+ *   WQ_ALGO_STAGED three kernels, one per mode product, over the whole mesh; every
+ *                  intermediate is computed once and kept in device memory. The
+ *                  first staged call allocates plan-owned scratch of
+ *                  nnz1_3 * (9 nqp1 nqp2 + 4 nqp1 nnz1_2) values (nnz1_l = band
+ *                  pairs of direction l; 2.3 GB in FP64 at p = 4, 64^3).
+ *   WQ_ALGO_AUTO   (default) staged
+ * All give the same values up to rounding order. */
+enum { WQ_ALGO_FUSED = 0, WQ_ALGO_STAGED = 1, WQ_ALGO_AUTO = 2 };
+wq_status wq_plan_set_algorithm(wq_plan_t plan, int algorithm);
+
 /* Tile extents of the assembly kernels: each block assembles at most t1 x t2
  * rows in directions 1 x 2 for one i3 (the three mode products of
  * Eq. (sumfactorization) share their intermediates inside a tile). t1 = t2 = 0

@@ -147,6 +147,11 @@ class Plan:
                 ptr, on_dev = arr.ctypes.data, 0
         check(load().wq_plan_refresh(self._h, ctypes.c_void_p(ptr), on_dev, _stream(stream)))
 
+    def set_algorithm(self, algorithm: str) -> None:
+        """"fused" (one kernel, tiles in shared memory), "staged" (three kernels,
+        intermediates in device memory) or "auto" (the default: staged)."""
+        check(load().wq_plan_set_algorithm(self._h, {"fused": 0, "staged": 1, "auto": 2}[algorithm]))
+
     def set_tiles(self, t1: int = 0, t2: int = 0) -> None:
         """Assembly tile extents in directions 1 and 2 (0, 0 = defaults)."""
         check(load().wq_plan_set_tiles(self._h, int(t1), int(t2)))

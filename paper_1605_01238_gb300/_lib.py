@@ -39,6 +39,7 @@ SIGNATURES = {
     "wq_batch_launch": (c_int, [c_vp, c_vp]),
     "wq_batch_info": (c_int, [c_vp, ctypes.POINTER(c_i64), ctypes.POINTER(c_i64), ctypes.POINTER(c_int)]),
     "wq_batch_destroy": (c_int, [c_vp]),
+    "wq_plan_set_algorithm": (c_int, [c_vp, c_int]),
     "wq_plan_set_tiles": (c_int, [c_vp, c_int, c_int]),
     "wq_rules_noalloc": (c_int, [c_int, c_i64, c_vp, c_vp, c_vp, c_vp, c_int, c_vp]),
 }

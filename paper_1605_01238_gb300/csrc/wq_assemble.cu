@@ -609,10 +609,13 @@ static wq_status assemble(wq_plan_t plan, bool mass, const double* kappa, void* 
   if (value_dtype != WQ_VALUES_F64 && value_dtype != WQ_VALUES_F32)
     return set_error(WQ_ERR_INVALID_ARG, "unknown value dtype");
   cudaStream_t s = (cudaStream_t)stream;
-  if (precision == WQ_PREC_FP64) {
-    if (value_dtype != WQ_VALUES_F64) return set_error(WQ_ERR_INVALID_ARG, "FP64 contractions write FP64 values");
-    return wq::launch_assemble_f64(plan, mass, kappa, (double*)vals, s);
-  }
+  if (precision == WQ_PREC_FP64 && value_dtype != WQ_VALUES_F64)
+    return set_error(WQ_ERR_INVALID_ARG, "FP64 contractions write FP64 values");
+  const bool staged = plan->algorithm == WQ_ALGO_STAGED ||
+                      plan->algorithm == WQ_ALGO_AUTO;
+  if ((precision == WQ_PREC_FP64 || precision == WQ_PREC_FP32) && staged)
+    return wq::launch_staged(plan, mass, kappa, vals, value_dtype, precision, s);
+  if (precision == WQ_PREC_FP64) return wq::launch_assemble_f64(plan, mass, kappa, (double*)vals, s);
   if (precision == WQ_PREC_FP32) return wq::launch_assemble_f32(plan, mass, kappa, vals, value_dtype, s);
   return set_error(WQ_ERR_UNSUPPORTED, "unknown precision");
 }
@@ -623,6 +626,14 @@ extern "C" wq_status wq_plan_set_tiles(wq_plan_t plan, int t1, int t2) {
     return set_error(WQ_ERR_INVALID_ARG, "tile extents must both be 0 (default) or in 1..64");
   plan->tile[0] = t1;
   plan->tile[1] = t2;
+  return WQ_OK;
+}
+
+extern "C" wq_status wq_plan_set_algorithm(wq_plan_t plan, int algorithm) {
+  if (!plan) return set_error(WQ_ERR_INVALID_ARG, "NULL plan");
+  if (algorithm != WQ_ALGO_FUSED && algorithm != WQ_ALGO_STAGED && algorithm != WQ_ALGO_AUTO)
+    return set_error(WQ_ERR_INVALID_ARG, "unknown algorithm");
+  plan->algorithm = algorithm;
   return WQ_OK;
 }
 

@@ -110,6 +110,8 @@ struct DirData {
   double* w = nullptr;       // [4][n][NQ] rules w^{(a,b)}_{i, q0(i)+t}
   int64_t* prefix = nullptr; // [n+1] prefix sums of the band widths |I_i|
   dd* greville = nullptr;    // [n] Greville abscissae (xi_{i+1} + ... + xi_{i+p}) / p
+  int* pair_row = nullptr;   // [nnz1] row i of each band pair (staged assembly)
+  float* tab32 = nullptr;    // [6][n][NQ] float copies of w and bt (staged FP32 assembly)
 };
 
 }  // namespace wq
@@ -133,6 +135,11 @@ struct wq_plan_s {
   int tile[2] = {0, 0};           // assembly tile extents in directions 1, 2 (0 = default)
   double* jac = nullptr;          // [9][N_QP] DF at the points (allocated by the first wq_adjoint)
   double* adj_scratch = nullptr;  // adjoint fields (allocated by the first wq_adjoint)
+  int algorithm = WQ_ALGO_AUTO;   // WQ_ALGO_*
+  double* coefT = nullptr;        // staged: [8][N_QP] transposed coefficients (+ kappa)
+  void* stg_a = nullptr;          // staged: T3
+  void* stg_b = nullptr;          // staged: G
+  size_t stg_a_bytes = 0, stg_b_bytes = 0;
 };
 
 namespace wq {
@@ -151,6 +158,9 @@ wq_status launch_assemble_f64(wq_plan_s* pl, bool mass, const double* kappa, dou
                               cudaStream_t s);
 wq_status launch_assemble_f32(wq_plan_s* pl, bool mass, const double* kappa, void* vals,
                               int value_dtype, cudaStream_t s);
+// Staged assembly (wq_staged.cu).
+wq_status launch_staged(wq_plan_s* pl, bool mass, const double* kappa, void* vals, int value_dtype, int precision,
+                        cudaStream_t s);
 
 }  // namespace wq
 

@@ -735,12 +735,12 @@ static void free_plan(wq_plan_s* pl) {
   for (int l = 0; l < 3; ++l) {
     wq::DirData& d = pl->dir[l];
     void* ptrs[] = {d.knots, d.x, d.x_dd, d.first, d.q0, d.nq, d.bt_dd, d.bt, d.bp, d.gb, d.integ, d.w, d.prefix,
-                    d.greville};
+                    d.greville, d.pair_row, d.tab32};
     for (void* q : ptrs)
       if (q) cudaFree(q);
   }
   void* ptrs[] = {pl->ctrl, pl->ctrl_delta, pl->coef, pl->row_ptr, pl->col, pl->gauss, pl->err, pl->jac,
-                  pl->adj_scratch};
+                  pl->adj_scratch, pl->coefT, pl->stg_a, pl->stg_b};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   delete pl;

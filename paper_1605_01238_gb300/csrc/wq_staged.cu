@@ -1,0 +1,485 @@
+// Staged WQ assembly: the three mode products of Eq. (sumfactorization) as three
+// kernels over the whole mesh, with their intermediates in device memory.
+//
+//   K3  T3[p3][term][q1][q2] = sum_{q3 in Q_i3 n Q_j3} w3^{k3}(i3,q3) B3^{b3}(j3,q3) c_term(q1,q2,q3)
+//   K2  G[p3][g][q1][p2]     = sum_{classes of g} sum_{q2 in Q_i2 n Q_j2} B2^{b2}(j2,q2)
+//                               sum_{terms of the class} w2^{k2}(i2,q2) T3[p3][term][q1][q2]
+//   K1  s(i, j)              = sum_b sum_{q1 in Q_i1 n Q_j1} B1^{b}(j1,q1) sum_a w1^{(a,b)}(i1,q1) G[p3][(a,b)][q1][p2]
+//
+// with p3 = (i3, j3) and p2 = (i2, j2) running over the 1D band pairs |i - j| <= p
+// (prefix sums of the band widths index them). Every output of every stage is
+// computed exactly once, so the FP64 work is the halo-free count of the
+// factorisation; the price is writing and reading T3 and G once (a few GB at
+// p = 4, 64^3), cheap against the FP64 rate. Each stage has a path for regular
+// rows (p+1 <= i <= n-p-2: Q_i = [2i-p, 2i+p], the (point, output) pattern known
+// at compile time) and a general path for the rows next to the boundary.
+//
+// Layouts keep every access coalesced: K3 reads a transposed coefficient copy
+// cT[slot][q3][q1][q2] and writes T3 with q2 fastest (threads run over q2); K2
+// runs over i2 and writes G with the pair index p2 fastest; K1 runs over p2, so
+// neighbouring threads write neighbouring j2 blocks of the same CSR row.
+#include <algorithm>
+#include <vector>
+
+#include "wq_internal.h"
+
+namespace wq {
+
+namespace {
+
+__constant__ int sTermL[9] = {0, 0, 0, 1, 1, 1, 2, 2, 2};
+__constant__ int sTermM[9] = {0, 1, 2, 0, 1, 2, 0, 1, 2};
+// coefficient slot of each term: c_11 c_12 c_13 c_22 c_23 c_33 (c_lm = c_ml)
+__constant__ int sSlot[9] = {0, 1, 2, 1, 3, 4, 2, 4, 5};
+
+template <typename T>
+__device__ __forceinline__ T fmaR(T a, T b, T c);
+template <>
+__device__ __forceinline__ double fmaR<double>(double a, double b, double c) { return fma(a, b, c); }
+template <>
+__device__ __forceinline__ float fmaR<float>(float a, float b, float c) { return fmaf(a, b, c); }
+
+__device__ __forceinline__ int blo(int i, int p) { return i - p > 0 ? i - p : 0; }
+__device__ __forceinline__ int bw(int i, int p, int n) { return min(n - 1, i + p) - blo(i, p) + 1; }
+
+// Tables and coefficients come in the arithmetic type of the contractions (the
+// FP32 path reads float copies made once per call), so no conversion sits in
+// the inner loops.
+struct Dir {
+  int n, nqp;
+  const int* q0;
+  const int* nq;
+  const void* w;          // Real [4][n][NQ]
+  const void* bt;         // Real [2][n][NQ]
+  const int64_t* prefix;  // [n+1]
+  const int* pair_row;    // [nnz1]: i of each band pair
+};
+
+struct StagedArgs {
+  Dir d[3];
+  int NQ;
+  int64_t nnz1[3];
+  const void* cT;         // Real [7][nqp3][nqp1][nqp2]
+  const void* kappaT;     // NULL or Real [nqp3][nqp1][nqp2]
+  void* T3;               // Real [nnz1_3][NT][nqp1][nqp2]
+  void* G;                // Real [nnz1_3][NG][nqp1][nnz1_2]
+  void* vals;
+};
+
+template <typename Real>
+__device__ __forceinline__ const Real* tab(const void* p) { return reinterpret_cast<const Real*>(p); }
+
+__global__ void k_to_float(const double* __restrict__ in, float* __restrict__ out, int64_t n) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) out[i] = (float)in[i];
+}
+
+// (q1, q2, q3) -> (q3, q1, q2) copy of the coefficient planes (and kappa)
+template <typename Real>
+__global__ void k_transpose_coef(const double* __restrict__ c, const double* __restrict__ kappa,
+                                 Real* __restrict__ cT, Real* __restrict__ kT, int nq1, int nq2, int nq3,
+                                 int nplanes) {
+  __shared__ Real tile[32][33];
+  const int bx = blockIdx.x * 32, by = blockIdx.y * 32;  // q1, q2 tile
+  const int plane = blockIdx.z;                          // slot * nq3 + q3
+  const int slot = plane / nq3;
+  const double* src = slot < nplanes ? c + (int64_t)plane * nq1 * nq2 : kappa + (int64_t)(plane - nplanes * nq3) * nq1 * nq2;
+  Real* dst = slot < nplanes ? cT + (int64_t)plane * nq1 * nq2 : kT + (int64_t)(plane - nplanes * nq3) * nq1 * nq2;
+  for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+    const int q2 = by + k, q1 = bx + threadIdx.x;
+    if (q1 < nq1 && q2 < nq2) tile[k][threadIdx.x] = (Real)src[(int64_t)q2 * nq1 + q1];
+  }
+  __syncthreads();
+  for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+    const int q1 = bx + k, q2 = by + threadIdx.x;
+    if (q1 < nq1 && q2 < nq2) dst[(int64_t)q1 * nq2 + q2] = tile[threadIdx.x][k];
+  }
+}
+
+// K3: one thread per (q2, q1, i3); all terms and all j3 of the band. Blocks with
+// consecutive i3 (blockIdx.x) read overlapping coefficient planes back to back.
+template <int P, bool MASS, typename Real>
+__global__ void __launch_bounds__(128) k_stage3(StagedArgs A) {
+  constexpr int MAXQ = 4 * P + 1;
+  constexpr int NT = MASS ? 1 : 9;
+  constexpr int BW = 2 * P + 1;
+  const Dir& D3 = A.d[2];
+  const int nq1 = A.d[0].nqp, nq2 = A.d[1].nqp;
+  const int i3 = blockIdx.x;
+  const int64_t e = blockIdx.y * (int64_t)blockDim.x + threadIdx.x;  // point index q1 * nq2 + q2
+  const int q1 = (int)(e / nq2), q2 = (int)(e % nq2);
+  const int NQ = A.NQ;
+  const int qi3 = D3.q0[i3], ni3 = D3.nq[i3];
+  const int jlo = blo(i3, P), jhi = min(D3.n - 1, i3 + P);
+  // a3[k][jj][t] = w3^{k}(i3, qi3 + t) B3^{k & 1}(j3, qi3 + t) on the overlap [lo, hi) of Q_i3 and Q_j3
+  __shared__ Real a3[4][BW][MAXQ];
+  __shared__ int olo[BW], ohi[BW];
+  for (int e = threadIdx.x; e < 4 * BW * MAXQ; e += blockDim.x) {
+    const int t = e % MAXQ, jj = (e / MAXQ) % BW, k = e / (MAXQ * BW);
+    const int j3 = jlo + jj;
+    double v = 0.0;
+    if (j3 <= jhi && t < ni3) {
+      const int loc = qi3 + t - D3.q0[j3];
+      if (loc >= 0 && loc < D3.nq[j3])
+        v = (double)tab<Real>(D3.w)[((size_t)k * D3.n + i3) * NQ + t] *
+            (double)tab<Real>(D3.bt)[((size_t)(k & 1) * D3.n + j3) * NQ + loc];
+    }
+    a3[k][jj][t] = (Real)v;
+  }
+  for (int jj = threadIdx.x; jj < BW; jj += blockDim.x) {
+    const int j3 = jlo + jj;
+    if (j3 <= jhi) {
+      const int qj = D3.q0[j3];
+      olo[jj] = max(qi3, qj) - qi3;
+      ohi[jj] = min(qi3 + ni3, qj + D3.nq[j3]) - qi3;
+    }
+  }
+  __syncthreads();
+  if (q1 >= nq1) return;
+  const int64_t plane = (int64_t)nq1 * nq2;
+  const int64_t pt = (int64_t)q1 * nq2 + q2;
+  const int64_t p3base = D3.prefix[i3];
+  Real* T3 = reinterpret_cast<Real*>(A.T3);
+  const int nslots = MASS ? 1 : 6;
+  for (int s = 0; s < nslots; ++s) {
+    const int slot = MASS ? 6 : s;
+    Real c[MAXQ];
+    const Real* cs = tab<Real>(A.cT) + ((int64_t)slot * D3.nqp + qi3) * plane + pt;
+    const Real* ks = A.kappaT ? tab<Real>(A.kappaT) + (int64_t)qi3 * plane + pt : nullptr;
+    for (int t = 0; t < ni3; ++t) c[t] = ks ? cs[t * plane] * ks[t * plane] : cs[t * plane];
+    for (int term = 0; term < NT; ++term) {
+      if (!MASS && sSlot[term] != s) continue;
+      const int l = MASS ? 0 : sTermL[term], m = MASS ? 0 : sTermM[term];
+      const int k3 = MASS ? 0 : 2 * (l == 2) + (m == 2);
+      for (int jj = 0; jj <= jhi - jlo; ++jj) {
+        const Real* a = a3[k3][jj];
+        Real acc = (Real)0;
+        for (int t = olo[jj]; t < ohi[jj]; ++t) acc = fmaR<Real>(a[t], c[t], acc);
+        T3[(((p3base + jj) * NT + term) * nq1 + q1) * nq2 + q2] = acc;
+      }
+    }
+  }
+}
+
+// K2: one thread per (i2, q1, p3). Regular rows of direction 2 use a compile-time
+// (t, j2) pattern; rows next to the boundary loop over the support overlaps.
+// Regular rows: threads run over (i2 in [r_lo, r_hi), then q1), neighbouring
+// threads sharing q2 points. Boundary rows [0, r_lo) and [r_hi, n2): threads run
+// over (q1, then the row), so every lane has work.
+template <int P, bool MASS, typename Real, bool REG>
+__global__ void __launch_bounds__(128) k_stage2(StagedArgs A, int r_lo, int r_hi) {
+  constexpr int BW = 2 * P + 1;
+  constexpr int NT = MASS ? 1 : 9;
+  constexpr int NG = MASS ? 1 : 4;
+  constexpr int NC = MASS ? 1 : 6;
+  constexpr int MAXQ = 4 * P + 1;
+  // classes: (group, b2, first term, last term) with terms ordered as sTerm*
+  // class 0: (0,0) g3 b0; 1: (0,1) g2 b1; 2: (0,2) g2 b0; 3: (1,0),(2,0) g1 b0;
+  // 4: (1,1),(2,1) g0 b1; 5: (1,2),(2,2) g0 b0
+  constexpr int cls_terms[6][2] = {{0, -1}, {1, -1}, {2, -1}, {3, 6}, {4, 7}, {5, 8}};
+  constexpr int cls_group[6] = {3, 2, 2, 1, 0, 0};
+  constexpr int cls_b2[6] = {0, 1, 0, 0, 1, 0};
+  const Dir& D2 = A.d[1];
+  const int nq1 = A.d[0].nqp, nq2 = D2.nqp, NQ = A.NQ;
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t p3 = blockIdx.y;
+  int i2, q1;
+  if (REG) {
+    const int nreg = r_hi - r_lo;
+    if (e >= (int64_t)nreg * nq1) return;
+    i2 = r_lo + (int)(e % nreg);
+    q1 = (int)(e / nreg);
+  } else {
+    const int nb = r_lo + (D2.n - r_hi);
+    if (e >= (int64_t)nb * nq1) return;
+    q1 = (int)(e % nq1);
+    const int b = (int)(e / nq1);
+    i2 = b < r_lo ? b : r_hi + (b - r_lo);
+  }
+  const int64_t nnz2 = A.nnz1[1];
+  const Real* T3 = reinterpret_cast<const Real*>(A.T3) + ((p3 * NT) * nq1 + q1) * (int64_t)nq2;
+  const int64_t tstride = (int64_t)nq1 * nq2;
+  const int qi = D2.q0[i2], ni = REG ? BW : D2.nq[i2];
+  const int jlo = blo(i2, P), jhi = min(D2.n - 1, i2 + P);
+  Real acc[NG][BW];
+#pragma unroll
+  for (int g = 0; g < NG; ++g)
+#pragma unroll
+    for (int tt = 0; tt < BW; ++tt) acc[g][tt] = (Real)0;
+#pragma unroll
+  for (int c = 0; c < NC; ++c) {
+    Real h[REG ? BW : MAXQ];
+#pragma unroll
+    for (int t = 0; t < (REG ? BW : MAXQ); ++t) h[t] = (Real)0;
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      const int term = MASS ? 0 : cls_terms[c][k];
+      if (term < 0 || (MASS && k > 0)) continue;
+      const int l = MASS ? 0 : term / 3, m = MASS ? 0 : term % 3;
+      const int k2 = MASS ? 0 : 2 * (l == 1) + (m == 1);
+      const Real* wrow = tab<Real>(D2.w) + ((size_t)k2 * D2.n + i2) * NQ;
+      const Real* trow = T3 + term * tstride + qi;
+      if (REG) {
+#pragma unroll
+        for (int t = 0; t < BW; ++t) h[t] = fmaR<Real>(wrow[t], trow[t], h[t]);
+      } else {
+        for (int t = 0; t < ni; ++t) h[t] = fmaR<Real>(wrow[t], trow[t], h[t]);
+      }
+    }
+    const int g = MASS ? 0 : cls_group[c];
+    const int b2 = MASS ? 0 : cls_b2[c];
+    if (REG) {
+#pragma unroll
+      for (int tt = 0; tt < BW; ++tt) {
+        const int j2 = i2 - P + tt;
+        const Real* brow = tab<Real>(D2.bt) + ((size_t)b2 * D2.n + j2) * NQ + (qi - D2.q0[j2]);
+#pragma unroll
+        for (int t = 0; t < BW; ++t)
+          if (t >= 2 * tt - 2 * P && t <= 2 * tt) acc[g][tt] = fmaR<Real>(brow[t], h[t], acc[g][tt]);
+      }
+    } else {
+#pragma unroll
+      for (int tt = 0; tt < BW; ++tt) {
+        const int j2 = i2 - P + tt;
+        if (j2 < jlo || j2 > jhi) continue;
+        const int qj = D2.q0[j2];
+        const int lo = max(qi, qj), hi = min(qi + ni, qj + D2.nq[j2]);
+        const Real* brow = tab<Real>(D2.bt) + ((size_t)b2 * D2.n + j2) * NQ;
+        for (int q = lo; q < hi; ++q) acc[g][tt] = fmaR<Real>(brow[q - qj], h[q - qi], acc[g][tt]);
+      }
+    }
+  }
+  Real* G = reinterpret_cast<Real*>(A.G);
+  const int64_t pbase = D2.prefix[i2];
+#pragma unroll
+  for (int g = 0; g < NG; ++g) {
+    Real* dst = G + ((p3 * NG + g) * nq1 + q1) * nnz2 + pbase;
+#pragma unroll
+    for (int tt = 0; tt < BW; ++tt) {
+      const int j2 = i2 - P + tt;
+      if (REG || (j2 >= jlo && j2 <= jhi)) dst[j2 - jlo] = acc[g][tt];
+    }
+  }
+}
+
+// K1: one thread per (p2, i1, p3): the 2P+1 values of row (i1, i2, i3) in the
+// column block (j2, j3). A block covers 32 consecutive p2 and 4 consecutive i1, so
+// the G rows of overlapping supports are read from L1.
+template <int P, bool MASS, typename Real, typename OutT>
+__global__ void __launch_bounds__(128) k_stage1(StagedArgs A) {
+  constexpr int BW = 2 * P + 1;
+  constexpr int NG = MASS ? 1 : 4;
+  constexpr int MAXQ = 4 * P + 1;
+  const Dir& D1 = A.d[0];
+  const Dir& D2 = A.d[1];
+  const Dir& D3 = A.d[2];
+  const int64_t p2 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int i1 = blockIdx.y * blockDim.y + threadIdx.y;
+  const int64_t p3 = blockIdx.z;
+  const int64_t nnz2 = A.nnz1[1];
+  const int n1 = D1.n, n2 = D2.n, n3 = D3.n, nq1 = D1.nqp, NQ = A.NQ;
+  if (p2 >= nnz2 || i1 >= n1) return;
+  const int i2 = D2.pair_row[p2], j2 = blo(i2, P) + (int)(p2 - D2.prefix[i2]);
+  const int i3 = D3.pair_row[p3], j3 = blo(i3, P) + (int)(p3 - D3.prefix[i3]);
+  const int qi1 = D1.q0[i1], ni1 = D1.nq[i1];
+  const bool reg = i1 >= P + 1 && i1 <= n1 - P - 2;
+  const Real* G = reinterpret_cast<const Real*>(A.G) + ((p3 * NG) * nq1) * nnz2 + p2;
+  const int64_t gstride = (int64_t)nq1 * nnz2;  // next group
+  const int64_t N1 = D1.prefix[n1], N2 = D2.prefix[n2];
+  const int bw1 = bw(i1, P, n1), bw2 = bw(i2, P, n2), bw3 = bw(i3, P, n3);
+  const int jlo1 = blo(i1, P);
+  const int64_t row = D3.prefix[i3] * N2 * N1 + (int64_t)bw3 * (D2.prefix[i2] * N1 + (int64_t)bw2 * D1.prefix[i1]);
+  const int64_t base = row + ((int64_t)(j3 - blo(i3, P)) * bw2 + (j2 - blo(i2, P))) * bw1;  // + (j1 - jlo1)
+  OutT* out = reinterpret_cast<OutT*>(A.vals);
+  const Real* w = tab<Real>(D1.w) + (size_t)i1 * NQ;   // kind k at + k * n1 * NQ
+  const Real* bt1 = tab<Real>(D1.bt);
+  const int64_t wk = (int64_t)n1 * NQ;
+  const int64_t bder = (int64_t)n1 * NQ;          // B' table after B
+  Real s[BW];
+#pragma unroll
+  for (int tt = 0; tt < BW; ++tt) s[tt] = (Real)0;
+  if (reg) {
+#pragma unroll
+    for (int t = 0; t <= 2 * P; ++t) {
+      const Real* gq = G + (int64_t)(qi1 + t) * nnz2;
+      Real h0, h1 = (Real)0;
+      if (MASS) {
+        h0 = w[t] * gq[0];
+      } else {
+        h0 = fmaR<Real>(w[t], gq[0], w[t + 2 * wk] * gq[2 * gstride]);
+        h1 = fmaR<Real>(w[t + wk], gq[gstride], w[t + 3 * wk] * gq[3 * gstride]);
+      }
+#pragma unroll
+      for (int tt = 0; tt < BW; ++tt) {
+        if (t >= 2 * tt - 2 * P && t <= 2 * tt) {
+          const int j1 = i1 - P + tt;
+          const int64_t idx = (int64_t)j1 * NQ + (qi1 + t - D1.q0[j1]);
+          if (MASS)
+            s[tt] = fmaR<Real>(bt1[idx], h0, s[tt]);
+          else
+            s[tt] = fmaR<Real>(bt1[idx + bder], h1, fmaR<Real>(bt1[idx], h0, s[tt]));
+        }
+      }
+    }
+#pragma unroll
+    for (int tt = 0; tt < BW; ++tt) out[base + tt] = (OutT)s[tt];  // j1 - jlo1 = tt for regular rows
+  } else {
+    Real h0[MAXQ], h1[MAXQ];
+    for (int t = 0; t < ni1; ++t) {
+      const Real* gq = G + (int64_t)(qi1 + t) * nnz2;
+      if (MASS) {
+        h0[t] = w[t] * gq[0];
+      } else {
+        h0[t] = fmaR<Real>(w[t], gq[0], w[t + 2 * wk] * gq[2 * gstride]);
+        h1[t] = fmaR<Real>(w[t + wk], gq[gstride], w[t + 3 * wk] * gq[3 * gstride]);
+      }
+    }
+#pragma unroll
+    for (int tt = 0; tt < BW; ++tt) {
+      const int j1 = i1 - P + tt;
+      if (j1 < 0 || j1 >= n1) continue;
+      const int qj = D1.q0[j1];
+      const int lo = max(qi1, qj), hi = min(qi1 + ni1, qj + D1.nq[j1]);
+      const int64_t brow = (int64_t)j1 * NQ - qj;
+      Real v = (Real)0;
+      for (int q = lo; q < hi; ++q) {
+        if (MASS)
+          v = fmaR<Real>(bt1[brow + q], h0[q - qi1], v);
+        else
+          v = fmaR<Real>(bt1[brow + q + bder], h1[q - qi1], fmaR<Real>(bt1[brow + q], h0[q - qi1], v));
+      }
+      out[base + (j1 - jlo1)] = (OutT)v;
+    }
+  }
+}
+
+__global__ void k_pair_rows(const int64_t* __restrict__ prefix, int n, int* __restrict__ pair_row) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  for (int64_t k = prefix[i]; k < prefix[i + 1]; ++k) pair_row[k] = i;
+}
+
+}  // namespace
+
+// Scratch of the staged path, allocated on first use and owned by the plan.
+static wq_status staged_scratch(wq_plan_s* pl, bool mass, size_t real_size, cudaStream_t s) {
+  const int NT = mass ? 1 : 9, NG = mass ? 1 : 4;
+  const size_t t3 = std::max<size_t>(16, (size_t)pl->nnz1[2] * NT * pl->nqp[0] * pl->nqp[1] * real_size);
+  const size_t g = std::max<size_t>(16, (size_t)pl->nnz1[2] * NG * pl->nqp[0] * pl->nnz1[1] * real_size);
+  if (pl->stg_a_bytes < t3 || pl->stg_b_bytes < g) {
+    if (pl->stg_a) cudaFree(pl->stg_a);
+    if (pl->stg_b) cudaFree(pl->stg_b);
+    pl->stg_a = pl->stg_b = nullptr;
+    pl->stg_a_bytes = pl->stg_b_bytes = 0;
+    cudaError_t e = cudaMalloc(&pl->stg_a, t3);
+    if (e == cudaSuccess) e = cudaMalloc(&pl->stg_b, g);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      if (pl->stg_a) cudaFree(pl->stg_a);
+      pl->stg_a = nullptr;
+      return set_error(WQ_ERR_OOM, "staged assembly scratch (T3, G) does not fit in device memory");
+    }
+    pl->stg_a_bytes = t3;
+    pl->stg_b_bytes = g;
+  }
+  if (!pl->coefT) {
+    cudaError_t e = cudaMalloc(&pl->coefT, sizeof(double) * 8 * (size_t)pl->n_qp_total);
+    if (e != cudaSuccess) return wq::cuda_error(e, "transposed coefficient allocation");
+  }
+  if (real_size == sizeof(float))
+    for (int l = 0; l < 3; ++l)
+      if (!pl->dir[l].tab32) {
+        const size_t nt = (size_t)6 * pl->dir[l].n * pl->nq_max;  // 4 rule kinds + 2 basis tables
+        cudaError_t e = cudaMalloc(&pl->dir[l].tab32, sizeof(float) * nt);
+        if (e != cudaSuccess) return wq::cuda_error(e, "float table allocation");
+      }
+  for (int l = 1; l < 3; ++l)
+    if (!pl->dir[l].pair_row) {
+      cudaError_t e = cudaMalloc(&pl->dir[l].pair_row, sizeof(int) * (size_t)std::max<int64_t>(1, pl->nnz1[l]));
+      if (e != cudaSuccess) return wq::cuda_error(e, "pair index allocation");
+      k_pair_rows<<<(pl->dir[l].n + 127) / 128, 128, 0, s>>>(pl->dir[l].prefix, pl->dir[l].n, pl->dir[l].pair_row);
+      count_launch();
+    }
+  return WQ_OK;
+}
+
+template <int P, bool MASS, typename Real, typename OutT>
+static wq_status staged_t(wq_plan_s* pl, const double* kappa, void* vals, cudaStream_t s) {
+  wq_status st = staged_scratch(pl, MASS, sizeof(Real), s);
+  if (st != WQ_OK) return st;
+  StagedArgs A;
+  const bool f32 = sizeof(Real) == sizeof(float);
+  for (int l = 0; l < 3; ++l) {
+    const DirData& d = pl->dir[l];
+    const void* w = d.w;
+    const void* bt = d.bt;
+    if (f32) {
+      const int64_t nw = (int64_t)4 * d.n * pl->nq_max, nb = (int64_t)2 * d.n * pl->nq_max;
+      k_to_float<<<(unsigned)((nw + 255) / 256), 256, 0, s>>>(d.w, d.tab32, nw);
+      k_to_float<<<(unsigned)((nb + 255) / 256), 256, 0, s>>>(d.bt, d.tab32 + nw, nb);
+      count_launch(2);
+      w = d.tab32;
+      bt = d.tab32 + nw;
+    }
+    A.d[l] = Dir{d.n, d.nqp, d.q0, d.nq, w, bt, d.prefix, d.pair_row};
+    A.nnz1[l] = pl->nnz1[l];
+  }
+  A.NQ = pl->nq_max;
+  const int nq1 = (int)pl->nqp[0], nq2 = (int)pl->nqp[1], nq3 = (int)pl->nqp[2];
+  const int64_t NQP = pl->n_qp_total;
+  Real* cT = reinterpret_cast<Real*>(pl->coefT);
+  A.cT = cT;
+  A.kappaT = kappa ? cT + 7 * NQP : nullptr;
+  A.T3 = pl->stg_a;
+  A.G = pl->stg_b;
+  A.vals = vals;
+  // transposed coefficients (the slots this matrix uses) and kappa, in Real
+  {
+    dim3 blk(32, 8), grd((nq1 + 31) / 32, (nq2 + 31) / 32, 7 * nq3 + (kappa ? nq3 : 0));
+    k_transpose_coef<Real><<<grd, blk, 0, s>>>(pl->coef, kappa, cT, cT + 7 * NQP, nq1, nq2, nq3, 7);
+  }
+  const int n1 = (int)pl->n[0], n2 = (int)pl->n[1], n3 = (int)pl->n[2];
+  k_stage3<P, MASS, Real><<<dim3(n3, (unsigned)(((int64_t)nq1 * nq2 + 127) / 128)), 128, 0, s>>>(A);
+  int r_lo = P + 1, r_hi = n2 - P - 1;  // regular rows [r_lo, r_hi)
+  if (r_hi <= r_lo) r_lo = r_hi = n2;   // no regular rows: every row takes the boundary path
+  const int64_t np3 = pl->nnz1[2];
+  if (r_hi > r_lo)
+    k_stage2<P, MASS, Real, true>
+        <<<dim3((unsigned)(((int64_t)(r_hi - r_lo) * nq1 + 127) / 128), (unsigned)np3), 128, 0, s>>>(A, r_lo, r_hi);
+  const int nb = r_lo + (n2 - r_hi);
+  k_stage2<P, MASS, Real, false><<<dim3((unsigned)(((int64_t)nb * nq1 + 127) / 128), (unsigned)np3), 128, 0, s>>>(
+      A, r_lo, r_hi);
+  k_stage1<P, MASS, Real, OutT>
+      <<<dim3((unsigned)((pl->nnz1[1] + 31) / 32), (n1 + 3) / 4, (unsigned)np3), dim3(32, 4), 0, s>>>(A);
+  count_launch(r_hi > r_lo ? 5 : 4);
+  WQ_CUDA_TRY(cudaGetLastError(), "staged assembly launch");
+  return WQ_OK;
+}
+
+template <bool MASS, typename Real, typename OutT>
+static wq_status staged_dispatch(wq_plan_s* pl, const double* kappa, void* vals, cudaStream_t s) {
+  switch (pl->p) {
+    case 2: return staged_t<2, MASS, Real, OutT>(pl, kappa, vals, s);
+    case 3: return staged_t<3, MASS, Real, OutT>(pl, kappa, vals, s);
+    case 4: return staged_t<4, MASS, Real, OutT>(pl, kappa, vals, s);
+    case 5: return staged_t<5, MASS, Real, OutT>(pl, kappa, vals, s);
+    case 6: return staged_t<6, MASS, Real, OutT>(pl, kappa, vals, s);
+    case 7: return staged_t<7, MASS, Real, OutT>(pl, kappa, vals, s);
+    case 8: return staged_t<8, MASS, Real, OutT>(pl, kappa, vals, s);
+    default: return set_error(WQ_ERR_UNSUPPORTED, "degree out of range");
+  }
+}
+
+wq_status launch_staged(wq_plan_s* pl, bool mass, const double* kappa, void* vals, int value_dtype, int precision,
+                        cudaStream_t s) {
+  if (precision == WQ_PREC_FP64)
+    return mass ? staged_dispatch<true, double, double>(pl, kappa, vals, s)
+                : staged_dispatch<false, double, double>(pl, kappa, vals, s);
+  if (value_dtype == WQ_VALUES_F32)
+    return mass ? staged_dispatch<true, float, float>(pl, kappa, vals, s)
+                : staged_dispatch<false, float, float>(pl, kappa, vals, s);
+  return mass ? staged_dispatch<true, float, double>(pl, kappa, vals, s)
+              : staged_dispatch<false, float, double>(pl, kappa, vals, s);
+}
+
+}  // namespace wq

@@ -33,6 +33,7 @@ def test_batch_matches_single_plan_assembly_and_oracle(wq):
         batch.launch()
     torch.cuda.synchronize()
     for k, (pl, pt) in enumerate(zip(plans, patches)):
+        pl.set_algorithm("fused")                   # the batch runs the fused tile kernel
         ref = pl.stiffness()
         torch.cuda.synchronize()
         assert torch.equal(S[k], ref), k

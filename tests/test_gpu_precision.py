@@ -1,0 +1,52 @@
+"""Precision study on the p = 5, 128^3 workload (N_DOF = 133^3, 2.94e9 nonzeros):
+FP32 contractions with FP32 or FP64 values against the FP64 oracle on sampled rows.
+Reports the worst row-relative max-entry error and the Frobenius error of the
+sampled rows; the bar is 1e-6 row-relative."""
+import os
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle import Oracle3D, rows_c  # noqa: E402
+from wq_synth import sample_rows, workload_p5_128  # noqa: E402
+
+THREADS = max(1, min(16, os.cpu_count() or 1))
+
+
+@pytest.fixture(scope="module")
+def setup():
+    import paper_1605_01238_gb300 as wq
+    from paper_1605_01238_gb300 import build
+    build.build()
+    patch = workload_p5_128()
+    plan = wq.Plan(patch.p, patch.knots, patch.ctrl)
+    orc = Oracle3D(patch.p, patch.knots, patch.ctrl)
+    rows = sample_rows(plan.n, plan.p, 48, seed=4000)
+    ref = rows_c(orc, rows, "stiffness", threads=THREADS)
+    rp = plan.pattern()[0].cpu().numpy()
+    yield plan, rows, ref, rp
+    plan.close()
+
+
+@pytest.mark.parametrize("dtype", ["float32", "float64"])
+def test_fp32_contractions_p5_128(setup, dtype):
+    plan, rows, ref, rp = setup
+    vals = plan.stiffness(precision="fp32", dtype=getattr(torch, dtype))
+    torch.cuda.synchronize()
+    idx = np.concatenate([np.arange(rp[r], rp[r + 1]) for r in rows])
+    got = vals[torch.as_tensor(idx, device="cuda")].double().cpu().numpy()
+    off, worst, num, den = 0, 0.0, 0.0, 0.0
+    for rv in ref:
+        g = got[off:off + len(rv)]
+        worst = max(worst, np.abs(g - rv).max() / np.abs(rv).max())
+        num += float(np.sum((g - rv) ** 2))
+        den += float(np.sum(rv ** 2))
+        off += len(rv)
+    frob = (num / den) ** 0.5
+    print(f"p=5 128^3 fp32 contractions, {dtype} values: max row-relative {worst:.3e}, Frobenius {frob:.3e}")
+    del vals
+    torch.cuda.empty_cache()
+    assert worst <= 1e-6

@@ -1,0 +1,78 @@
+"""The staged assembly (three kernels, one per mode product, intermediates in device
+memory) against the oracle, and against the fused kernel."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle import Oracle3D  # noqa: E402
+from test_gpu_parity import TOL_F64, TOL_F64_P8, check_rows  # noqa: E402
+from wq_synth import (graded_breaks, perturbed_cube, random_field, sample_rows, workload_p4_64,  # noqa: E402
+                      workload_sweep)
+
+
+@pytest.fixture(scope="module")
+def wq():
+    import paper_1605_01238_gb300 as wq
+    from paper_1605_01238_gb300 import build
+    build.build()
+    wq.load()
+    return wq
+
+
+SMALL = [
+    ("p2_2x2x2", lambda: perturbed_cube(2, (2, 2, 2), seed=3)),
+    ("p3_2x3x7", lambda: perturbed_cube(3, (2, 3, 7), seed=4)),
+    ("p4_3x9x5", lambda: perturbed_cube(4, (3, 9, 5), seed=5)),
+    ("p5_12x7x4", lambda: perturbed_cube(5, (12, 7, 4), seed=6)),
+    ("p3_graded", lambda: perturbed_cube(3, (9, 11, 7), seed=7,
+                                         breaks=[graded_breaks(e, seed=40 + k) for k, e in enumerate((9, 11, 7))])),
+    ("p2_ragged_37x5x3", lambda: perturbed_cube(2, (37, 5, 3), seed=8)),
+]
+
+
+@pytest.mark.parametrize("name,factory", SMALL, ids=[s[0] for s in SMALL])
+def test_staged_every_row(wq, name, factory):
+    patch = factory()
+    plan = wq.Plan(patch.p, patch.knots, patch.ctrl)
+    plan.set_algorithm("staged")
+    orc = Oracle3D(patch.p, patch.knots, patch.ctrl)
+    kappa = random_field(int(np.prod(plan.n_qp)), seed=9, kind="positive")
+    kd = torch.as_tensor(kappa, device="cuda")
+    S, M = plan.stiffness(), plan.mass(kappa=kd)
+    torch.cuda.synchronize()
+    rows = np.arange(plan.n_rows)
+    check_rows(orc, plan, S, "stiffness", rows)
+    check_rows(Oracle3D(patch.p, patch.knots, patch.ctrl, kappa=kappa), plan, M, "mass", rows)
+    plan.set_algorithm("fused")
+    S2 = plan.stiffness()
+    torch.cuda.synchronize()
+    assert float((S - S2).abs().max()) <= 1e-13 * float(S2.abs().max())
+
+
+@pytest.mark.parametrize("p,count", [(4, 120), (5, 48), (8, 12)])
+def test_staged_full_size_sampled_rows(wq, p, count):
+    patch = workload_p4_64() if p == 4 else workload_sweep(p)
+    plan = wq.Plan(patch.p, patch.knots, patch.ctrl)
+    plan.set_algorithm("staged")
+    S = plan.stiffness()
+    torch.cuda.synchronize()
+    orc = Oracle3D(patch.p, patch.knots, patch.ctrl)
+    rows = sample_rows(plan.n, plan.p, count, seed=7000 + p)
+    check_rows(orc, plan, S, "stiffness", rows, tol=TOL_F64_P8 if p == 8 else TOL_F64)
+    del S
+    plan.close()
+    torch.cuda.empty_cache()
+
+
+def test_staged_fp32(wq):
+    patch = perturbed_cube(4, (12, 10, 9), seed=12)
+    plan = wq.Plan(patch.p, patch.knots, patch.ctrl)
+    plan.set_algorithm("staged")
+    S = plan.stiffness(precision="fp32", dtype=torch.float32)
+    torch.cuda.synchronize()
+    orc = Oracle3D(patch.p, patch.knots, patch.ctrl)
+    rows = sample_rows(plan.n, plan.p, 120, seed=5)
+    worst = check_rows(orc, plan, S, "stiffness", rows, tol=2e-6)
+    print(f"staged fp32: worst row-relative error {worst:.3e}")
