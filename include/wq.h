@@ -60,7 +60,9 @@ enum { WQ_VALUES_F64 = 0, WQ_VALUES_F32 = 1 };
  * Jacobian, its inverse and determinant always run in FP64. */
 enum {
   WQ_PREC_FP64 = 0,          /* FP64 FMA throughout */
-  WQ_PREC_FP32 = 1           /* FP32 FMA, FP32 intermediates */
+  WQ_PREC_FP32 = 1,          /* FP32 FMA, FP32 intermediates */
+  WQ_PREC_MIXED = 2          /* FP64 for the first two mode products (contracting q3, q2),
+                                FP32 for the last one (q1, half of the work); staged only */
 };
 
 /* ---- plan ------------------------------------------------------------------
@@ -123,7 +125,7 @@ wq_status wq_plan_refresh(wq_plan_t plan, const double* ctrl, int ctrl_on_device
  *            (Eq. (mass2): c absorbs the PDE coefficient)
  *   d_vals   device array of nnz values of type value_dtype, caller-owned
  *   value_dtype  WQ_VALUES_F64 or WQ_VALUES_F32
- *   precision    WQ_PREC_FP64 (requires WQ_VALUES_F64) or WQ_PREC_FP32
+ *   precision    WQ_PREC_FP64 (requires WQ_VALUES_F64), WQ_PREC_FP32 or WQ_PREC_MIXED
  * Asynchronous on `stream`; no allocation, no synchronisation. */
 wq_status wq_assemble_stiffness(wq_plan_t plan, const double* d_kappa, void* d_vals,
                                 int value_dtype, int precision, void* stream);
@@ -250,7 +252,7 @@ wq_status wq_get_coefficients(wq_plan_t plan, double* h_coef);
  *   nq_stride  row stride of d_w: at least max_i |Q_i| (at most 4p+1)
  * It calls no cudaMalloc, cudaFree or allocating library routine. Its
  * intermediate tables live in one fixed device array of
- * WQ_RULES_NOALLOC_SCRATCH_BYTES (5.75 MB) that every GPU loading the
+ * WQ_RULES_NOALLOC_SCRATCH_BYTES (5.9 MB) that every GPU loading the
  * library holds until the process exits; knot vectors with more than
  * WQ_RULES_NOALLOC_MAX_N basis functions are rejected with WQ_ERR_INVALID_ARG.
  * The first call on a device looks up that array's device address
@@ -260,7 +262,7 @@ wq_status wq_get_coefficients(wq_plan_t plan, double* h_coef);
  * race on it, so serialise them. The call synchronises `stream` before it returns
  * (to report a rule breakdown as WQ_ERR_SINGULAR_RULE). */
 #define WQ_RULES_NOALLOC_MAX_N 1024
-#define WQ_RULES_NOALLOC_SCRATCH_BYTES 5754880
+#define WQ_RULES_NOALLOC_SCRATCH_BYTES 5903872
 wq_status wq_rules_noalloc(int p, int64_t n_knots, const double* h_knots, double* d_w, int32_t* d_q0,
                            int32_t* d_nq, int nq_stride, void* stream);
 

@@ -112,6 +112,7 @@ struct DirData {
   dd* greville = nullptr;    // [n] Greville abscissae (xi_{i+1} + ... + xi_{i+p}) / p
   int* pair_row = nullptr;   // [nnz1] row i of each band pair (staged assembly)
   float* tab32 = nullptr;    // [6][n][NQ] float copies of w and bt (staged FP32 assembly)
+  dd* recip = nullptr;       // [p+1][n+p+1] 1 / (xi_{j+k} - xi_j), double-double
 };
 
 }  // namespace wq
@@ -139,7 +140,8 @@ struct wq_plan_s {
   double* coefT = nullptr;        // staged: [8][N_QP] transposed coefficients (+ kappa)
   void* stg_a = nullptr;          // staged: T3
   void* stg_b = nullptr;          // staged: G
-  size_t stg_a_bytes = 0, stg_b_bytes = 0;
+  void* stg_c = nullptr;          // staged, mixed precision: FP64 edge copy of G
+  size_t stg_a_bytes = 0, stg_b_bytes = 0, stg_c_bytes = 0;
 };
 
 namespace wq {

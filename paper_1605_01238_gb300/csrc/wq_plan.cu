@@ -32,23 +32,18 @@ namespace wq {
 // s is the knot-vector index of the span start (xi_s <= x < xi_{s+1} for points
 // of that span); the p+1 functions B_{s-p+t}, t = 0..p, are returned with their
 // first derivatives, as the span's polynomial pieces evaluated at x.
-__device__ void basis_dd(const double* xi, int p, int s, dd x, dd* val, dd* der) {
+__device__ void basis_dd(const double* xi, const dd* rc, int ld, int p, int s, dd x, dd* val, dd* der) {
+  // rc[k * ld + j] = 1 / (xi_{j+k} - xi_j) (zero for a repeated knot), see k_recips
   dd cur[kMaxP + 1], nxt[kMaxP + 1], low[kMaxP + 1];
   cur[0] = dd_make(1.0);
   for (int k = 1; k <= p; ++k) {
     for (int t = 0; t <= k; ++t) {
       int j = s - k + t;
       dd v = dd_make(0.0);
-      if (t >= 1) {  // (x - xi_j)/(xi_{j+k} - xi_j) B_{j,k-1}
-        dd num = dd_sub(x, dd_make(xi[j]));
-        dd den = two_sum(xi[j + k], -xi[j]);
-        v = dd_add(v, dd_mul(dd_div(num, den), cur[t - 1]));
-      }
-      if (t <= k - 1) {  // (xi_{j+k+1} - x)/(xi_{j+k+1} - xi_{j+1}) B_{j+1,k-1}
-        dd num = dd_sub(dd_make(xi[j + k + 1]), x);
-        dd den = two_sum(xi[j + k + 1], -xi[j + 1]);
-        v = dd_add(v, dd_mul(dd_div(num, den), cur[t]));
-      }
+      if (t >= 1)  // (x - xi_j)/(xi_{j+k} - xi_j) B_{j,k-1}
+        v = dd_add(v, dd_mul(dd_mul(dd_sub(x, dd_make(xi[j])), rc[k * ld + j]), cur[t - 1]));
+      if (t <= k - 1)  // (xi_{j+k+1} - x)/(xi_{j+k+1} - xi_{j+1}) B_{j+1,k-1}
+        v = dd_add(v, dd_mul(dd_mul(dd_sub(dd_make(xi[j + k + 1]), x), rc[k * ld + j + 1]), cur[t]));
       nxt[t] = v;
     }
     if (k == p)
@@ -59,11 +54,25 @@ __device__ void basis_dd(const double* xi, int p, int s, dd x, dd* val, dd* der)
     val[t] = cur[t];
     int j = s - p + t;
     dd d = dd_make(0.0);
-    if (t >= 1) d = dd_add(d, dd_div(dd_mul_d(low[t - 1], (double)p), two_sum(xi[j + p], -xi[j])));
-    if (t <= p - 1)
-      d = dd_sub(d, dd_div(dd_mul_d(low[t], (double)p), two_sum(xi[j + p + 1], -xi[j + 1])));
+    if (t >= 1) d = dd_add(d, dd_mul_d(dd_mul(low[t - 1], rc[p * ld + j]), (double)p));
+    if (t <= p - 1) d = dd_sub(d, dd_mul_d(dd_mul(low[t], rc[p * ld + j + 1]), (double)p));
     der[t] = d;
   }
+}
+
+// Reciprocals of the knot differences: rc[k * ld + j] = 1/(xi_{j+k} - xi_j),
+// k = 1..p, j = 0..n+p-k, in double-double (zero where the knots coincide).
+__global__ void k_recips(const double* __restrict__ xi, int n, int p, int ld, dd* __restrict__ rc) {
+  const int id = blockIdx.x * blockDim.x + threadIdx.x;
+  const int len = n + p + 1;
+  if (id >= p * ld) return;
+  const int k = 1 + id / ld, j = id % ld;
+  dd v = dd_make(0.0);
+  if (j + k < len) {
+    dd d = two_sum(xi[j + k], -xi[j]);
+    if (d.hi != 0.0) v = dd_div(dd_make(1.0), d);
+  }
+  rc[k * ld + j] = v;
 }
 
 // Legendre P_m and P_{m-1} at x by the three-term recurrence, double-double.
@@ -127,6 +136,7 @@ struct DirArgs {
   int64_t* prefix;
   dd* greville;
   const dd* gauss;
+  const dd* recip;  // [p+1][n+p+1] knot-difference reciprocals
   int* err;
 };
 
@@ -158,6 +168,7 @@ static DirArgs dir_args(wq_plan_s* pl, int l) {
   a.w = d.w;
   a.prefix = d.prefix;
   a.greville = d.greville;
+  a.recip = d.recip;
   a.gauss = pl->gauss;
   a.err = pl->err;
   return a;
@@ -214,7 +225,7 @@ __global__ void k_basis_points(DirArgs3 A) {
   const int p = a.p;
   int f = a.first[q];
   dd val[kMaxP + 1], der[kMaxP + 1];
-  basis_dd(a.knots, p, f + p, a.x_dd[q], val, der);
+  basis_dd(a.knots, a.recip, a.n + p + 1, p, f + p, a.x_dd[q], val, der);
   for (int t = 0; t <= p; ++t) {
     a.bp[(0 * a.nqp + q) * (p + 1) + t] = dd_to_d(val[t]);
     a.bp[(1 * a.nqp + q) * (p + 1) + t] = dd_to_d(der[t]);
@@ -245,7 +256,7 @@ __global__ void k_gauss_basis(DirArgs3 A) {
   half = dd{0.5 * half.hi, 0.5 * half.lo};
   dd x = dd_add(mid, dd_mul(half, a.gauss[g]));
   dd val[kMaxP + 1], der[kMaxP + 1];
-  basis_dd(a.knots, p, span + p, x, val, der);
+  basis_dd(a.knots, a.recip, a.n + p + 1, p, span + p, x, val, der);
   dd* out = a.gb + ((size_t)span * m + g) * 2 * m;
   for (int t = 0; t <= p; ++t) {
     out[t] = val[t];
@@ -445,19 +456,19 @@ __global__ void k_row_ptr(PatternArgs a) {
 }
 
 // Column indices: one warp per row, ascending j1 + n1 (j2 + n2 j3). Each lane
-// walks its entries e = lane, lane + 32, ... keeping (t1, t2, t3) up to date
-// by carries instead of dividing every index.
+// walks its entries e = lane, lane + 32, ... keeping (t1, t2, t3) up to date by
+// carries; N_DOF < 2^31, so the column arithmetic stays in 32 bits.
 __global__ void k_cols(PatternArgs a) {
   const int64_t N = (int64_t)a.n1 * a.n2 * a.n3;
   const int lane = threadIdx.x & 31;
   int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int n12 = a.n1 * a.n2;
   for (int64_t r = warp; r < N; r += nwarps) {
-    int i1 = (int)(r % a.n1);
-    int i2 = (int)((r / a.n1) % a.n2);
-    int i3 = (int)(r / ((int64_t)a.n1 * a.n2));
-    int w1 = band_w(i1, a.p, a.n1), w2 = band_w(i2, a.p, a.n2), w3 = band_w(i3, a.p, a.n3);
-    int l1 = band_lo(i1, a.p), l2 = band_lo(i2, a.p), l3 = band_lo(i3, a.p);
+    const int rr = (int)r;
+    const int i1 = rr % a.n1, i2 = (rr / a.n1) % a.n2, i3 = rr / n12;
+    const int w1 = band_w(i1, a.p, a.n1), w2 = band_w(i2, a.p, a.n2), w3 = band_w(i3, a.p, a.n3);
+    const int c0 = band_lo(i1, a.p) + a.n1 * band_lo(i2, a.p) + n12 * band_lo(i3, a.p);
     int32_t* out = a.col + a.row_ptr[r];
     const int cnt = w1 * w2 * w3;
     int t1 = lane % w1, rest = lane / w1;
@@ -465,12 +476,12 @@ __global__ void k_cols(PatternArgs a) {
     const int s1 = 32 % w1, c1 = 32 / w1;        // step of 32 entries: +s1 in t1, +c1 carried to t2
     const int s2 = c1 % w2, c2 = c1 / w2;
     for (int e = lane; e < cnt; e += 32) {
-      out[e] = (int32_t)((l1 + t1) + (int64_t)a.n1 * ((l2 + t2) + (int64_t)a.n2 * (l3 + t3)));
+      out[e] = c0 + t1 + a.n1 * t2 + n12 * t3;
       t1 += s1;
       int k2 = s2, k3 = c2;
       if (t1 >= w1) { t1 -= w1; ++k2; }
       t2 += k2;
-      while (t2 >= w2) { t2 -= w2; ++k3; }
+      if (t2 >= w2) { t2 -= w2; ++k3; }
       t3 += k3;
     }
   }
@@ -664,6 +675,12 @@ wq_status run_setup(wq_plan_s* pl, cudaStream_t s, bool with_pattern) {
     WQ_CUDA_TRY(cudaMemsetAsync(d.bt_dd, 0, tab * sizeof(dd), s), "table reset");
   }
   const int tb = 128;
+  for (int l = 0; l < 3; ++l) {
+    const DirData& d = pl->dir[l];
+    const int ld = d.n + p + 1;
+    k_recips<<<(p * ld + tb - 1) / tb, tb, 0, s>>>(d.knots, d.n, p, ld, d.recip);
+  }
+  count_launch(3);
   k_points<<<dim3((max_qp + tb - 1) / tb, 3), tb, 0, s>>>(A);
   k_qranges<<<dim3((max_n + tb - 1) / tb, 3), tb, 0, s>>>(A);
   k_basis_points<<<dim3((max_qp + tb - 1) / tb, 3), tb, 0, s>>>(A);
@@ -735,12 +752,12 @@ static void free_plan(wq_plan_s* pl) {
   for (int l = 0; l < 3; ++l) {
     wq::DirData& d = pl->dir[l];
     void* ptrs[] = {d.knots, d.x, d.x_dd, d.first, d.q0, d.nq, d.bt_dd, d.bt, d.bp, d.gb, d.integ, d.w, d.prefix,
-                    d.greville, d.pair_row, d.tab32};
+                    d.greville, d.pair_row, d.tab32, d.recip};
     for (void* q : ptrs)
       if (q) cudaFree(q);
   }
   void* ptrs[] = {pl->ctrl, pl->ctrl_delta, pl->coef, pl->row_ptr, pl->col, pl->gauss, pl->err, pl->jac,
-                  pl->adj_scratch, pl->coefT, pl->stg_a, pl->stg_b};
+                  pl->adj_scratch, pl->coefT, pl->stg_a, pl->stg_b, pl->stg_c};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   delete pl;
@@ -844,6 +861,7 @@ extern "C" wq_status wq_plan_create(wq_plan_t* out, int d, int p, const int64_t 
     ALLOC(dd.w, sizeof(double) * 4 * dd.n * nqmax, "rules");
     ALLOC(dd.prefix, sizeof(int64_t) * (dd.n + 1), "band prefix");
     ALLOC(dd.greville, sizeof(wq::dd) * dd.n, "Greville points");
+    ALLOC(dd.recip, sizeof(wq::dd) * (p + 1) * (dd.n + p + 1), "knot reciprocals");
   }
   ALLOC(pl->ctrl, sizeof(double) * 3 * N, "control points");
   ALLOC(pl->ctrl_delta, sizeof(double) * 3 * N, "control point offsets");
@@ -987,7 +1005,7 @@ constexpr int kNoAllocMaxQp = 2 * kNoAllocMaxElems + 2 * kMaxP - 1;
 constexpr size_t align256(size_t x) { return (x + 255) / 256 * 256; }
 
 struct NoAllocLayout {
-  size_t knots, x, x_dd, first, bt_dd, bt, bp, gb, integ, gauss, err, total;
+  size_t knots, x, x_dd, first, bt_dd, bt, bp, gb, integ, gauss, recip, err, total;
 };
 
 constexpr NoAllocLayout noalloc_layout() {
@@ -1003,6 +1021,7 @@ constexpr NoAllocLayout noalloc_layout() {
   L.gb = o; o += align256(sizeof(dd) * kNoAllocMaxElems * (kMaxP + 1) * 2 * (kMaxP + 1));
   L.integ = o; o += align256(sizeof(dd) * 4 * kNoAllocMaxN * (2 * kMaxP + 1));
   L.gauss = o; o += align256(sizeof(dd) * 2 * (kMaxP + 1));
+  L.recip = o; o += align256(sizeof(dd) * (kMaxP + 1) * kNoAllocMaxKnots);
   L.err = o; o += align256(sizeof(int));
   L.total = o;
   return L;
@@ -1088,6 +1107,7 @@ extern "C" wq_status wq_rules_noalloc(int p, int64_t n_knots, const double* h_kn
   a.prefix = nullptr;
   a.greville = nullptr;
   a.gauss = reinterpret_cast<const wq::dd*>(base + L.gauss);
+  a.recip = reinterpret_cast<const wq::dd*>(base + L.recip);
   int* err = reinterpret_cast<int*>(base + L.err);
   a.err = err;
   // the scratch keeps the previous call's contents: clear what is read before written
@@ -1101,13 +1121,15 @@ extern "C" wq_status wq_rules_noalloc(int p, int64_t n_knots, const double* h_kn
   wq::DirArgs3 A;
   A.d[0] = a;
   wq::k_gauss<<<1, 32, 0, s>>>(reinterpret_cast<wq::dd*>(base + L.gauss), p + 1);
+  wq::k_recips<<<(p * (int)n_knots + tb - 1) / tb, tb, 0, s>>>(reinterpret_cast<const double*>(base + L.knots), (int)n,
+                                                                p, (int)n_knots, reinterpret_cast<wq::dd*>(base + L.recip));
   wq::k_points<<<(nqp + tb - 1) / tb, tb, 0, s>>>(A);
   wq::k_qranges<<<((int)n + tb - 1) / tb, tb, 0, s>>>(A);
   wq::k_basis_points<<<(nqp + tb - 1) / tb, tb, 0, s>>>(A);
   wq::k_gauss_basis<<<(n_el * (p + 1) + tb - 1) / tb, tb, 0, s>>>(A);
   wq::k_integrals<<<((int)n * (2 * p + 1) + tb - 1) / tb, tb, 0, s>>>(A);
   wq::k_rules<<<dim3((unsigned)n, 4, 1), 32, 0, s>>>(A);
-  wq::count_launch(7);
+  wq::count_launch(8);
   WQ_CUDA_TRY(cudaGetLastError(), "rule kernels");
   int h_err = 0;
   WQ_CUDA_TRY(cudaMemcpyAsync(&h_err, err, sizeof(int), cudaMemcpyDeviceToHost, s), "error word read");

@@ -64,7 +64,20 @@ struct StagedArgs {
   void* T3;               // Real [nnz1_3][NT][nqp1][nqp2]
   void* G;                // Real [nnz1_3][NG][nqp1][nnz1_2]
   void* vals;
+  // Mixed precision only: an FP64 copy of G at the q1 points that the first and
+  // last P+1 rows of direction 1 read (q1 < nbl and q1 >= hstart), and the FP64
+  // direction-1 tables, so that stage 1 runs those rows in FP64.
+  double* Gb;             // NULL or double [nnz1_3][NG][nbq][nnz1_2]
+  const double* w1d;      // double [4][n1][NQ]
+  const double* bt1d;     // double [2][n1][NQ]
+  int nbl, hstart, nbq;
 };
+
+// position of point q1 in the FP64 edge copy of G (in range for every q1 that a
+// first or last P+1 row of direction 1 reads; clamped for any other q1)
+__device__ __forceinline__ int edge_row(int q1, int nbl, int hstart, int nbq) {
+  return q1 < nbl ? q1 : min(nbq - 1, max(nbl, q1 - hstart + nbl));
+}
 
 template <typename Real>
 __device__ __forceinline__ const Real* tab(const void* p) { return reinterpret_cast<const Real*>(p); }
@@ -165,8 +178,9 @@ __global__ void __launch_bounds__(128) k_stage3(StagedArgs A) {
 // (t, j2) pattern; rows next to the boundary loop over the support overlaps.
 // Regular rows: threads run over (i2 in [r_lo, r_hi), then q1), neighbouring
 // threads sharing q2 points. Boundary rows [0, r_lo) and [r_hi, n2): threads run
-// over (q1, then the row), so every lane has work.
-template <int P, bool MASS, typename Real, bool REG>
+// over (the row, then q1), so every lane has work and the rows of one side read
+// neighbouring q2 and write neighbouring band pairs.
+template <int P, bool MASS, typename Real, bool REG, typename GOut>
 __global__ void __launch_bounds__(128) k_stage2(StagedArgs A, int r_lo, int r_hi) {
   constexpr int BW = 2 * P + 1;
   constexpr int NT = MASS ? 1 : 9;
@@ -192,8 +206,8 @@ __global__ void __launch_bounds__(128) k_stage2(StagedArgs A, int r_lo, int r_hi
   } else {
     const int nb = r_lo + (D2.n - r_hi);
     if (e >= (int64_t)nb * nq1) return;
-    q1 = (int)(e % nq1);
-    const int b = (int)(e / nq1);
+    const int b = (int)(e % nb);
+    q1 = (int)(e / nb);
     i2 = b < r_lo ? b : r_hi + (b - r_lo);
   }
   const int64_t nnz2 = A.nnz1[1];
@@ -249,27 +263,80 @@ __global__ void __launch_bounds__(128) k_stage2(StagedArgs A, int r_lo, int r_hi
       }
     }
   }
-  Real* G = reinterpret_cast<Real*>(A.G);
+  GOut* G = reinterpret_cast<GOut*>(A.G);
   const int64_t pbase = D2.prefix[i2];
 #pragma unroll
   for (int g = 0; g < NG; ++g) {
-    Real* dst = G + ((p3 * NG + g) * nq1 + q1) * nnz2 + pbase;
+    GOut* dst = G + ((p3 * NG + g) * nq1 + q1) * nnz2 + pbase;
 #pragma unroll
     for (int tt = 0; tt < BW; ++tt) {
       const int j2 = i2 - P + tt;
-      if (REG || (j2 >= jlo && j2 <= jhi)) dst[j2 - jlo] = acc[g][tt];
+      if (REG || (j2 >= jlo && j2 <= jhi)) dst[j2 - jlo] = (GOut)acc[g][tt];
     }
+  }
+  if (sizeof(GOut) < sizeof(Real) && A.Gb && (q1 < A.nbl || q1 >= A.hstart)) {
+    const int qb = edge_row(q1, A.nbl, A.hstart, A.nbq);
+#pragma unroll
+    for (int g = 0; g < NG; ++g) {
+      double* dst = A.Gb + ((p3 * NG + g) * A.nbq + qb) * nnz2 + pbase;
+#pragma unroll
+      for (int tt = 0; tt < BW; ++tt) {
+        const int j2 = i2 - P + tt;
+        if (REG || (j2 >= jlo && j2 <= jhi)) dst[j2 - jlo] = (double)acc[g][tt];
+      }
+    }
+  }
+}
+
+// Stage 1 for a first or last P+1 row of direction 1: Q_i1 is not the regular
+// 2P+1 window and the band is clipped. G points at (p3, group 0, row 0, p2);
+// MAPQ maps q1 into the FP64 edge copy. out + base + j1 is the value of column j1.
+template <int P, bool MASS, typename T, typename OutT, bool MAPQ>
+__device__ __forceinline__ void stage1_edge(const T* G, int64_t gstride, int64_t nnz2, const T* w, int64_t wk,
+                                            const T* bt1, int64_t bder, const Dir& D1, int i1, int n1, int NQ,
+                                            int nbl, int hstart, int nbq, OutT* out, int64_t base) {
+  constexpr int BW = 2 * P + 1;
+  constexpr int MAXQ = 4 * P + 1;
+  const int qi1 = D1.q0[i1], ni1 = D1.nq[i1];
+  T h0[MAXQ], h1[MAXQ];
+  for (int t = 0; t < ni1; ++t) {
+    const int qr = MAPQ ? edge_row(qi1 + t, nbl, hstart, nbq) : qi1 + t;
+    const T* gq = G + (int64_t)qr * nnz2;
+    if (MASS) {
+      h0[t] = w[t] * gq[0];
+    } else {
+      h0[t] = fmaR<T>(w[t], gq[0], w[t + 2 * wk] * gq[2 * gstride]);
+      h1[t] = fmaR<T>(w[t + wk], gq[gstride], w[t + 3 * wk] * gq[3 * gstride]);
+    }
+  }
+#pragma unroll
+  for (int tt = 0; tt < BW; ++tt) {
+    const int j1 = i1 - P + tt;
+    if (j1 < 0 || j1 >= n1) continue;
+    const int qj = D1.q0[j1];
+    const int lo = max(qi1, qj), hi = min(qi1 + ni1, qj + D1.nq[j1]);
+    const int64_t brow = (int64_t)j1 * NQ - qj;
+    T v = (T)0;
+    for (int q = lo; q < hi; ++q) {
+      if (MASS)
+        v = fmaR<T>(bt1[brow + q], h0[q - qi1], v);
+      else
+        v = fmaR<T>(bt1[brow + q + bder], h1[q - qi1], fmaR<T>(bt1[brow + q], h0[q - qi1], v));
+    }
+    out[base + j1] = (OutT)v;
   }
 }
 
 // K1: one thread per (p2, i1, p3): the 2P+1 values of row (i1, i2, i3) in the
 // column block (j2, j3). A block covers 32 consecutive p2 and 4 consecutive i1, so
 // the G rows of overlapping supports are read from L1.
-template <int P, bool MASS, typename Real, typename OutT>
+// EDGE64: the first and last P+1 rows of direction 1 run in FP64 from the edge
+// copy of G (mixed precision), where the large, sign-alternating WQ weights near
+// the boundary amplify FP32 rounding.
+template <int P, bool MASS, typename Real, typename OutT, bool EDGE64>
 __global__ void __launch_bounds__(128) k_stage1(StagedArgs A) {
   constexpr int BW = 2 * P + 1;
   constexpr int NG = MASS ? 1 : 4;
-  constexpr int MAXQ = 4 * P + 1;
   const Dir& D1 = A.d[0];
   const Dir& D2 = A.d[1];
   const Dir& D3 = A.d[2];
@@ -281,7 +348,7 @@ __global__ void __launch_bounds__(128) k_stage1(StagedArgs A) {
   if (p2 >= nnz2 || i1 >= n1) return;
   const int i2 = D2.pair_row[p2], j2 = blo(i2, P) + (int)(p2 - D2.prefix[i2]);
   const int i3 = D3.pair_row[p3], j3 = blo(i3, P) + (int)(p3 - D3.prefix[i3]);
-  const int qi1 = D1.q0[i1], ni1 = D1.nq[i1];
+  const int qi1 = D1.q0[i1];
   const bool reg = i1 >= P + 1 && i1 <= n1 - P - 2;
   const Real* G = reinterpret_cast<const Real*>(A.G) + ((p3 * NG) * nq1) * nnz2 + p2;
   const int64_t gstride = (int64_t)nq1 * nnz2;  // next group
@@ -323,33 +390,13 @@ __global__ void __launch_bounds__(128) k_stage1(StagedArgs A) {
     }
 #pragma unroll
     for (int tt = 0; tt < BW; ++tt) out[base + tt] = (OutT)s[tt];  // j1 - jlo1 = tt for regular rows
+  } else if (EDGE64 && A.Gb) {
+    const double* Gd = A.Gb + ((p3 * NG) * A.nbq) * nnz2 + p2;
+    stage1_edge<P, MASS, double, OutT, true>(Gd, (int64_t)A.nbq * nnz2, nnz2, A.w1d + (size_t)i1 * NQ, wk, A.bt1d,
+                                             bder, D1, i1, n1, NQ, A.nbl, A.hstart, A.nbq, out, base - jlo1);
   } else {
-    Real h0[MAXQ], h1[MAXQ];
-    for (int t = 0; t < ni1; ++t) {
-      const Real* gq = G + (int64_t)(qi1 + t) * nnz2;
-      if (MASS) {
-        h0[t] = w[t] * gq[0];
-      } else {
-        h0[t] = fmaR<Real>(w[t], gq[0], w[t + 2 * wk] * gq[2 * gstride]);
-        h1[t] = fmaR<Real>(w[t + wk], gq[gstride], w[t + 3 * wk] * gq[3 * gstride]);
-      }
-    }
-#pragma unroll
-    for (int tt = 0; tt < BW; ++tt) {
-      const int j1 = i1 - P + tt;
-      if (j1 < 0 || j1 >= n1) continue;
-      const int qj = D1.q0[j1];
-      const int lo = max(qi1, qj), hi = min(qi1 + ni1, qj + D1.nq[j1]);
-      const int64_t brow = (int64_t)j1 * NQ - qj;
-      Real v = (Real)0;
-      for (int q = lo; q < hi; ++q) {
-        if (MASS)
-          v = fmaR<Real>(bt1[brow + q], h0[q - qi1], v);
-        else
-          v = fmaR<Real>(bt1[brow + q + bder], h1[q - qi1], fmaR<Real>(bt1[brow + q], h0[q - qi1], v));
-      }
-      out[base + (j1 - jlo1)] = (OutT)v;
-    }
+    stage1_edge<P, MASS, Real, OutT, false>(G, gstride, nnz2, w, wk, bt1, bder, D1, i1, n1, NQ, 0, 0, 0, out,
+                                            base - jlo1);
   }
 }
 
@@ -362,10 +409,9 @@ __global__ void k_pair_rows(const int64_t* __restrict__ prefix, int n, int* __re
 }  // namespace
 
 // Scratch of the staged path, allocated on first use and owned by the plan.
-static wq_status staged_scratch(wq_plan_s* pl, bool mass, size_t real_size, cudaStream_t s) {
-  const int NT = mass ? 1 : 9, NG = mass ? 1 : 4;
-  const size_t t3 = std::max<size_t>(16, (size_t)pl->nnz1[2] * NT * pl->nqp[0] * pl->nqp[1] * real_size);
-  const size_t g = std::max<size_t>(16, (size_t)pl->nnz1[2] * NG * pl->nqp[0] * pl->nnz1[1] * real_size);
+static wq_status staged_scratch(wq_plan_s* pl, size_t t3, size_t g, size_t gb, bool need_f32, cudaStream_t s) {
+  t3 = std::max<size_t>(16, t3);
+  g = std::max<size_t>(16, g);
   if (pl->stg_a_bytes < t3 || pl->stg_b_bytes < g) {
     if (pl->stg_a) cudaFree(pl->stg_a);
     if (pl->stg_b) cudaFree(pl->stg_b);
@@ -382,11 +428,23 @@ static wq_status staged_scratch(wq_plan_s* pl, bool mass, size_t real_size, cuda
     pl->stg_a_bytes = t3;
     pl->stg_b_bytes = g;
   }
+  if (pl->stg_c_bytes < gb) {
+    if (pl->stg_c) cudaFree(pl->stg_c);
+    pl->stg_c = nullptr;
+    pl->stg_c_bytes = 0;
+    cudaError_t e = cudaMalloc(&pl->stg_c, gb);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      pl->stg_c = nullptr;
+      return set_error(WQ_ERR_OOM, "staged assembly scratch (FP64 edge copy of G) does not fit in device memory");
+    }
+    pl->stg_c_bytes = gb;
+  }
   if (!pl->coefT) {
     cudaError_t e = cudaMalloc(&pl->coefT, sizeof(double) * 8 * (size_t)pl->n_qp_total);
     if (e != cudaSuccess) return wq::cuda_error(e, "transposed coefficient allocation");
   }
-  if (real_size == sizeof(float))
+  if (need_f32)
     for (int l = 0; l < 3; ++l)
       if (!pl->dir[l].tab32) {
         const size_t nt = (size_t)6 * pl->dir[l].n * pl->nq_max;  // 4 rule kinds + 2 basis tables
@@ -403,36 +461,64 @@ static wq_status staged_scratch(wq_plan_s* pl, bool mass, size_t real_size, cuda
   return WQ_OK;
 }
 
-template <int P, bool MASS, typename Real, typename OutT>
+// The q1 points that the first and last p+1 rows of direction 1 read: [0, nbl) and
+// [hstart, nqp) (Q_i = points inside the support of B_i; the whole range when the
+// two ends meet).
+static void edge_points(const wq_plan_s* pl, int* nbl, int* hstart, int* nbq) {
+  const int p = pl->p, ne = pl->dir[0].n_el, nqp = (int)pl->nqp[0], n1 = (int)pl->n[0];
+  const int il = std::min(p, n1 - 1), ih = std::max(n1 - p - 1, 0);
+  const int hi = std::min(ne, il + 1), lo = std::max(0, ih - p);
+  *nbl = (hi == ne ? nqp - 1 : 2 * hi + p - 2) + 1;
+  *hstart = lo == 0 ? 0 : 2 * lo + p;
+  if (*hstart <= *nbl) *nbl = *hstart = nqp;
+  *nbq = *nbl + (nqp - *hstart);
+}
+
+// Real: arithmetic of stages 3 and 2 (and T3); R1: arithmetic of stage 1 (and G).
+template <int P, bool MASS, typename Real, typename R1, typename OutT>
 static wq_status staged_t(wq_plan_s* pl, const double* kappa, void* vals, cudaStream_t s) {
-  wq_status st = staged_scratch(pl, MASS, sizeof(Real), s);
+  const int NT = MASS ? 1 : 9, NG = MASS ? 1 : 4;
+  constexpr bool EDGE64 = sizeof(R1) < sizeof(Real);
+  int nbl = 0, hstart = 0, nbq = 0;
+  if (EDGE64) edge_points(pl, &nbl, &hstart, &nbq);
+  wq_status st = staged_scratch(pl, (size_t)pl->nnz1[2] * NT * pl->nqp[0] * pl->nqp[1] * sizeof(Real),
+                                (size_t)pl->nnz1[2] * NG * pl->nqp[0] * pl->nnz1[1] * sizeof(R1),
+                                (size_t)pl->nnz1[2] * NG * nbq * pl->nnz1[1] * sizeof(double),
+                                sizeof(Real) == sizeof(float) || sizeof(R1) == sizeof(float), s);
   if (st != WQ_OK) return st;
-  StagedArgs A;
-  const bool f32 = sizeof(Real) == sizeof(float);
+  StagedArgs A, A1;  // A: tables in Real (stages 3, 2); A1: tables in R1 (stage 1)
   for (int l = 0; l < 3; ++l) {
     const DirData& d = pl->dir[l];
-    const void* w = d.w;
-    const void* bt = d.bt;
-    if (f32) {
+    const void* w32 = d.w;
+    const void* bt32 = d.bt;
+    if (sizeof(Real) == sizeof(float) || sizeof(R1) == sizeof(float)) {
       const int64_t nw = (int64_t)4 * d.n * pl->nq_max, nb = (int64_t)2 * d.n * pl->nq_max;
       k_to_float<<<(unsigned)((nw + 255) / 256), 256, 0, s>>>(d.w, d.tab32, nw);
       k_to_float<<<(unsigned)((nb + 255) / 256), 256, 0, s>>>(d.bt, d.tab32 + nw, nb);
       count_launch(2);
-      w = d.tab32;
-      bt = d.tab32 + nw;
+      w32 = d.tab32;
+      bt32 = d.tab32 + nw;
     }
-    A.d[l] = Dir{d.n, d.nqp, d.q0, d.nq, w, bt, d.prefix, d.pair_row};
-    A.nnz1[l] = pl->nnz1[l];
+    const bool f = sizeof(Real) == sizeof(float), f1 = sizeof(R1) == sizeof(float);
+    A.d[l] = Dir{d.n, d.nqp, d.q0, d.nq, f ? w32 : d.w, f ? bt32 : d.bt, d.prefix, d.pair_row};
+    A1.d[l] = Dir{d.n, d.nqp, d.q0, d.nq, f1 ? w32 : d.w, f1 ? bt32 : d.bt, d.prefix, d.pair_row};
+    A.nnz1[l] = A1.nnz1[l] = pl->nnz1[l];
   }
-  A.NQ = pl->nq_max;
+  A.NQ = A1.NQ = pl->nq_max;
   const int nq1 = (int)pl->nqp[0], nq2 = (int)pl->nqp[1], nq3 = (int)pl->nqp[2];
   const int64_t NQP = pl->n_qp_total;
   Real* cT = reinterpret_cast<Real*>(pl->coefT);
-  A.cT = cT;
-  A.kappaT = kappa ? cT + 7 * NQP : nullptr;
-  A.T3 = pl->stg_a;
-  A.G = pl->stg_b;
-  A.vals = vals;
+  A.cT = A1.cT = cT;
+  A.kappaT = A1.kappaT = kappa ? cT + 7 * NQP : nullptr;
+  A.T3 = A1.T3 = pl->stg_a;
+  A.G = A1.G = pl->stg_b;
+  A.vals = A1.vals = vals;
+  A.Gb = A1.Gb = EDGE64 ? reinterpret_cast<double*>(pl->stg_c) : nullptr;
+  A.w1d = A1.w1d = pl->dir[0].w;
+  A.bt1d = A1.bt1d = pl->dir[0].bt;
+  A.nbl = A1.nbl = nbl;
+  A.hstart = A1.hstart = hstart;
+  A.nbq = A1.nbq = nbq;
   // transposed coefficients (the slots this matrix uses) and kappa, in Real
   {
     dim3 blk(32, 8), grd((nq1 + 31) / 32, (nq2 + 31) / 32, 7 * nq3 + (kappa ? nq3 : 0));
@@ -444,42 +530,50 @@ static wq_status staged_t(wq_plan_s* pl, const double* kappa, void* vals, cudaSt
   if (r_hi <= r_lo) r_lo = r_hi = n2;   // no regular rows: every row takes the boundary path
   const int64_t np3 = pl->nnz1[2];
   if (r_hi > r_lo)
-    k_stage2<P, MASS, Real, true>
+    k_stage2<P, MASS, Real, true, R1>
         <<<dim3((unsigned)(((int64_t)(r_hi - r_lo) * nq1 + 127) / 128), (unsigned)np3), 128, 0, s>>>(A, r_lo, r_hi);
   const int nb = r_lo + (n2 - r_hi);
-  k_stage2<P, MASS, Real, false><<<dim3((unsigned)(((int64_t)nb * nq1 + 127) / 128), (unsigned)np3), 128, 0, s>>>(
+  k_stage2<P, MASS, Real, false, R1><<<dim3((unsigned)(((int64_t)nb * nq1 + 127) / 128), (unsigned)np3), 128, 0, s>>>(
       A, r_lo, r_hi);
-  k_stage1<P, MASS, Real, OutT>
-      <<<dim3((unsigned)((pl->nnz1[1] + 31) / 32), (n1 + 3) / 4, (unsigned)np3), dim3(32, 4), 0, s>>>(A);
+  k_stage1<P, MASS, R1, OutT, EDGE64>
+      <<<dim3((unsigned)((pl->nnz1[1] + 31) / 32), (n1 + 3) / 4, (unsigned)np3), dim3(32, 4), 0, s>>>(A1);
   count_launch(r_hi > r_lo ? 5 : 4);
   WQ_CUDA_TRY(cudaGetLastError(), "staged assembly launch");
   return WQ_OK;
 }
 
-template <bool MASS, typename Real, typename OutT>
+template <bool MASS, typename Real, typename R1, typename OutT>
 static wq_status staged_dispatch(wq_plan_s* pl, const double* kappa, void* vals, cudaStream_t s) {
   switch (pl->p) {
-    case 2: return staged_t<2, MASS, Real, OutT>(pl, kappa, vals, s);
-    case 3: return staged_t<3, MASS, Real, OutT>(pl, kappa, vals, s);
-    case 4: return staged_t<4, MASS, Real, OutT>(pl, kappa, vals, s);
-    case 5: return staged_t<5, MASS, Real, OutT>(pl, kappa, vals, s);
-    case 6: return staged_t<6, MASS, Real, OutT>(pl, kappa, vals, s);
-    case 7: return staged_t<7, MASS, Real, OutT>(pl, kappa, vals, s);
-    case 8: return staged_t<8, MASS, Real, OutT>(pl, kappa, vals, s);
+    case 2: return staged_t<2, MASS, Real, R1, OutT>(pl, kappa, vals, s);
+    case 3: return staged_t<3, MASS, Real, R1, OutT>(pl, kappa, vals, s);
+    case 4: return staged_t<4, MASS, Real, R1, OutT>(pl, kappa, vals, s);
+    case 5: return staged_t<5, MASS, Real, R1, OutT>(pl, kappa, vals, s);
+    case 6: return staged_t<6, MASS, Real, R1, OutT>(pl, kappa, vals, s);
+    case 7: return staged_t<7, MASS, Real, R1, OutT>(pl, kappa, vals, s);
+    case 8: return staged_t<8, MASS, Real, R1, OutT>(pl, kappa, vals, s);
     default: return set_error(WQ_ERR_UNSUPPORTED, "degree out of range");
   }
 }
 
 wq_status launch_staged(wq_plan_s* pl, bool mass, const double* kappa, void* vals, int value_dtype, int precision,
                         cudaStream_t s) {
+  const bool v32 = value_dtype == WQ_VALUES_F32;
   if (precision == WQ_PREC_FP64)
-    return mass ? staged_dispatch<true, double, double>(pl, kappa, vals, s)
-                : staged_dispatch<false, double, double>(pl, kappa, vals, s);
-  if (value_dtype == WQ_VALUES_F32)
-    return mass ? staged_dispatch<true, float, float>(pl, kappa, vals, s)
-                : staged_dispatch<false, float, float>(pl, kappa, vals, s);
-  return mass ? staged_dispatch<true, float, double>(pl, kappa, vals, s)
-              : staged_dispatch<false, float, double>(pl, kappa, vals, s);
+    return mass ? staged_dispatch<true, double, double, double>(pl, kappa, vals, s)
+                : staged_dispatch<false, double, double, double>(pl, kappa, vals, s);
+  if (precision == WQ_PREC_MIXED) {
+    if (v32)
+      return mass ? staged_dispatch<true, double, float, float>(pl, kappa, vals, s)
+                  : staged_dispatch<false, double, float, float>(pl, kappa, vals, s);
+    return mass ? staged_dispatch<true, double, float, double>(pl, kappa, vals, s)
+                : staged_dispatch<false, double, float, double>(pl, kappa, vals, s);
+  }
+  if (v32)
+    return mass ? staged_dispatch<true, float, float, float>(pl, kappa, vals, s)
+                : staged_dispatch<false, float, float, float>(pl, kappa, vals, s);
+  return mass ? staged_dispatch<true, float, float, double>(pl, kappa, vals, s)
+              : staged_dispatch<false, float, float, double>(pl, kappa, vals, s);
 }
 
 }  // namespace wq

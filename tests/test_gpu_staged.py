@@ -76,3 +76,20 @@ def test_staged_fp32(wq):
     rows = sample_rows(plan.n, plan.p, 120, seed=5)
     worst = check_rows(orc, plan, S, "stiffness", rows, tol=2e-6)
     print(f"staged fp32: worst row-relative error {worst:.3e}")
+
+
+@pytest.mark.parametrize("p", [2, 3, 4, 5, 6, 8])
+@pytest.mark.parametrize("which", ["stiffness", "mass"])
+def test_staged_mixed_precision(wq, p, which):
+    """FP64 for the q3 and q2 mode products, FP32 for the q1 one: 1e-6 row-relative."""
+    patch = perturbed_cube(p, (2 * p + 5, p + 4, p + 3), seed=40 + p)
+    plan = wq.Plan(patch.p, patch.knots, patch.ctrl)
+    kappa = random_field(int(np.prod(plan.n_qp)), seed=90 + p, kind="positive")
+    fn = plan.stiffness if which == "stiffness" else plan.mass
+    S = fn(kappa=torch.as_tensor(kappa, device="cuda"), precision="mixed", dtype=torch.float32)
+    torch.cuda.synchronize()
+    orc = Oracle3D(patch.p, patch.knots, patch.ctrl, kappa=kappa)
+    rows = sample_rows(plan.n, plan.p, 80, seed=600 + p)
+    worst = check_rows(orc, plan, S, which, rows, tol=1e-6)
+    print(f"mixed p={p} {which}: worst row-relative error {worst:.3e}")
+    plan.close()
