@@ -82,6 +82,12 @@ __device__ __forceinline__ int edge_row(int q1, int nbl, int hstart, int nbq) {
 template <typename Real>
 __device__ __forceinline__ const Real* tab(const void* p) { return reinterpret_cast<const Real*>(p); }
 
+// Loads of data that no kernel of the launch writes (tables, T3 in stage 2, G in
+// stage 1) go through the read-only path, so the compiler may move them across
+// the kernel's own stores.
+template <typename T>
+__device__ __forceinline__ T ro(const T* p) { return __ldg(p); }
+
 __global__ void k_to_float(const double* __restrict__ in, float* __restrict__ out, int64_t n) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i < n) out[i] = (float)in[i];
@@ -193,6 +199,8 @@ __global__ void __launch_bounds__(128) k_stage2(StagedArgs A, int r_lo, int r_hi
   constexpr int cls_terms[6][2] = {{0, -1}, {1, -1}, {2, -1}, {3, 6}, {4, 7}, {5, 8}};
   constexpr int cls_group[6] = {3, 2, 2, 1, 0, 0};
   constexpr int cls_b2[6] = {0, 1, 0, 0, 1, 0};
+  constexpr bool cls_first[6] = {true, true, false, true, true, false};
+  constexpr bool cls_last[6] = {true, false, true, true, false, true};
   const Dir& D2 = A.d[1];
   const int nq1 = A.d[0].nqp, nq2 = D2.nqp, NQ = A.NQ;
   const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -215,13 +223,15 @@ __global__ void __launch_bounds__(128) k_stage2(StagedArgs A, int r_lo, int r_hi
   const int64_t tstride = (int64_t)nq1 * nq2;
   const int qi = D2.q0[i2], ni = REG ? BW : D2.nq[i2];
   const int jlo = blo(i2, P), jhi = min(D2.n - 1, i2 + P);
-  Real acc[NG][BW];
-#pragma unroll
-  for (int g = 0; g < NG; ++g)
-#pragma unroll
-    for (int tt = 0; tt < BW; ++tt) acc[g][tt] = (Real)0;
+  const int64_t pbase = D2.prefix[i2];
+  // classes come grouped by G group (g3 | g2 g2 | g1 | g0 g0): one group's
+  // accumulators are live at a time, zeroed at its first class, stored after its last
+  Real acc[BW];
 #pragma unroll
   for (int c = 0; c < NC; ++c) {
+    if (MASS || cls_first[c])
+#pragma unroll
+      for (int tt = 0; tt < BW; ++tt) acc[tt] = (Real)0;
     Real h[REG ? BW : MAXQ];
 #pragma unroll
     for (int t = 0; t < (REG ? BW : MAXQ); ++t) h[t] = (Real)0;
@@ -235,9 +245,9 @@ __global__ void __launch_bounds__(128) k_stage2(StagedArgs A, int r_lo, int r_hi
       const Real* trow = T3 + term * tstride + qi;
       if (REG) {
 #pragma unroll
-        for (int t = 0; t < BW; ++t) h[t] = fmaR<Real>(wrow[t], trow[t], h[t]);
+        for (int t = 0; t < BW; ++t) h[t] = fmaR<Real>(ro(wrow + t), ro(trow + t), h[t]);
       } else {
-        for (int t = 0; t < ni; ++t) h[t] = fmaR<Real>(wrow[t], trow[t], h[t]);
+        for (int t = 0; t < ni; ++t) h[t] = fmaR<Real>(ro(wrow + t), ro(trow + t), h[t]);
       }
     }
     const int g = MASS ? 0 : cls_group[c];
@@ -249,7 +259,7 @@ __global__ void __launch_bounds__(128) k_stage2(StagedArgs A, int r_lo, int r_hi
         const Real* brow = tab<Real>(D2.bt) + ((size_t)b2 * D2.n + j2) * NQ + (qi - D2.q0[j2]);
 #pragma unroll
         for (int t = 0; t < BW; ++t)
-          if (t >= 2 * tt - 2 * P && t <= 2 * tt) acc[g][tt] = fmaR<Real>(brow[t], h[t], acc[g][tt]);
+          if (t >= 2 * tt - 2 * P && t <= 2 * tt) acc[tt] = fmaR<Real>(ro(brow + t), h[t], acc[tt]);
       }
     } else {
 #pragma unroll
@@ -259,30 +269,23 @@ __global__ void __launch_bounds__(128) k_stage2(StagedArgs A, int r_lo, int r_hi
         const int qj = D2.q0[j2];
         const int lo = max(qi, qj), hi = min(qi + ni, qj + D2.nq[j2]);
         const Real* brow = tab<Real>(D2.bt) + ((size_t)b2 * D2.n + j2) * NQ;
-        for (int q = lo; q < hi; ++q) acc[g][tt] = fmaR<Real>(brow[q - qj], h[q - qi], acc[g][tt]);
+        for (int q = lo; q < hi; ++q) acc[tt] = fmaR<Real>(ro(brow + (q - qj)), h[q - qi], acc[tt]);
       }
     }
-  }
-  GOut* G = reinterpret_cast<GOut*>(A.G);
-  const int64_t pbase = D2.prefix[i2];
-#pragma unroll
-  for (int g = 0; g < NG; ++g) {
-    GOut* dst = G + ((p3 * NG + g) * nq1 + q1) * nnz2 + pbase;
-#pragma unroll
-    for (int tt = 0; tt < BW; ++tt) {
-      const int j2 = i2 - P + tt;
-      if (REG || (j2 >= jlo && j2 <= jhi)) dst[j2 - jlo] = (GOut)acc[g][tt];
-    }
-  }
-  if (sizeof(GOut) < sizeof(Real) && A.Gb && (q1 < A.nbl || q1 >= A.hstart)) {
-    const int qb = edge_row(q1, A.nbl, A.hstart, A.nbq);
-#pragma unroll
-    for (int g = 0; g < NG; ++g) {
-      double* dst = A.Gb + ((p3 * NG + g) * A.nbq + qb) * nnz2 + pbase;
+    if (MASS || cls_last[c]) {
+      GOut* dst = reinterpret_cast<GOut*>(A.G) + ((p3 * NG + g) * nq1 + q1) * nnz2 + pbase;
 #pragma unroll
       for (int tt = 0; tt < BW; ++tt) {
         const int j2 = i2 - P + tt;
-        if (REG || (j2 >= jlo && j2 <= jhi)) dst[j2 - jlo] = (double)acc[g][tt];
+        if (REG || (j2 >= jlo && j2 <= jhi)) dst[j2 - jlo] = (GOut)acc[tt];
+      }
+      if (sizeof(GOut) < sizeof(Real) && A.Gb && (q1 < A.nbl || q1 >= A.hstart)) {
+        double* dd = A.Gb + ((p3 * NG + g) * A.nbq + edge_row(q1, A.nbl, A.hstart, A.nbq)) * nnz2 + pbase;
+#pragma unroll
+        for (int tt = 0; tt < BW; ++tt) {
+          const int j2 = i2 - P + tt;
+          if (REG || (j2 >= jlo && j2 <= jhi)) dd[j2 - jlo] = (double)acc[tt];
+        }
       }
     }
   }
@@ -325,6 +328,219 @@ __device__ __forceinline__ void stage1_edge(const T* G, int64_t gstride, int64_t
     }
     out[base + j1] = (OutT)v;
   }
+}
+
+// K2 on the regular rows of direction 2 (Q_i2 = [2 i2 - P, 2 i2 + P]), with the
+// rule and B-spline tables of the block's rows in shared memory: lanes run over
+// 32 consecutive rows i2 (so the T3 reads of a warp are contiguous), the four
+// warps over pairs of q1, and the tables are read from shared memory instead of one cache
+// line per lane. Bs holds B_j2 of the trial rows i0-P .. i0+31+P aligned to the
+// regular pattern: Bs[b][j2 - i0 + P][u] is B^(b)_j2 at point 2 j2 - P + u.
+template <int P, bool MASS, typename Real, typename GOut>
+__global__ void __launch_bounds__(128) k_stage2_reg(StagedArgs A, int r_lo, int r_hi) {
+  constexpr int BW = 2 * P + 1;
+  constexpr int NT = MASS ? 1 : 9;
+  constexpr int NG = MASS ? 1 : 4;
+  constexpr int NC = MASS ? 1 : 6;
+  constexpr int NK = MASS ? 1 : 4;   // rule kinds
+  constexpr int NB = MASS ? 1 : 2;   // trial kinds
+  constexpr int RW = 32;             // rows per block
+  constexpr int NJS = RW + 2 * P;    // trial rows per block
+  constexpr int cls_terms[6][2] = {{0, -1}, {1, -1}, {2, -1}, {3, 6}, {4, 7}, {5, 8}};
+  constexpr int cls_group[6] = {3, 2, 2, 1, 0, 0};
+  constexpr int cls_b2[6] = {0, 1, 0, 0, 1, 0};
+  constexpr bool cls_first[6] = {true, true, false, true, true, false};
+  constexpr bool cls_last[6] = {true, false, true, true, false, true};
+  __shared__ Real Ws[NK][RW][BW];
+  __shared__ Real Bs[NB][NJS][BW];
+  const Dir& D2 = A.d[1];
+  const int nq1 = A.d[0].nqp, nq2 = D2.nqp, NQ = A.NQ, n2 = D2.n;
+  const int i0 = r_lo + blockIdx.x * RW;
+  const int64_t p3 = blockIdx.y;
+  const int lane = threadIdx.x, warp = threadIdx.y, tid = warp * 32 + lane;
+  for (int e = tid; e < NK * RW * BW; e += 128) {
+    const int t = e % BW, r = (e / BW) % RW, k = e / (BW * RW);
+    const int i2 = i0 + r;
+    Ws[k][r][t] = i2 < r_hi ? ro(tab<Real>(D2.w) + ((size_t)k * n2 + i2) * NQ + t) : (Real)0;
+  }
+  for (int e = tid; e < NB * NJS * BW; e += 128) {
+    const int u = e % BW, jr = (e / BW) % NJS, b = e / (BW * NJS);
+    const int j2 = i0 - P + jr;
+    Real v = (Real)0;
+    if (j2 >= 0 && j2 < n2) {
+      const int idx = u + 2 * j2 - P - D2.q0[j2];
+      if (idx >= 0 && idx < D2.nq[j2]) v = ro(tab<Real>(D2.bt) + ((size_t)b * n2 + j2) * NQ + idx);
+    }
+    Bs[b][jr][u] = v;
+  }
+  __syncthreads();
+  const int i2 = i0 + lane;
+  if (i2 >= r_hi) return;
+  const int64_t nnz2 = A.nnz1[1];
+  const int64_t pbase = D2.prefix[i2];
+  const int64_t tstride = (int64_t)nq1 * nq2;
+  const Real* T3p = reinterpret_cast<const Real*>(A.T3) + (p3 * NT) * tstride + (2 * i2 - P);
+  // volatile views: the compiler would otherwise hoist all of the row's table
+  // values out of the q1 loop into registers and spill
+  const volatile Real* Wv = &Ws[0][lane][0];
+  const volatile Real* Bv = &Bs[0][lane][0];
+  // two q1 points per iteration: every shared-memory value feeds two FMA chains
+#pragma unroll 1
+  for (int qa = 2 * warp; qa < nq1; qa += 8) {
+    const int qb = min(qa + 1, nq1 - 1);  // the last iteration may repeat qa
+    const Real* Ta = T3p + (int64_t)qa * nq2;
+    const Real* Tb = T3p + (int64_t)qb * nq2;
+    Real acc[2][BW];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      if (MASS || cls_first[c])
+#pragma unroll
+        for (int tt = 0; tt < BW; ++tt) acc[0][tt] = acc[1][tt] = (Real)0;
+      Real h[2][BW];
+#pragma unroll
+      for (int t = 0; t < BW; ++t) h[0][t] = h[1][t] = (Real)0;
+#pragma unroll
+      for (int k = 0; k < 2; ++k) {
+        const int term = MASS ? 0 : cls_terms[c][k];
+        if (term < 0 || (MASS && k > 0)) continue;
+        const int l = MASS ? 0 : term / 3, m = MASS ? 0 : term % 3;
+        const int k2 = MASS ? 0 : 2 * (l == 1) + (m == 1);
+#pragma unroll
+        for (int t = 0; t < BW; ++t) {
+          const Real wv = Wv[k2 * RW * BW + t];
+          h[0][t] = fmaR<Real>(wv, ro(Ta + term * tstride + t), h[0][t]);
+          h[1][t] = fmaR<Real>(wv, ro(Tb + term * tstride + t), h[1][t]);
+        }
+      }
+      const int g = MASS ? 0 : cls_group[c];
+      const int b2 = MASS ? 0 : cls_b2[c];
+#pragma unroll
+      for (int tt = 0; tt < BW; ++tt)
+#pragma unroll
+        for (int t = 0; t < BW; ++t)
+          if (t >= 2 * tt - 2 * P && t <= 2 * tt) {
+            const Real bv = Bv[(b2 * NJS + tt) * BW + t - 2 * tt + 2 * P];
+            acc[0][tt] = fmaR<Real>(bv, h[0][t], acc[0][tt]);
+            acc[1][tt] = fmaR<Real>(bv, h[1][t], acc[1][tt]);
+          }
+      if (MASS || cls_last[c]) {
+#pragma unroll
+        for (int v = 0; v < 2; ++v) {
+          const int q1 = v ? qb : qa;
+          if (v && qb == qa) break;
+          GOut* dst = reinterpret_cast<GOut*>(A.G) + ((p3 * NG + g) * nq1 + q1) * nnz2 + pbase;
+#pragma unroll
+          for (int tt = 0; tt < BW; ++tt) dst[tt] = (GOut)acc[v][tt];
+          if (sizeof(GOut) < sizeof(Real) && A.Gb && (q1 < A.nbl || q1 >= A.hstart)) {
+            double* dd = A.Gb + ((p3 * NG + g) * A.nbq + edge_row(q1, A.nbl, A.hstart, A.nbq)) * nnz2 + pbase;
+#pragma unroll
+            for (int tt = 0; tt < BW; ++tt) dd[tt] = (double)acc[v][tt];
+          }
+        }
+      }
+    }
+  }
+}
+
+// Compile-time point patterns of the first and last P+1 rows of a direction
+// (valid when the direction has n_el >= 2P+2 spans, so that the two ends do not
+// meet). Row R from the low end (H = false) or the high end (H = true) has
+// NI = 2R+P+1 points and NJ = R+P+1 band members j = jlo + jj; the overlap of Q_i
+// and Q_j is t in [e_tlo, e_thi) relative to the first point of Q_i, and
+// B_j at that point is entry t + e_toff of its table row.
+__host__ __device__ constexpr int e_ni(int P, int R) { return 2 * R + P + 1; }
+__host__ __device__ constexpr int e_nj(int P, int R) { return R + P + 1; }
+__host__ __device__ constexpr int e_s(int P, int R, int jj) { return R + P - jj; }
+__host__ __device__ constexpr int e_tlo(int P, int R, bool H, int jj) {
+  return !H ? (jj <= P ? 0 : 2 * jj - P)
+            : (e_ni(P, R) - 2 * e_s(P, R, jj) - P - 1 > 0 ? e_ni(P, R) - 2 * e_s(P, R, jj) - P - 1 : 0);
+}
+__host__ __device__ constexpr int e_thi(int P, int R, bool H, int jj) {
+  return !H ? (2 * jj + P + 1 < e_ni(P, R) ? 2 * jj + P + 1 : e_ni(P, R))
+            : e_ni(P, R) - (e_s(P, R, jj) <= P ? 0 : 2 * e_s(P, R, jj) - P);
+}
+__host__ __device__ constexpr int e_toff(int P, int R, bool H, int jj) {
+  return !H ? -(jj <= P ? 0 : 2 * jj - P) : -e_ni(P, R) + 2 * e_s(P, R, jj) + P + 1;
+}
+
+// Stage 2 for edge row R of direction 2 (i2 = R or n2-1-R) at point q1 of pair p3.
+template <int P, bool MASS, typename Real, typename GOut, int R, bool H>
+__device__ __forceinline__ void stage2_edge_row(const StagedArgs& A, int q1, int64_t p3) {
+  constexpr int NT = MASS ? 1 : 9;
+  constexpr int NG = MASS ? 1 : 4;
+  constexpr int NC = MASS ? 1 : 6;
+  constexpr int NI = e_ni(P, R), NJ = e_nj(P, R);
+  constexpr int cls_terms[6][2] = {{0, -1}, {1, -1}, {2, -1}, {3, 6}, {4, 7}, {5, 8}};
+  constexpr int cls_group[6] = {3, 2, 2, 1, 0, 0};
+  constexpr int cls_b2[6] = {0, 1, 0, 0, 1, 0};
+  constexpr bool cls_first[6] = {true, true, false, true, true, false};
+  constexpr bool cls_last[6] = {true, false, true, true, false, true};
+  const Dir& D2 = A.d[1];
+  const int nq1 = A.d[0].nqp, nq2 = D2.nqp, NQ = A.NQ, n2 = D2.n;
+  const int i2 = H ? n2 - 1 - R : R;
+  const int qi = H ? nq2 - NI : 0;
+  const int jlo = H ? n2 - 1 - R - P : 0;
+  const int64_t nnz2 = A.nnz1[1];
+  const Real* T3 = reinterpret_cast<const Real*>(A.T3) + ((p3 * NT) * nq1 + q1) * (int64_t)nq2 + qi;
+  const int64_t tstride = (int64_t)nq1 * nq2;
+  const int64_t pbase = D2.prefix[i2];
+  Real acc[NJ];  // one G group at a time (classes come grouped)
+#pragma unroll
+  for (int c = 0; c < NC; ++c) {
+    if (MASS || cls_first[c])
+#pragma unroll
+      for (int jj = 0; jj < NJ; ++jj) acc[jj] = (Real)0;
+    Real h[NI];
+#pragma unroll
+    for (int t = 0; t < NI; ++t) h[t] = (Real)0;
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      const int term = MASS ? 0 : cls_terms[c][k];
+      if (term < 0 || (MASS && k > 0)) continue;
+      const int l = MASS ? 0 : term / 3, m = MASS ? 0 : term % 3;
+      const int k2 = MASS ? 0 : 2 * (l == 1) + (m == 1);
+      const Real* wrow = tab<Real>(D2.w) + ((size_t)k2 * n2 + i2) * NQ;
+      const Real* trow = T3 + term * tstride;
+#pragma unroll
+      for (int t = 0; t < NI; ++t) h[t] = fmaR<Real>(ro(wrow + t), ro(trow + t), h[t]);
+    }
+    const int g = MASS ? 0 : cls_group[c];
+    const int b2 = MASS ? 0 : cls_b2[c];
+#pragma unroll
+    for (int jj = 0; jj < NJ; ++jj) {
+      const Real* brow = tab<Real>(D2.bt) + ((size_t)b2 * n2 + jlo + jj) * NQ + e_toff(P, R, H, jj);
+#pragma unroll
+      for (int t = e_tlo(P, R, H, jj); t < e_thi(P, R, H, jj); ++t)
+        acc[jj] = fmaR<Real>(ro(brow + t), h[t], acc[jj]);
+    }
+    if (MASS || cls_last[c]) {
+      GOut* dst = reinterpret_cast<GOut*>(A.G) + ((p3 * NG + g) * nq1 + q1) * nnz2 + pbase;
+#pragma unroll
+      for (int jj = 0; jj < NJ; ++jj) dst[jj] = (GOut)acc[jj];
+      if (sizeof(GOut) < sizeof(Real) && A.Gb && (q1 < A.nbl || q1 >= A.hstart)) {
+        double* dd = A.Gb + ((p3 * NG + g) * A.nbq + edge_row(q1, A.nbl, A.hstart, A.nbq)) * nnz2 + pbase;
+#pragma unroll
+        for (int jj = 0; jj < NJ; ++jj) dd[jj] = (double)acc[jj];
+      }
+    }
+  }
+}
+
+// K2 on one edge row of direction 2 (R from the low or the high end) with its
+// compile-time point pattern; threads over q1, so a warp shares one pattern. One
+// instantiation per edge row keeps each row's registers to itself.
+template <int P, bool MASS, typename Real, typename GOut, int R, bool H>
+__global__ void __launch_bounds__(128) k_stage2_edge(StagedArgs A) {
+  const int q1 = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q1 >= A.d[0].nqp) return;
+  stage2_edge_row<P, MASS, Real, GOut, R, H>(A, q1, (int64_t)blockIdx.y);
+}
+
+template <int P, bool MASS, typename Real, typename GOut, int B = 0>
+static void launch_stage2_edge(const StagedArgs& A, int nq1, int64_t np3, cudaStream_t s) {
+  k_stage2_edge<P, MASS, Real, GOut, (B <= P ? B : B - P - 1), (B > P)>
+      <<<dim3((unsigned)((nq1 + 127) / 128), (unsigned)np3), 128, 0, s>>>(A);
+  if constexpr (B + 1 < 2 * P + 2) launch_stage2_edge<P, MASS, Real, GOut, B + 1>(A, nq1, np3, s);
 }
 
 // K1: one thread per (p2, i1, p3): the 2P+1 values of row (i1, i2, i3) in the
@@ -529,15 +745,27 @@ static wq_status staged_t(wq_plan_s* pl, const double* kappa, void* vals, cudaSt
   int r_lo = P + 1, r_hi = n2 - P - 1;  // regular rows [r_lo, r_hi)
   if (r_hi <= r_lo) r_lo = r_hi = n2;   // no regular rows: every row takes the boundary path
   const int64_t np3 = pl->nnz1[2];
-  if (r_hi > r_lo)
+  // Regular rows: k_stage2_reg (tables in shared memory, 32 rows per block) unless
+  // the FP64 pipe, not L1, bounds the flat mapping (FP64, P <= 4: measured at 97%
+  // of the DFMA rate) and 32-row blocks would leave more than 4% of lanes idle.
+  const int nreg = r_hi - r_lo;
+  const bool flat = sizeof(Real) == sizeof(double) && P <= 4 && 32 * ((nreg + 31) / 32) * 100 > 104 * nreg;
+  if (nreg > 0 && flat)
     k_stage2<P, MASS, Real, true, R1>
-        <<<dim3((unsigned)(((int64_t)(r_hi - r_lo) * nq1 + 127) / 128), (unsigned)np3), 128, 0, s>>>(A, r_lo, r_hi);
+        <<<dim3((unsigned)(((int64_t)nreg * nq1 + 127) / 128), (unsigned)np3), 128, 0, s>>>(A, r_lo, r_hi);
+  else if (nreg > 0)
+    k_stage2_reg<P, MASS, Real, R1>
+        <<<dim3((unsigned)((nreg + 31) / 32), (unsigned)np3), dim3(32, 4), 0, s>>>(A, r_lo, r_hi);
   const int nb = r_lo + (n2 - r_hi);
-  k_stage2<P, MASS, Real, false, R1><<<dim3((unsigned)(((int64_t)nb * nq1 + 127) / 128), (unsigned)np3), 128, 0, s>>>(
-      A, r_lo, r_hi);
+  const bool edge2 = pl->dir[1].n_el >= 2 * P + 2;  // edge rows with compile-time patterns
+  if (edge2)
+    launch_stage2_edge<P, MASS, Real, R1>(A, nq1, np3, s);
+  else
+    k_stage2<P, MASS, Real, false, R1>
+        <<<dim3((unsigned)(((int64_t)nb * nq1 + 127) / 128), (unsigned)np3), 128, 0, s>>>(A, r_lo, r_hi);
   k_stage1<P, MASS, R1, OutT, EDGE64>
       <<<dim3((unsigned)((pl->nnz1[1] + 31) / 32), (n1 + 3) / 4, (unsigned)np3), dim3(32, 4), 0, s>>>(A1);
-  count_launch(r_hi > r_lo ? 5 : 4);
+  count_launch(3 + (r_hi > r_lo ? 1 : 0) + (edge2 ? 2 * P + 2 : 1));
   WQ_CUDA_TRY(cudaGetLastError(), "staged assembly launch");
   return WQ_OK;
 }

@@ -93,3 +93,33 @@ def test_staged_mixed_precision(wq, p, which):
     worst = check_rows(orc, plan, S, which, rows, tol=1e-6)
     print(f"mixed p={p} {which}: worst row-relative error {worst:.3e}")
     plan.close()
+
+
+def _edge_rows(n, p):
+    """Every row whose direction-2 index is within p+1 of an end, crossed with a
+    few direction-1 and direction-3 indices (ends, p, n-p-1, middle)."""
+    def picks(m):
+        return sorted({0, min(p, m - 1), m // 2, max(0, m - p - 1), m - 1})
+    e2 = [i for i in range(n[1]) if i <= p or i >= n[1] - p - 1]
+    return np.array([(i3 * n[1] + i2) * n[0] + i1 for i3 in picks(n[2]) for i2 in e2 for i1 in picks(n[0])])
+
+
+@pytest.mark.parametrize("p", [2, 3, 4, 5, 6, 8])
+@pytest.mark.parametrize("extra", [0, 1])
+def test_staged_edge_rows_compile_time_patterns(wq, p, extra):
+    """Direction 2 with n_el = 2p+2 (+1): the first and last p+1 rows take the
+    kernels with compile-time point patterns; FP64 stiffness, FP64 mass with a
+    coefficient field, and mixed-precision stiffness against the oracle."""
+    patch = perturbed_cube(p, (3, 2 * p + 2 + extra, 2), seed=70 + p + extra)
+    plan = wq.Plan(patch.p, patch.knots, patch.ctrl)
+    kappa = random_field(int(np.prod(plan.n_qp)), seed=80 + p, kind="positive")
+    rows = _edge_rows(plan.n, p)
+    S = plan.stiffness()
+    M = plan.mass(kappa=torch.as_tensor(kappa, device="cuda"))
+    X = plan.stiffness(precision="mixed", dtype=torch.float32)
+    torch.cuda.synchronize()
+    tol = TOL_F64_P8 if p == 8 else TOL_F64
+    check_rows(Oracle3D(patch.p, patch.knots, patch.ctrl), plan, S, "stiffness", rows, tol=tol)
+    check_rows(Oracle3D(patch.p, patch.knots, patch.ctrl, kappa=kappa), plan, M, "mass", rows, tol=tol)
+    check_rows(Oracle3D(patch.p, patch.knots, patch.ctrl), plan, X, "stiffness", rows, tol=1e-6)
+    plan.close()
