@@ -32,6 +32,24 @@ sys.path.insert(0, ROOT)
 
 METRIC = "WQ 3D stiffness nnz/s and % of HBM-write roofline; mixed vs FP64 at ≤1e-6 error"
 
+# DRAM traffic of one FP64 staged stiffness assembly (k_stage3, k_stage2 and its
+# edge-row kernels, k_stage1) at p = 4, 64^3, from one ncu capture of
+# dram__bytes_read.sum + dram__bytes_write.sum (profiles/assembly_traffic_p4_nel64.md).
+# It is reported only while the kernel sources still hash to the captured value.
+TRAFFIC_CAPTURE = {"p": 4, "n_el": 64, "bytes": 3987.36e6 + 4339.13e6, "sources": "601eafef47817690",
+                   "files": ("paper_1605_01238_gb300/csrc/wq_staged.cu", "paper_1605_01238_gb300/csrc/wq_internal.h")}
+
+
+def captured_traffic(p: int, n_el: int):
+    import hashlib
+    if (p, n_el) != (TRAFFIC_CAPTURE["p"], TRAFFIC_CAPTURE["n_el"]):
+        return None
+    h = hashlib.sha256()
+    for f in TRAFFIC_CAPTURE["files"]:
+        with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), f), "rb") as fh:
+            h.update(fh.read())
+    return TRAFFIC_CAPTURE["bytes"] if h.hexdigest()[:16] == TRAFFIC_CAPTURE["sources"] else None
+
 
 def peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
@@ -391,8 +409,11 @@ def run_ours(args):
                    "l2": "no flush: each step writes 2.5 GB (values + columns) > 126 MB L2",
                    "parallelism": f"{world} independent patches, one per GPU"},
         "roofline": {"bound": "alu", "achieved": achieved_tf, "peak": peak_tf, "unit": "TFLOP/s",
-                     "frac": achieved_tf / peak_tf, "traffic": None,
-                     "kernel": f"k_assemble<{p},stiffness,fp64> ({args.algo})",
+                     "frac": achieved_tf / peak_tf,
+                     "traffic": captured_traffic(p, args.nel) if args.algo in ("auto", "staged") else None,
+                     "kernel": (f"wq_assemble_stiffness, FP64, p={p}: k_stage3, k_stage2 (regular rows + "
+                                f"{2 * p + 2} edge-row kernels), k_stage1" if args.algo in ("auto", "staged")
+                                else f"k_assemble<{p},stiffness,fp64> (fused)"),
                      "flops_per_launch": flops,
                      "note": f"FP64 FMA pipe: {fpn:.1f} algorithmic flop/nnz (exact census of the factorisation "
                              f"for this mesh); peak = 152 SMs x 2 DFMA/clk "
