@@ -346,50 +346,62 @@ __global__ void k_rules(DirArgs3 A) {
     G[ss][rr] = acc;
   }
   __syncwarp();
-  if (kb == 1 && lane == 0) {
-    dd tr = dd_make(0.0), un = dd_make(0.0);
-    for (int rr = 0; rr < m; ++rr) {
-      tr = dd_add(tr, G[rr][rr]);
-      double u = 1.0 / scale[rr];  // exact: scale is a power of two
-      un = dd_add(un, dd_mul_d(dd_make(u), u));
+  if (kb == 1) {  // G += sigma u u^T, u = D^{-1} 1 (the left null vector of the scaled system)
+    __shared__ dd sig_s;
+    if (lane == 0) {
+      dd tr = dd_make(0.0), un = dd_make(0.0);
+      for (int rr = 0; rr < m; ++rr) {
+        tr = dd_add(tr, G[rr][rr]);
+        double u = 1.0 / scale[rr];  // exact: scale is a power of two
+        un = dd_add(un, dd_mul_d(dd_make(u), u));
+      }
+      sig_s = dd_div(tr, dd_mul_d(un, (double)m));
     }
-    dd sig = dd_div(tr, dd_mul_d(un, (double)m));
-    for (int rr = 0; rr < m; ++rr)
-      for (int ss = 0; ss < m; ++ss)
-        G[rr][ss] = dd_add(G[rr][ss], dd_mul_d(dd_mul_d(sig, 1.0 / scale[rr]), 1.0 / scale[ss]));
+    __syncwarp();
+    const dd sig = sig_s;
+    for (int e = lane; e < m * m; e += 32) {
+      const int rr = e / m, ss = e % m;
+      G[rr][ss] = dd_add(G[rr][ss], dd_mul_d(dd_mul_d(sig, 1.0 / scale[rr]), 1.0 / scale[ss]));
+    }
   }
   __syncwarp();
-  // LDL^T, column by column; L stored in the strict lower triangle of G.
+  // Right-looking LDL^T: at column c every lane updates part of the trailing block.
+  // L is stored in the strict lower triangle of G, D in Dg.
   double gmax = 0.0;
   for (int rr = 0; rr < m; ++rr) gmax = fmax(gmax, G[rr][rr].hi);
+  __shared__ dd col[kMaxI];
   for (int c = 0; c < m; ++c) {
+    const dd d = G[c][c];
     if (lane == 0) {
-      dd d = G[c][c];
-      for (int k = 0; k < c; ++k) d = dd_sub(d, dd_mul(dd_mul(G[c][k], G[c][k]), Dg[k]));
       Dg[c] = d;
       if (!(d.hi > 1e-28 * gmax)) bad = 1;
     }
+    for (int rr = c + 1 + lane; rr < m; rr += 32) col[rr] = G[rr][c];
     __syncwarp();
-    for (int rr = c + 1 + lane; rr < m; rr += 32) {
-      dd v = G[rr][c];
-      for (int k = 0; k < c; ++k) v = dd_sub(v, dd_mul(dd_mul(G[rr][k], G[c][k]), Dg[k]));
-      G[rr][c] = dd_div(v, Dg[c]);
+    for (int rr = c + 1 + lane; rr < m; rr += 32) G[rr][c] = dd_div(col[rr], d);
+    __syncwarp();
+    const int t = m - c - 1;  // trailing block (c, m) x (c, m), lower triangle
+    for (int e = lane; e < t * t; e += 32) {
+      const int rr = c + 1 + e / t, ss = c + 1 + e % t;
+      if (ss <= rr) G[rr][ss] = dd_sub(G[rr][ss], dd_mul(G[rr][c], col[ss]));
     }
     __syncwarp();
   }
-  if (lane == 0) {
-    if (bad) atomicOr(a.err, kErrSingularRule);
-    for (int rr = 0; rr < m; ++rr) {  // L z = r
-      dd v = r[rr];
-      for (int k = 0; k < rr; ++k) v = dd_sub(v, dd_mul(G[rr][k], y[k]));
-      y[rr] = v;
-    }
-    for (int rr = 0; rr < m; ++rr) y[rr] = dd_div(y[rr], Dg[rr]);
-    for (int rr = m - 1; rr >= 0; --rr) {  // L^T y = z / D
-      dd v = y[rr];
-      for (int k = rr + 1; k < m; ++k) v = dd_sub(v, dd_mul(G[k][rr], y[k]));
-      y[rr] = v;
-    }
+  if (lane == 0 && bad) atomicOr(a.err, kErrSingularRule);
+  // L z = r, z /= D, L^T y = z: column by column, rows in parallel
+  for (int rr = lane; rr < m; rr += 32) y[rr] = r[rr];
+  __syncwarp();
+  for (int k = 0; k < m; ++k) {
+    const dd yk = y[k];
+    for (int rr = k + 1 + lane; rr < m; rr += 32) y[rr] = dd_sub(y[rr], dd_mul(G[rr][k], yk));
+    __syncwarp();
+  }
+  for (int rr = lane; rr < m; rr += 32) y[rr] = dd_div(y[rr], Dg[rr]);
+  __syncwarp();
+  for (int k = m - 1; k > 0; --k) {
+    const dd yk = y[k];
+    for (int rr = lane; rr < k; rr += 32) y[rr] = dd_sub(y[rr], dd_mul(G[k][rr], yk));
+    __syncwarp();
   }
   __syncwarp();
   double* wout = a.w + ((size_t)kind * a.n + i) * a.nq_stride;

@@ -527,19 +527,21 @@ __device__ __forceinline__ void stage2_edge_row(const StagedArgs& A, int q1, int
 }
 
 // K2 on one edge row of direction 2 (R from the low or the high end) with its
-// compile-time point pattern; threads over q1, so a warp shares one pattern. One
-// instantiation per edge row keeps each row's registers to itself.
+// compile-time point pattern; threads over (p3, q1), so a warp shares one pattern
+// and every lane has work. One instantiation per edge row keeps each row's
+// registers to itself.
 template <int P, bool MASS, typename Real, typename GOut, int R, bool H>
-__global__ void __launch_bounds__(128) k_stage2_edge(StagedArgs A) {
-  const int q1 = blockIdx.x * blockDim.x + threadIdx.x;
-  if (q1 >= A.d[0].nqp) return;
-  stage2_edge_row<P, MASS, Real, GOut, R, H>(A, q1, (int64_t)blockIdx.y);
+__global__ void __launch_bounds__(128) k_stage2_edge(StagedArgs A, int64_t np3) {
+  const int nq1 = A.d[0].nqp;
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;  // p3 * nq1 + q1
+  if (e >= np3 * nq1) return;
+  stage2_edge_row<P, MASS, Real, GOut, R, H>(A, (int)(e % nq1), e / nq1);
 }
 
 template <int P, bool MASS, typename Real, typename GOut, int B = 0>
 static void launch_stage2_edge(const StagedArgs& A, int nq1, int64_t np3, cudaStream_t s) {
   k_stage2_edge<P, MASS, Real, GOut, (B <= P ? B : B - P - 1), (B > P)>
-      <<<dim3((unsigned)((nq1 + 127) / 128), (unsigned)np3), 128, 0, s>>>(A);
+      <<<(unsigned)((np3 * nq1 + 127) / 128), 128, 0, s>>>(A, np3);
   if constexpr (B + 1 < 2 * P + 2) launch_stage2_edge<P, MASS, Real, GOut, B + 1>(A, nq1, np3, s);
 }
 
