@@ -61,8 +61,10 @@ enum { WQ_VALUES_F64 = 0, WQ_VALUES_F32 = 1 };
 enum {
   WQ_PREC_FP64 = 0,          /* FP64 FMA throughout */
   WQ_PREC_FP32 = 1,          /* FP32 FMA, FP32 intermediates */
-  WQ_PREC_MIXED = 2          /* FP64 for the first two mode products (contracting q3, q2),
+  WQ_PREC_MIXED = 2,         /* FP64 for the first two mode products (contracting q3, q2),
                                 FP32 for the last one (q1, half of the work); staged only */
+  WQ_PREC_F32X2 = 3          /* double-float: every value a pair of floats (~48 significant
+                                bits), all three mode products on the FP32 pipe; staged only */
 };
 
 /* ---- plan ------------------------------------------------------------------
@@ -125,7 +127,8 @@ wq_status wq_plan_refresh(wq_plan_t plan, const double* ctrl, int ctrl_on_device
  *            (Eq. (mass2): c absorbs the PDE coefficient)
  *   d_vals   device array of nnz values of type value_dtype, caller-owned
  *   value_dtype  WQ_VALUES_F64 or WQ_VALUES_F32
- *   precision    WQ_PREC_FP64 (requires WQ_VALUES_F64), WQ_PREC_FP32 or WQ_PREC_MIXED
+ *   precision    WQ_PREC_FP64 (requires WQ_VALUES_F64), WQ_PREC_FP32, WQ_PREC_MIXED or
+ *                WQ_PREC_F32X2
  * Asynchronous on `stream`; no allocation, no synchronisation. */
 wq_status wq_assemble_stiffness(wq_plan_t plan, const double* d_kappa, void* d_vals,
                                 int value_dtype, int precision, void* stream);

@@ -18,8 +18,8 @@ from ._lib import WqError, check, load
 __all__ = ["Plan", "Batch", "bilinear", "WqError", "launch_count", "load", "VALUES_F64", "VALUES_F32", "PREC_FP64", "PREC_FP32"]
 
 VALUES_F64, VALUES_F32 = 0, 1
-PREC_FP64, PREC_FP32, PREC_MIXED = 0, 1, 2
-_PREC = {"fp64": PREC_FP64, "fp32": PREC_FP32, "mixed": PREC_MIXED}
+PREC_FP64, PREC_FP32, PREC_MIXED, PREC_F32X2 = 0, 1, 2, 3
+_PREC = {"fp64": PREC_FP64, "fp32": PREC_FP32, "mixed": PREC_MIXED, "f32x2": PREC_F32X2}
 
 
 def _torch():

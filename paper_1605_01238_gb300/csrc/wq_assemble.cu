@@ -612,7 +612,8 @@ static wq_status assemble(wq_plan_t plan, bool mass, const double* kappa, void* 
   if (precision == WQ_PREC_FP64 && value_dtype != WQ_VALUES_F64)
     return set_error(WQ_ERR_INVALID_ARG, "FP64 contractions write FP64 values");
   const bool staged = plan->algorithm == WQ_ALGO_STAGED || plan->algorithm == WQ_ALGO_AUTO;
-  if (precision == WQ_PREC_MIXED || ((precision == WQ_PREC_FP64 || precision == WQ_PREC_FP32) && staged))
+  if (precision == WQ_PREC_MIXED || precision == WQ_PREC_F32X2 ||
+      ((precision == WQ_PREC_FP64 || precision == WQ_PREC_FP32) && staged))
     return wq::launch_staged(plan, mass, kappa, vals, value_dtype, precision, s);
   if (precision == WQ_PREC_FP64) return wq::launch_assemble_f64(plan, mass, kappa, (double*)vals, s);
   if (precision == WQ_PREC_FP32) return wq::launch_assemble_f32(plan, mass, kappa, vals, value_dtype, s);

@@ -112,6 +112,7 @@ struct DirData {
   dd* greville = nullptr;    // [n] Greville abscissae (xi_{i+1} + ... + xi_{i+p}) / p
   int* pair_row = nullptr;   // [nnz1] row i of each band pair (staged assembly)
   float* tab32 = nullptr;    // [6][n][NQ] float copies of w and bt (staged FP32 assembly)
+  void* tabf2 = nullptr;     // [6][n][NQ] double-float copies of w and bt (staged F32X2 assembly)
   dd* recip = nullptr;       // [p+1][n+p+1] 1 / (xi_{j+k} - xi_j), double-double
 };
 

@@ -264,15 +264,19 @@ __global__ void k_gauss_basis(DirArgs3 A) {
   }
 }
 
-// I^{(a,b)}_{i,j} for j = i - p + t, all four kinds, by Gauss on the common spans.
+// I^{(a,b)}_{i,j} for j = i - p + t by Gauss on the common spans, one thread per
+// (i, t, kind = 2a + b): the double-double chains are short and spread over many SMs.
 __global__ void k_integrals(DirArgs3 A) {
   const DirArgs& a = A.d[blockIdx.y];
   int id = blockIdx.x * blockDim.x + threadIdx.x;
   const int p = a.p, m = p + 1, bw = 2 * p + 1;
-  if (id >= a.n * bw) return;
-  int i = id / bw, t = id % bw;
-  int j = i - p + t;
-  dd acc[4] = {dd_make(0.0), dd_make(0.0), dd_make(0.0), dd_make(0.0)};
+  if (id >= a.n * bw * 4) return;
+  const int kind = id & 3;
+  id >>= 2;
+  const int i = id / bw, t = id % bw;
+  const int j = i - p + t;
+  const int ta = kind >> 1, tb = kind & 1;
+  dd acc = dd_make(0.0);
   if (j >= 0 && j < a.n) {
     const double* chi = a.knots + p;
     int k0 = max(max(i, j) - p, 0), k1 = min(min(i, j), a.n_el - 1);
@@ -281,18 +285,13 @@ __global__ void k_integrals(DirArgs3 A) {
       half = dd{0.5 * half.hi, 0.5 * half.lo};
       const dd* gbk = a.gb + (size_t)k * m * 2 * m;
       for (int g = 0; g < m; ++g) {
-        dd wg = dd_mul(a.gauss[m + g], half);
         const dd* row = gbk + (size_t)g * 2 * m;
-        dd bi[2] = {row[i - k], row[m + i - k]};
-        dd bj[2] = {row[j - k], row[m + j - k]};
-        for (int ta = 0; ta < 2; ++ta) {
-          dd wi = dd_mul(wg, bi[ta]);
-          for (int tb = 0; tb < 2; ++tb) acc[2 * ta + tb] = dd_add(acc[2 * ta + tb], dd_mul(wi, bj[tb]));
-        }
+        dd wi = dd_mul(dd_mul(a.gauss[m + g], half), row[ta * m + i - k]);
+        acc = dd_add(acc, dd_mul(wi, row[tb * m + j - k]));
       }
     }
   }
-  for (int kind = 0; kind < 4; ++kind) a.integ[((size_t)kind * a.n + i) * bw + t] = acc[kind];
+  a.integ[((size_t)kind * a.n + i) * bw + t] = acc;
 }
 
 // Minimum-norm rule of kind (a,b) for test function i: one warp per system.
@@ -695,9 +694,10 @@ wq_status run_setup(wq_plan_s* pl, cudaStream_t s, bool with_pattern) {
   count_launch(3);
   k_points<<<dim3((max_qp + tb - 1) / tb, 3), tb, 0, s>>>(A);
   k_qranges<<<dim3((max_n + tb - 1) / tb, 3), tb, 0, s>>>(A);
-  k_basis_points<<<dim3((max_qp + tb - 1) / tb, 3), tb, 0, s>>>(A);
-  k_gauss_basis<<<dim3((max_el * (p + 1) + tb - 1) / tb, 3), tb, 0, s>>>(A);
-  k_integrals<<<dim3((max_n * (2 * p + 1) + tb - 1) / tb, 3), tb, 0, s>>>(A);
+  // double-double chains: one warp per block, so the work spreads over the SMs
+  k_basis_points<<<dim3((max_qp + 31) / 32, 3), 32, 0, s>>>(A);
+  k_gauss_basis<<<dim3((max_el * (p + 1) + 31) / 32, 3), 32, 0, s>>>(A);
+  k_integrals<<<dim3((max_n * (2 * p + 1) * 4 + 31) / 32, 3), 32, 0, s>>>(A);
   k_rules<<<dim3(max_n, 4, 3), 32, 0, s>>>(A);
   k_prefix<<<dim3(1, 3), 32, 0, s>>>(A);
   k_greville<<<dim3((max_n + tb - 1) / tb, 3), tb, 0, s>>>(A);
@@ -764,7 +764,7 @@ static void free_plan(wq_plan_s* pl) {
   for (int l = 0; l < 3; ++l) {
     wq::DirData& d = pl->dir[l];
     void* ptrs[] = {d.knots, d.x, d.x_dd, d.first, d.q0, d.nq, d.bt_dd, d.bt, d.bp, d.gb, d.integ, d.w, d.prefix,
-                    d.greville, d.pair_row, d.tab32, d.recip};
+                    d.greville, d.pair_row, d.tab32, d.tabf2, d.recip};
     for (void* q : ptrs)
       if (q) cudaFree(q);
   }
@@ -1137,9 +1137,9 @@ extern "C" wq_status wq_rules_noalloc(int p, int64_t n_knots, const double* h_kn
                                                                 p, (int)n_knots, reinterpret_cast<wq::dd*>(base + L.recip));
   wq::k_points<<<(nqp + tb - 1) / tb, tb, 0, s>>>(A);
   wq::k_qranges<<<((int)n + tb - 1) / tb, tb, 0, s>>>(A);
-  wq::k_basis_points<<<(nqp + tb - 1) / tb, tb, 0, s>>>(A);
-  wq::k_gauss_basis<<<(n_el * (p + 1) + tb - 1) / tb, tb, 0, s>>>(A);
-  wq::k_integrals<<<((int)n * (2 * p + 1) + tb - 1) / tb, tb, 0, s>>>(A);
+  wq::k_basis_points<<<(nqp + 31) / 32, 32, 0, s>>>(A);
+  wq::k_gauss_basis<<<(n_el * (p + 1) + 31) / 32, 32, 0, s>>>(A);
+  wq::k_integrals<<<((int)n * (2 * p + 1) * 4 + 31) / 32, 32, 0, s>>>(A);
   wq::k_rules<<<dim3((unsigned)n, 4, 1), 32, 0, s>>>(A);
   wq::count_launch(8);
   WQ_CUDA_TRY(cudaGetLastError(), "rule kernels");

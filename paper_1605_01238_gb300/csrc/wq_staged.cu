@@ -19,6 +19,7 @@
 // runs over i2 and writes G with the pair index p2 fastest; K1 runs over p2, so
 // neighbouring threads write neighbouring j2 blocks of the same CSR row.
 #include <algorithm>
+#include <type_traits>
 #include <vector>
 
 #include "wq_internal.h"
@@ -32,12 +33,127 @@ __constant__ int sTermM[9] = {0, 1, 2, 0, 1, 2, 0, 1, 2};
 // coefficient slot of each term: c_11 c_12 c_13 c_22 c_23 c_33 (c_lm = c_ml)
 __constant__ int sSlot[9] = {0, 1, 2, 1, 3, 4, 2, 4, 5};
 
+// Stage-2 classes of equal (group, b2), terms ordered as sTerm*:
+// class 0: (0,0) g3 b0; 1: (0,1) g2 b1; 2: (0,2) g2 b0; 3: (1,0),(2,0) g1 b0;
+// 4: (1,1),(2,1) g0 b1; 5: (1,2),(2,2) g0 b0. Classes come grouped by G group
+// (g3 | g2 g2 | g1 | g0 g0): one group's accumulators are live at a time, zeroed
+// at its first class and stored after its last.
+struct ClassInfo {
+  int term[2], g, b2;
+  bool first, last;
+};
+__constant__ ClassInfo sClass[6] = {{{0, -1}, 3, 0, true, true},  {{1, -1}, 2, 1, true, false},
+                                    {{2, -1}, 2, 0, false, true}, {{3, 6}, 1, 0, true, true},
+                                    {{4, 7}, 0, 1, true, false},  {{5, 8}, 0, 0, false, true}};
+
+// Class c: from compile-time tables when the class loop is unrolled (c folds to a
+// constant), from constant memory when it is rolled (double-float, whose ~15
+// instructions per multiply-add would otherwise overflow the instruction cache).
+template <bool ROLL>
+__device__ __forceinline__ ClassInfo class_info(int c) {
+  if (ROLL) return sClass[c];
+  constexpr int terms[6][2] = {{0, -1}, {1, -1}, {2, -1}, {3, 6}, {4, 7}, {5, 8}};
+  constexpr int group[6] = {3, 2, 2, 1, 0, 0};
+  constexpr int b2[6] = {0, 1, 0, 0, 1, 0};
+  constexpr bool first[6] = {true, true, false, true, true, false};
+  constexpr bool last[6] = {true, false, true, true, false, true};
+  return ClassInfo{{terms[c][0], terms[c][1]}, group[c], b2[c], first[c], last[c]};
+}
+
+// Double-float numbers (WQ_PREC_F32X2): value = hi + lo with |lo| <= ulp(hi)/2,
+// about 48 significant bits carried on the FP32 pipe, which GB300 runs at ~60x
+// its FP64 rate. Arithmetic by the error-free transformations of Knuth (two-sum)
+// and Dekker (two-product, here in its FMA form), renormalised by the fast
+// two-sum; the _rn intrinsics keep the compiler from contracting them.
+struct f2 {
+  float hi, lo;
+};
+
+__device__ __forceinline__ f2 f2_renorm(float s, float t) {  // fast two-sum, |s| >= |t|
+  const float hi = __fadd_rn(s, t);
+  return f2{hi, __fsub_rn(t, __fsub_rn(hi, s))};
+}
+
+// a * b + c
+__device__ __forceinline__ f2 f2_fma(f2 a, f2 b, f2 c) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float e = __fmaf_rn(a.hi, b.hi, -p);                         // a.hi b.hi = p + e exactly
+  e = __fmaf_rn(a.hi, b.lo, __fmaf_rn(a.lo, b.hi, e));         // cross terms (a.lo b.lo < 2^-46 |ab|)
+  const float s = __fadd_rn(p, c.hi);                          // two-sum of p and c.hi
+  const float v = __fsub_rn(s, p);
+  float t = __fadd_rn(__fsub_rn(p, __fsub_rn(s, v)), __fsub_rn(c.hi, v));
+  t = __fadd_rn(t, __fadd_rn(e, c.lo));
+  return f2_renorm(s, t);
+}
+
+__device__ __forceinline__ f2 f2_mul(f2 a, f2 b) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float e = __fmaf_rn(a.hi, b.hi, -p);
+  e = __fmaf_rn(a.hi, b.lo, __fmaf_rn(a.lo, b.hi, e));
+  return f2_renorm(p, e);
+}
+
+__device__ __forceinline__ f2 f2_from(double x) {
+  const float hi = __double2float_rn(x);
+  return f2{hi, __double2float_rn(x - (double)hi)};
+}
+
+// Arithmetic of the contractions: Real = double, float or f2.
 template <typename T>
 __device__ __forceinline__ T fmaR(T a, T b, T c);
 template <>
 __device__ __forceinline__ double fmaR<double>(double a, double b, double c) { return fma(a, b, c); }
 template <>
 __device__ __forceinline__ float fmaR<float>(float a, float b, float c) { return fmaf(a, b, c); }
+template <>
+__device__ __forceinline__ f2 fmaR<f2>(f2 a, f2 b, f2 c) { return f2_fma(a, b, c); }
+
+template <typename T>
+__device__ __forceinline__ T mulR(T a, T b) { return a * b; }
+template <>
+__device__ __forceinline__ f2 mulR<f2>(f2 a, f2 b) { return f2_mul(a, b); }
+
+template <typename T>
+__device__ __forceinline__ T zeroR() { return (T)0; }
+template <>
+__device__ __forceinline__ f2 zeroR<f2>() { return f2{0.0f, 0.0f}; }
+
+template <typename T>
+__device__ __forceinline__ T fromD(double x) { return (T)x; }
+template <>
+__device__ __forceinline__ f2 fromD<f2>(double x) { return f2_from(x); }
+
+// float -> double by re-packing the IEEE-754 fields (exact; integer instructions
+// instead of a conversion on the FP64 pipe). Float subnormals (below 1.2e-38)
+// become zero, far below the values' rounding.
+__device__ __forceinline__ double f2d_exact(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned e = (u >> 23) & 0xffu, sign = u & 0x80000000u, m = u & 0x7fffffu;
+  if (e == 0u) return __hiloint2double((int)sign, 0);
+  const unsigned de = e == 0xffu ? 0x7ffu : e + 896u;
+  return __hiloint2double((int)(sign | (de << 20) | (m >> 3)), (int)(m << 29));
+}
+
+template <typename T>
+__device__ __forceinline__ double toD(T x) { return (double)x; }
+template <>
+__device__ __forceinline__ double toD<f2>(f2 x) { return f2d_exact(x.hi) + f2d_exact(x.lo); }
+
+// value in an output / intermediate type O
+template <typename O, typename T>
+__device__ __forceinline__ O toOut(T x) { return (O)x; }
+template <>
+__device__ __forceinline__ double toOut<double, f2>(f2 x) { return toD(x); }
+template <>
+__device__ __forceinline__ float toOut<float, f2>(f2 x) { return __fadd_rn(x.hi, x.lo); }
+template <>
+__device__ __forceinline__ f2 toOut<f2, f2>(f2 x) { return x; }
+
+// read of a volatile shared-memory value
+template <typename T>
+__device__ __forceinline__ T vld(const volatile T* p) { return *p; }
+template <>
+__device__ __forceinline__ f2 vld<f2>(const volatile f2* p) { return f2{p->hi, p->lo}; }
 
 __device__ __forceinline__ int blo(int i, int p) { return i - p > 0 ? i - p : 0; }
 __device__ __forceinline__ int bw(int i, int p, int n) { return min(n - 1, i + p) - blo(i, p) + 1; }
@@ -87,10 +203,20 @@ __device__ __forceinline__ const Real* tab(const void* p) { return reinterpret_c
 // the kernel's own stores.
 template <typename T>
 __device__ __forceinline__ T ro(const T* p) { return __ldg(p); }
+template <>
+__device__ __forceinline__ f2 ro<f2>(const f2* p) {
+  const float2 v = __ldg(reinterpret_cast<const float2*>(p));
+  return f2{v.x, v.y};
+}
 
 __global__ void k_to_float(const double* __restrict__ in, float* __restrict__ out, int64_t n) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i < n) out[i] = (float)in[i];
+}
+
+__global__ void k_to_f2(const double* __restrict__ in, f2* __restrict__ out, int64_t n) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) out[i] = f2_from(in[i]);
 }
 
 // (q1, q2, q3) -> (q3, q1, q2) copy of the coefficient planes (and kappa)
@@ -106,7 +232,7 @@ __global__ void k_transpose_coef(const double* __restrict__ c, const double* __r
   Real* dst = slot < nplanes ? cT + (int64_t)plane * nq1 * nq2 : kT + (int64_t)(plane - nplanes * nq3) * nq1 * nq2;
   for (int k = threadIdx.y; k < 32; k += blockDim.y) {
     const int q2 = by + k, q1 = bx + threadIdx.x;
-    if (q1 < nq1 && q2 < nq2) tile[k][threadIdx.x] = (Real)src[(int64_t)q2 * nq1 + q1];
+    if (q1 < nq1 && q2 < nq2) tile[k][threadIdx.x] = fromD<Real>(src[(int64_t)q2 * nq1 + q1]);
   }
   __syncthreads();
   for (int k = threadIdx.y; k < 32; k += blockDim.y) {
@@ -140,10 +266,10 @@ __global__ void __launch_bounds__(128) k_stage3(StagedArgs A) {
     if (j3 <= jhi && t < ni3) {
       const int loc = qi3 + t - D3.q0[j3];
       if (loc >= 0 && loc < D3.nq[j3])
-        v = (double)tab<Real>(D3.w)[((size_t)k * D3.n + i3) * NQ + t] *
-            (double)tab<Real>(D3.bt)[((size_t)(k & 1) * D3.n + j3) * NQ + loc];
+        v = toD(tab<Real>(D3.w)[((size_t)k * D3.n + i3) * NQ + t]) *
+            toD(tab<Real>(D3.bt)[((size_t)(k & 1) * D3.n + j3) * NQ + loc]);
     }
-    a3[k][jj][t] = (Real)v;
+    a3[k][jj][t] = fromD<Real>(v);
   }
   for (int jj = threadIdx.x; jj < BW; jj += blockDim.x) {
     const int j3 = jlo + jj;
@@ -165,14 +291,14 @@ __global__ void __launch_bounds__(128) k_stage3(StagedArgs A) {
     Real c[MAXQ];
     const Real* cs = tab<Real>(A.cT) + ((int64_t)slot * D3.nqp + qi3) * plane + pt;
     const Real* ks = A.kappaT ? tab<Real>(A.kappaT) + (int64_t)qi3 * plane + pt : nullptr;
-    for (int t = 0; t < ni3; ++t) c[t] = ks ? cs[t * plane] * ks[t * plane] : cs[t * plane];
+    for (int t = 0; t < ni3; ++t) c[t] = ks ? mulR(cs[t * plane], ks[t * plane]) : cs[t * plane];
     for (int term = 0; term < NT; ++term) {
       if (!MASS && sSlot[term] != s) continue;
       const int l = MASS ? 0 : sTermL[term], m = MASS ? 0 : sTermM[term];
       const int k3 = MASS ? 0 : 2 * (l == 2) + (m == 2);
       for (int jj = 0; jj <= jhi - jlo; ++jj) {
         const Real* a = a3[k3][jj];
-        Real acc = (Real)0;
+        Real acc = zeroR<Real>();
         for (int t = olo[jj]; t < ohi[jj]; ++t) acc = fmaR<Real>(a[t], c[t], acc);
         T3[(((p3base + jj) * NT + term) * nq1 + q1) * nq2 + q2] = acc;
       }
@@ -193,14 +319,8 @@ __global__ void __launch_bounds__(128) k_stage2(StagedArgs A, int r_lo, int r_hi
   constexpr int NG = MASS ? 1 : 4;
   constexpr int NC = MASS ? 1 : 6;
   constexpr int MAXQ = 4 * P + 1;
-  // classes: (group, b2, first term, last term) with terms ordered as sTerm*
-  // class 0: (0,0) g3 b0; 1: (0,1) g2 b1; 2: (0,2) g2 b0; 3: (1,0),(2,0) g1 b0;
-  // 4: (1,1),(2,1) g0 b1; 5: (1,2),(2,2) g0 b0
-  constexpr int cls_terms[6][2] = {{0, -1}, {1, -1}, {2, -1}, {3, 6}, {4, 7}, {5, 8}};
-  constexpr int cls_group[6] = {3, 2, 2, 1, 0, 0};
-  constexpr int cls_b2[6] = {0, 1, 0, 0, 1, 0};
-  constexpr bool cls_first[6] = {true, true, false, true, true, false};
-  constexpr bool cls_last[6] = {true, false, true, true, false, true};
+  constexpr bool ROLL = std::is_same<Real, f2>::value;
+  constexpr int CU = ROLL ? 1 : NC;
   const Dir& D2 = A.d[1];
   const int nq1 = A.d[0].nqp, nq2 = D2.nqp, NQ = A.NQ;
   const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -227,17 +347,18 @@ __global__ void __launch_bounds__(128) k_stage2(StagedArgs A, int r_lo, int r_hi
   // classes come grouped by G group (g3 | g2 g2 | g1 | g0 g0): one group's
   // accumulators are live at a time, zeroed at its first class, stored after its last
   Real acc[BW];
-#pragma unroll
+#pragma unroll(CU)
   for (int c = 0; c < NC; ++c) {
-    if (MASS || cls_first[c])
+    const ClassInfo ci = class_info<ROLL>(c);
+    if (MASS || ci.first)
 #pragma unroll
-      for (int tt = 0; tt < BW; ++tt) acc[tt] = (Real)0;
+      for (int tt = 0; tt < BW; ++tt) acc[tt] = zeroR<Real>();
     Real h[REG ? BW : MAXQ];
 #pragma unroll
-    for (int t = 0; t < (REG ? BW : MAXQ); ++t) h[t] = (Real)0;
+    for (int t = 0; t < (REG ? BW : MAXQ); ++t) h[t] = zeroR<Real>();
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
-      const int term = MASS ? 0 : cls_terms[c][k];
+      const int term = MASS ? 0 : ci.term[k];
       if (term < 0 || (MASS && k > 0)) continue;
       const int l = MASS ? 0 : term / 3, m = MASS ? 0 : term % 3;
       const int k2 = MASS ? 0 : 2 * (l == 1) + (m == 1);
@@ -250,8 +371,8 @@ __global__ void __launch_bounds__(128) k_stage2(StagedArgs A, int r_lo, int r_hi
         for (int t = 0; t < ni; ++t) h[t] = fmaR<Real>(ro(wrow + t), ro(trow + t), h[t]);
       }
     }
-    const int g = MASS ? 0 : cls_group[c];
-    const int b2 = MASS ? 0 : cls_b2[c];
+    const int g = MASS ? 0 : ci.g;
+    const int b2 = MASS ? 0 : ci.b2;
     if (REG) {
 #pragma unroll
       for (int tt = 0; tt < BW; ++tt) {
@@ -272,19 +393,19 @@ __global__ void __launch_bounds__(128) k_stage2(StagedArgs A, int r_lo, int r_hi
         for (int q = lo; q < hi; ++q) acc[tt] = fmaR<Real>(ro(brow + (q - qj)), h[q - qi], acc[tt]);
       }
     }
-    if (MASS || cls_last[c]) {
+    if (MASS || ci.last) {
       GOut* dst = reinterpret_cast<GOut*>(A.G) + ((p3 * NG + g) * nq1 + q1) * nnz2 + pbase;
 #pragma unroll
       for (int tt = 0; tt < BW; ++tt) {
         const int j2 = i2 - P + tt;
-        if (REG || (j2 >= jlo && j2 <= jhi)) dst[j2 - jlo] = (GOut)acc[tt];
+        if (REG || (j2 >= jlo && j2 <= jhi)) dst[j2 - jlo] = toOut<GOut>(acc[tt]);
       }
       if (sizeof(GOut) < sizeof(Real) && A.Gb && (q1 < A.nbl || q1 >= A.hstart)) {
         double* dd = A.Gb + ((p3 * NG + g) * A.nbq + edge_row(q1, A.nbl, A.hstart, A.nbq)) * nnz2 + pbase;
 #pragma unroll
         for (int tt = 0; tt < BW; ++tt) {
           const int j2 = i2 - P + tt;
-          if (REG || (j2 >= jlo && j2 <= jhi)) dd[j2 - jlo] = (double)acc[tt];
+          if (REG || (j2 >= jlo && j2 <= jhi)) dd[j2 - jlo] = toD(acc[tt]);
         }
       }
     }
@@ -306,10 +427,10 @@ __device__ __forceinline__ void stage1_edge(const T* G, int64_t gstride, int64_t
     const int qr = MAPQ ? edge_row(qi1 + t, nbl, hstart, nbq) : qi1 + t;
     const T* gq = G + (int64_t)qr * nnz2;
     if (MASS) {
-      h0[t] = w[t] * gq[0];
+      h0[t] = mulR(w[t], gq[0]);
     } else {
-      h0[t] = fmaR<T>(w[t], gq[0], w[t + 2 * wk] * gq[2 * gstride]);
-      h1[t] = fmaR<T>(w[t + wk], gq[gstride], w[t + 3 * wk] * gq[3 * gstride]);
+      h0[t] = fmaR<T>(w[t], gq[0], mulR(w[t + 2 * wk], gq[2 * gstride]));
+      h1[t] = fmaR<T>(w[t + wk], gq[gstride], mulR(w[t + 3 * wk], gq[3 * gstride]));
     }
   }
 #pragma unroll
@@ -319,14 +440,14 @@ __device__ __forceinline__ void stage1_edge(const T* G, int64_t gstride, int64_t
     const int qj = D1.q0[j1];
     const int lo = max(qi1, qj), hi = min(qi1 + ni1, qj + D1.nq[j1]);
     const int64_t brow = (int64_t)j1 * NQ - qj;
-    T v = (T)0;
+    T v = zeroR<T>();
     for (int q = lo; q < hi; ++q) {
       if (MASS)
         v = fmaR<T>(bt1[brow + q], h0[q - qi1], v);
       else
         v = fmaR<T>(bt1[brow + q + bder], h1[q - qi1], fmaR<T>(bt1[brow + q], h0[q - qi1], v));
     }
-    out[base + j1] = (OutT)v;
+    out[base + j1] = toOut<OutT>(v);
   }
 }
 
@@ -346,11 +467,8 @@ __global__ void __launch_bounds__(128) k_stage2_reg(StagedArgs A, int r_lo, int 
   constexpr int NB = MASS ? 1 : 2;   // trial kinds
   constexpr int RW = 32;             // rows per block
   constexpr int NJS = RW + 2 * P;    // trial rows per block
-  constexpr int cls_terms[6][2] = {{0, -1}, {1, -1}, {2, -1}, {3, 6}, {4, 7}, {5, 8}};
-  constexpr int cls_group[6] = {3, 2, 2, 1, 0, 0};
-  constexpr int cls_b2[6] = {0, 1, 0, 0, 1, 0};
-  constexpr bool cls_first[6] = {true, true, false, true, true, false};
-  constexpr bool cls_last[6] = {true, false, true, true, false, true};
+  constexpr bool ROLL = std::is_same<Real, f2>::value;
+  constexpr int CU = ROLL ? 1 : NC;
   __shared__ Real Ws[NK][RW][BW];
   __shared__ Real Bs[NB][NJS][BW];
   const Dir& D2 = A.d[1];
@@ -361,12 +479,12 @@ __global__ void __launch_bounds__(128) k_stage2_reg(StagedArgs A, int r_lo, int 
   for (int e = tid; e < NK * RW * BW; e += 128) {
     const int t = e % BW, r = (e / BW) % RW, k = e / (BW * RW);
     const int i2 = i0 + r;
-    Ws[k][r][t] = i2 < r_hi ? ro(tab<Real>(D2.w) + ((size_t)k * n2 + i2) * NQ + t) : (Real)0;
+    Ws[k][r][t] = i2 < r_hi ? ro(tab<Real>(D2.w) + ((size_t)k * n2 + i2) * NQ + t) : zeroR<Real>();
   }
   for (int e = tid; e < NB * NJS * BW; e += 128) {
     const int u = e % BW, jr = (e / BW) % NJS, b = e / (BW * NJS);
     const int j2 = i0 - P + jr;
-    Real v = (Real)0;
+    Real v = zeroR<Real>();
     if (j2 >= 0 && j2 < n2) {
       const int idx = u + 2 * j2 - P - D2.q0[j2];
       if (idx >= 0 && idx < D2.nq[j2]) v = ro(tab<Real>(D2.bt) + ((size_t)b * n2 + j2) * NQ + idx);
@@ -391,50 +509,51 @@ __global__ void __launch_bounds__(128) k_stage2_reg(StagedArgs A, int r_lo, int 
     const Real* Ta = T3p + (int64_t)qa * nq2;
     const Real* Tb = T3p + (int64_t)qb * nq2;
     Real acc[2][BW];
-#pragma unroll
+#pragma unroll(CU)
     for (int c = 0; c < NC; ++c) {
-      if (MASS || cls_first[c])
+      const ClassInfo ci = class_info<ROLL>(c);
+      if (MASS || ci.first)
 #pragma unroll
-        for (int tt = 0; tt < BW; ++tt) acc[0][tt] = acc[1][tt] = (Real)0;
+        for (int tt = 0; tt < BW; ++tt) acc[0][tt] = acc[1][tt] = zeroR<Real>();
       Real h[2][BW];
 #pragma unroll
-      for (int t = 0; t < BW; ++t) h[0][t] = h[1][t] = (Real)0;
+      for (int t = 0; t < BW; ++t) h[0][t] = h[1][t] = zeroR<Real>();
 #pragma unroll
       for (int k = 0; k < 2; ++k) {
-        const int term = MASS ? 0 : cls_terms[c][k];
+        const int term = MASS ? 0 : ci.term[k];
         if (term < 0 || (MASS && k > 0)) continue;
         const int l = MASS ? 0 : term / 3, m = MASS ? 0 : term % 3;
         const int k2 = MASS ? 0 : 2 * (l == 1) + (m == 1);
 #pragma unroll
         for (int t = 0; t < BW; ++t) {
-          const Real wv = Wv[k2 * RW * BW + t];
+          const Real wv = vld(Wv + k2 * RW * BW + t);
           h[0][t] = fmaR<Real>(wv, ro(Ta + term * tstride + t), h[0][t]);
           h[1][t] = fmaR<Real>(wv, ro(Tb + term * tstride + t), h[1][t]);
         }
       }
-      const int g = MASS ? 0 : cls_group[c];
-      const int b2 = MASS ? 0 : cls_b2[c];
+      const int g = MASS ? 0 : ci.g;
+      const int b2 = MASS ? 0 : ci.b2;
 #pragma unroll
       for (int tt = 0; tt < BW; ++tt)
 #pragma unroll
         for (int t = 0; t < BW; ++t)
           if (t >= 2 * tt - 2 * P && t <= 2 * tt) {
-            const Real bv = Bv[(b2 * NJS + tt) * BW + t - 2 * tt + 2 * P];
+            const Real bv = vld(Bv + (b2 * NJS + tt) * BW + t - 2 * tt + 2 * P);
             acc[0][tt] = fmaR<Real>(bv, h[0][t], acc[0][tt]);
             acc[1][tt] = fmaR<Real>(bv, h[1][t], acc[1][tt]);
           }
-      if (MASS || cls_last[c]) {
+      if (MASS || ci.last) {
 #pragma unroll
         for (int v = 0; v < 2; ++v) {
           const int q1 = v ? qb : qa;
           if (v && qb == qa) break;
           GOut* dst = reinterpret_cast<GOut*>(A.G) + ((p3 * NG + g) * nq1 + q1) * nnz2 + pbase;
 #pragma unroll
-          for (int tt = 0; tt < BW; ++tt) dst[tt] = (GOut)acc[v][tt];
+          for (int tt = 0; tt < BW; ++tt) dst[tt] = toOut<GOut>(acc[v][tt]);
           if (sizeof(GOut) < sizeof(Real) && A.Gb && (q1 < A.nbl || q1 >= A.hstart)) {
             double* dd = A.Gb + ((p3 * NG + g) * A.nbq + edge_row(q1, A.nbl, A.hstart, A.nbq)) * nnz2 + pbase;
 #pragma unroll
-            for (int tt = 0; tt < BW; ++tt) dd[tt] = (double)acc[v][tt];
+            for (int tt = 0; tt < BW; ++tt) dd[tt] = toD(acc[v][tt]);
           }
         }
       }
@@ -470,11 +589,8 @@ __device__ __forceinline__ void stage2_edge_row(const StagedArgs& A, int q1, int
   constexpr int NG = MASS ? 1 : 4;
   constexpr int NC = MASS ? 1 : 6;
   constexpr int NI = e_ni(P, R), NJ = e_nj(P, R);
-  constexpr int cls_terms[6][2] = {{0, -1}, {1, -1}, {2, -1}, {3, 6}, {4, 7}, {5, 8}};
-  constexpr int cls_group[6] = {3, 2, 2, 1, 0, 0};
-  constexpr int cls_b2[6] = {0, 1, 0, 0, 1, 0};
-  constexpr bool cls_first[6] = {true, true, false, true, true, false};
-  constexpr bool cls_last[6] = {true, false, true, true, false, true};
+  constexpr bool ROLL = std::is_same<Real, f2>::value;
+  constexpr int CU = ROLL ? 1 : NC;
   const Dir& D2 = A.d[1];
   const int nq1 = A.d[0].nqp, nq2 = D2.nqp, NQ = A.NQ, n2 = D2.n;
   const int i2 = H ? n2 - 1 - R : R;
@@ -485,17 +601,18 @@ __device__ __forceinline__ void stage2_edge_row(const StagedArgs& A, int q1, int
   const int64_t tstride = (int64_t)nq1 * nq2;
   const int64_t pbase = D2.prefix[i2];
   Real acc[NJ];  // one G group at a time (classes come grouped)
-#pragma unroll
+#pragma unroll(CU)
   for (int c = 0; c < NC; ++c) {
-    if (MASS || cls_first[c])
+    const ClassInfo ci = class_info<ROLL>(c);
+    if (MASS || ci.first)
 #pragma unroll
-      for (int jj = 0; jj < NJ; ++jj) acc[jj] = (Real)0;
+      for (int jj = 0; jj < NJ; ++jj) acc[jj] = zeroR<Real>();
     Real h[NI];
 #pragma unroll
-    for (int t = 0; t < NI; ++t) h[t] = (Real)0;
+    for (int t = 0; t < NI; ++t) h[t] = zeroR<Real>();
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
-      const int term = MASS ? 0 : cls_terms[c][k];
+      const int term = MASS ? 0 : ci.term[k];
       if (term < 0 || (MASS && k > 0)) continue;
       const int l = MASS ? 0 : term / 3, m = MASS ? 0 : term % 3;
       const int k2 = MASS ? 0 : 2 * (l == 1) + (m == 1);
@@ -504,8 +621,8 @@ __device__ __forceinline__ void stage2_edge_row(const StagedArgs& A, int q1, int
 #pragma unroll
       for (int t = 0; t < NI; ++t) h[t] = fmaR<Real>(ro(wrow + t), ro(trow + t), h[t]);
     }
-    const int g = MASS ? 0 : cls_group[c];
-    const int b2 = MASS ? 0 : cls_b2[c];
+    const int g = MASS ? 0 : ci.g;
+    const int b2 = MASS ? 0 : ci.b2;
 #pragma unroll
     for (int jj = 0; jj < NJ; ++jj) {
       const Real* brow = tab<Real>(D2.bt) + ((size_t)b2 * n2 + jlo + jj) * NQ + e_toff(P, R, H, jj);
@@ -513,14 +630,14 @@ __device__ __forceinline__ void stage2_edge_row(const StagedArgs& A, int q1, int
       for (int t = e_tlo(P, R, H, jj); t < e_thi(P, R, H, jj); ++t)
         acc[jj] = fmaR<Real>(ro(brow + t), h[t], acc[jj]);
     }
-    if (MASS || cls_last[c]) {
+    if (MASS || ci.last) {
       GOut* dst = reinterpret_cast<GOut*>(A.G) + ((p3 * NG + g) * nq1 + q1) * nnz2 + pbase;
 #pragma unroll
-      for (int jj = 0; jj < NJ; ++jj) dst[jj] = (GOut)acc[jj];
+      for (int jj = 0; jj < NJ; ++jj) dst[jj] = toOut<GOut>(acc[jj]);
       if (sizeof(GOut) < sizeof(Real) && A.Gb && (q1 < A.nbl || q1 >= A.hstart)) {
         double* dd = A.Gb + ((p3 * NG + g) * A.nbq + edge_row(q1, A.nbl, A.hstart, A.nbq)) * nnz2 + pbase;
 #pragma unroll
-        for (int jj = 0; jj < NJ; ++jj) dd[jj] = (double)acc[jj];
+        for (int jj = 0; jj < NJ; ++jj) dd[jj] = toD(acc[jj]);
       }
     }
   }
@@ -582,17 +699,17 @@ __global__ void __launch_bounds__(128) k_stage1(StagedArgs A) {
   const int64_t bder = (int64_t)n1 * NQ;          // B' table after B
   Real s[BW];
 #pragma unroll
-  for (int tt = 0; tt < BW; ++tt) s[tt] = (Real)0;
+  for (int tt = 0; tt < BW; ++tt) s[tt] = zeroR<Real>();
   if (reg) {
 #pragma unroll
     for (int t = 0; t <= 2 * P; ++t) {
       const Real* gq = G + (int64_t)(qi1 + t) * nnz2;
-      Real h0, h1 = (Real)0;
+      Real h0, h1 = zeroR<Real>();
       if (MASS) {
-        h0 = w[t] * gq[0];
+        h0 = mulR(w[t], gq[0]);
       } else {
-        h0 = fmaR<Real>(w[t], gq[0], w[t + 2 * wk] * gq[2 * gstride]);
-        h1 = fmaR<Real>(w[t + wk], gq[gstride], w[t + 3 * wk] * gq[3 * gstride]);
+        h0 = fmaR<Real>(w[t], gq[0], mulR(w[t + 2 * wk], gq[2 * gstride]));
+        h1 = fmaR<Real>(w[t + wk], gq[gstride], mulR(w[t + 3 * wk], gq[3 * gstride]));
       }
 #pragma unroll
       for (int tt = 0; tt < BW; ++tt) {
@@ -607,7 +724,7 @@ __global__ void __launch_bounds__(128) k_stage1(StagedArgs A) {
       }
     }
 #pragma unroll
-    for (int tt = 0; tt < BW; ++tt) out[base + tt] = (OutT)s[tt];  // j1 - jlo1 = tt for regular rows
+    for (int tt = 0; tt < BW; ++tt) out[base + tt] = toOut<OutT>(s[tt]);  // j1 - jlo1 = tt for regular rows
   } else if (EDGE64 && A.Gb) {
     const double* Gd = A.Gb + ((p3 * NG) * A.nbq) * nnz2 + p2;
     stage1_edge<P, MASS, double, OutT, true>(Gd, (int64_t)A.nbq * nnz2, nnz2, A.w1d + (size_t)i1 * NQ, wk, A.bt1d,
@@ -704,11 +821,27 @@ static wq_status staged_t(wq_plan_s* pl, const double* kappa, void* vals, cudaSt
                                 (size_t)pl->nnz1[2] * NG * nbq * pl->nnz1[1] * sizeof(double),
                                 sizeof(Real) == sizeof(float) || sizeof(R1) == sizeof(float), s);
   if (st != WQ_OK) return st;
+  constexpr bool F2 = std::is_same<Real, f2>::value;
+  static_assert(!F2 || std::is_same<R1, f2>::value, "double-float runs every stage in double-float");
   StagedArgs A, A1;  // A: tables in Real (stages 3, 2); A1: tables in R1 (stage 1)
   for (int l = 0; l < 3; ++l) {
-    const DirData& d = pl->dir[l];
+    DirData& d = pl->dir[l];
     const void* w32 = d.w;
     const void* bt32 = d.bt;
+    if (F2) {
+      const int64_t nw = (int64_t)4 * d.n * pl->nq_max, nb = (int64_t)2 * d.n * pl->nq_max;
+      if (!d.tabf2) {
+        cudaError_t e = cudaMalloc(&d.tabf2, sizeof(f2) * (size_t)(nw + nb));
+        if (e != cudaSuccess) return wq::cuda_error(e, "double-float table allocation");
+      }
+      f2* t = reinterpret_cast<f2*>(d.tabf2);
+      k_to_f2<<<(unsigned)((nw + 255) / 256), 256, 0, s>>>(d.w, t, nw);
+      k_to_f2<<<(unsigned)((nb + 255) / 256), 256, 0, s>>>(d.bt, t + nw, nb);
+      count_launch(2);
+      A.d[l] = A1.d[l] = Dir{d.n, d.nqp, d.q0, d.nq, t, t + nw, d.prefix, d.pair_row};
+      A.nnz1[l] = A1.nnz1[l] = pl->nnz1[l];
+      continue;
+    }
     if (sizeof(Real) == sizeof(float) || sizeof(R1) == sizeof(float)) {
       const int64_t nw = (int64_t)4 * d.n * pl->nq_max, nb = (int64_t)2 * d.n * pl->nq_max;
       k_to_float<<<(unsigned)((nw + 255) / 256), 256, 0, s>>>(d.w, d.tab32, nw);
@@ -751,7 +884,7 @@ static wq_status staged_t(wq_plan_s* pl, const double* kappa, void* vals, cudaSt
   // the FP64 pipe, not L1, bounds the flat mapping (FP64, P <= 4: measured at 97%
   // of the DFMA rate) and 32-row blocks would leave more than 4% of lanes idle.
   const int nreg = r_hi - r_lo;
-  const bool flat = sizeof(Real) == sizeof(double) && P <= 4 && 32 * ((nreg + 31) / 32) * 100 > 104 * nreg;
+  const bool flat = std::is_same<Real, double>::value && P <= 4 && 32 * ((nreg + 31) / 32) * 100 > 104 * nreg;
   if (nreg > 0 && flat)
     k_stage2<P, MASS, Real, true, R1>
         <<<dim3((unsigned)(((int64_t)nreg * nq1 + 127) / 128), (unsigned)np3), 128, 0, s>>>(A, r_lo, r_hi);
@@ -792,6 +925,13 @@ wq_status launch_staged(wq_plan_s* pl, bool mass, const double* kappa, void* val
   if (precision == WQ_PREC_FP64)
     return mass ? staged_dispatch<true, double, double, double>(pl, kappa, vals, s)
                 : staged_dispatch<false, double, double, double>(pl, kappa, vals, s);
+  if (precision == WQ_PREC_F32X2) {
+    if (v32)
+      return mass ? staged_dispatch<true, f2, f2, float>(pl, kappa, vals, s)
+                  : staged_dispatch<false, f2, f2, float>(pl, kappa, vals, s);
+    return mass ? staged_dispatch<true, f2, f2, double>(pl, kappa, vals, s)
+                : staged_dispatch<false, f2, f2, double>(pl, kappa, vals, s);
+  }
   if (precision == WQ_PREC_MIXED) {
     if (v32)
       return mass ? staged_dispatch<true, double, float, float>(pl, kappa, vals, s)

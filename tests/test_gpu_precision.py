@@ -8,7 +8,9 @@ rows.
 row-relative. All-FP32 is held to 1e-5: its error is dominated by the FP32
 accumulation of the q3 contraction over weights that reach a few hundred times the
 row's largest entry near the boundary, so it is reported, and bounded, but it is not
-the 1e-6 mode."""
+the 1e-6 mode. "f32x2" (double-float, ~48 significant bits on the FP32 pipe) is held
+to the FP64 bar, 1e-12 (with FP64 values; FP32 values round it to ~6e-8, so that case
+is held to 1e-6)."""
 import os
 
 import numpy as np
@@ -38,10 +40,10 @@ def setup():
     plan.close()
 
 
-BARS = {"mixed": 1e-6, "fp32": 1e-5}
+BARS = {"mixed": 1e-6, "fp32": 1e-5, "f32x2": 1e-12}
 
 
-@pytest.mark.parametrize("precision", ["mixed", "fp32"])
+@pytest.mark.parametrize("precision", ["mixed", "fp32", "f32x2"])
 @pytest.mark.parametrize("dtype", ["float32", "float64"])
 def test_reduced_precision_p5_128(setup, precision, dtype):
     plan, rows, ref, rp = setup
@@ -61,4 +63,4 @@ def test_reduced_precision_p5_128(setup, precision, dtype):
           f"Frobenius {frob:.3e}")
     del vals
     torch.cuda.empty_cache()
-    assert worst <= BARS[precision]
+    assert worst <= (1e-6 if precision == "f32x2" and dtype == "float32" else BARS[precision])

@@ -123,3 +123,20 @@ def test_staged_edge_rows_compile_time_patterns(wq, p, extra):
     check_rows(Oracle3D(patch.p, patch.knots, patch.ctrl, kappa=kappa), plan, M, "mass", rows, tol=tol)
     check_rows(Oracle3D(patch.p, patch.knots, patch.ctrl), plan, X, "stiffness", rows, tol=1e-6)
     plan.close()
+
+
+@pytest.mark.parametrize("p", [2, 3, 4, 5, 6, 8])
+@pytest.mark.parametrize("which", ["stiffness", "mass"])
+def test_staged_double_float(wq, p, which):
+    """WQ_PREC_F32X2 (double-float on the FP32 pipe) holds the FP64 parity bar."""
+    patch = perturbed_cube(p, (2 * p + 5, 2 * p + 4, p + 3), seed=50 + p)
+    plan = wq.Plan(patch.p, patch.knots, patch.ctrl)
+    kappa = random_field(int(np.prod(plan.n_qp)), seed=60 + p, kind="positive")
+    fn = plan.stiffness if which == "stiffness" else plan.mass
+    S = fn(kappa=torch.as_tensor(kappa, device="cuda"), precision="f32x2")
+    torch.cuda.synchronize()
+    orc = Oracle3D(patch.p, patch.knots, patch.ctrl, kappa=kappa)
+    rows = sample_rows(plan.n, plan.p, 80, seed=900 + p)
+    worst = check_rows(orc, plan, S, which, rows, tol=TOL_F64_P8 if p == 8 else TOL_F64)
+    print(f"f32x2 p={p} {which}: worst row-relative error {worst:.3e}")
+    plan.close()
