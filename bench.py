@@ -370,6 +370,7 @@ def run_ours(args):
     f32_f64_ms = timed(lambda: plan.stiffness(out=vals, precision="fp32"))
     mix_ms = timed(lambda: plan.stiffness(out=vals32, dtype=torch.float32, precision="mixed"))
     mix_f64_ms = timed(lambda: plan.stiffness(out=vals, precision="mixed"))
+    f2_ms = timed(lambda: plan.stiffness(out=vals, precision="f32x2"))
     plan.set_algorithm("fused")
     f32f_ms = timed(lambda: plan.stiffness(out=vals32, dtype=torch.float32, precision="fp32"))
     f64f_ms = timed(lambda: plan.stiffness(out=vals))
@@ -424,6 +425,7 @@ def run_ours(args):
         "breakdown_ms": {"assembly": kernel_ms, "refresh": refresh_ms, "mass_fp64": mass_ms,
                          "stiffness_fp32_f32vals": f32_ms, "stiffness_fp32_f64vals": f32_f64_ms,
                          "stiffness_mixed_f32vals": mix_ms, "stiffness_mixed_f64vals": mix_f64_ms,
+                         "stiffness_f32x2_f64vals": f2_ms,
                          "stiffness_fp32_f32vals_fused": f32f_ms, "stiffness_fp64_fused": f64f_ms},
         "variants_nnz_per_s": {"stiffness_fp64_assembly_only": nnz / (kernel_ms * 1e-3),
                                "mass_fp64_assembly_only": nnz / (mass_ms * 1e-3),
@@ -431,6 +433,7 @@ def run_ours(args):
                                "stiffness_fp32_f64vals": nnz / (f32_f64_ms * 1e-3),
                                "stiffness_mixed_f32vals": nnz / (mix_ms * 1e-3),
                                "stiffness_mixed_f64vals": nnz / (mix_f64_ms * 1e-3),
+                               "stiffness_f32x2_f64vals": nnz / (f2_ms * 1e-3),
                                "stiffness_fp32_f32vals_fused": nnz / (f32f_ms * 1e-3),
                                "stiffness_fp64_fused_assembly_only": nnz / (f64f_ms * 1e-3)},
         "batch": batch_line,

@@ -61,8 +61,10 @@ enum { WQ_VALUES_F64 = 0, WQ_VALUES_F32 = 1 };
 enum {
   WQ_PREC_FP64 = 0,          /* FP64 FMA throughout */
   WQ_PREC_FP32 = 1,          /* FP32 FMA, FP32 intermediates */
-  WQ_PREC_MIXED = 2,         /* FP64 for the first two mode products (contracting q3, q2),
-                                FP32 for the last one (q1, half of the work); staged only */
+  WQ_PREC_MIXED = 2,         /* double-float (see below) for the first two mode products
+                                (contracting q3, q2), FP32 for the last one (q1, half of the
+                                work) except its first and last p+1 rows of direction 1, which
+                                run in FP64; <= 1e-6 row-relative; staged only */
   WQ_PREC_F32X2 = 3          /* double-float: every value a pair of floats (~48 significant
                                 bits), all three mode products on the FP32 pipe; staged only */
 };

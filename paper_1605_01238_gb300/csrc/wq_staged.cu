@@ -821,8 +821,8 @@ static wq_status staged_t(wq_plan_s* pl, const double* kappa, void* vals, cudaSt
                                 (size_t)pl->nnz1[2] * NG * nbq * pl->nnz1[1] * sizeof(double),
                                 sizeof(Real) == sizeof(float) || sizeof(R1) == sizeof(float), s);
   if (st != WQ_OK) return st;
-  constexpr bool F2 = std::is_same<Real, f2>::value;
-  static_assert(!F2 || std::is_same<R1, f2>::value, "double-float runs every stage in double-float");
+  constexpr bool F2 = std::is_same<Real, f2>::value, F2_1 = std::is_same<R1, f2>::value;
+  static_assert(!F2_1 || F2, "double-float stage 1 needs double-float stages 3 and 2");
   StagedArgs A, A1;  // A: tables in Real (stages 3, 2); A1: tables in R1 (stage 1)
   for (int l = 0; l < 3; ++l) {
     DirData& d = pl->dir[l];
@@ -838,9 +838,12 @@ static wq_status staged_t(wq_plan_s* pl, const double* kappa, void* vals, cudaSt
       k_to_f2<<<(unsigned)((nw + 255) / 256), 256, 0, s>>>(d.w, t, nw);
       k_to_f2<<<(unsigned)((nb + 255) / 256), 256, 0, s>>>(d.bt, t + nw, nb);
       count_launch(2);
-      A.d[l] = A1.d[l] = Dir{d.n, d.nqp, d.q0, d.nq, t, t + nw, d.prefix, d.pair_row};
+      A.d[l] = Dir{d.n, d.nqp, d.q0, d.nq, t, t + nw, d.prefix, d.pair_row};
       A.nnz1[l] = A1.nnz1[l] = pl->nnz1[l];
-      continue;
+      if (F2_1) {
+        A1.d[l] = A.d[l];
+        continue;
+      }
     }
     if (sizeof(Real) == sizeof(float) || sizeof(R1) == sizeof(float)) {
       const int64_t nw = (int64_t)4 * d.n * pl->nq_max, nb = (int64_t)2 * d.n * pl->nq_max;
@@ -851,7 +854,7 @@ static wq_status staged_t(wq_plan_s* pl, const double* kappa, void* vals, cudaSt
       bt32 = d.tab32 + nw;
     }
     const bool f = sizeof(Real) == sizeof(float), f1 = sizeof(R1) == sizeof(float);
-    A.d[l] = Dir{d.n, d.nqp, d.q0, d.nq, f ? w32 : d.w, f ? bt32 : d.bt, d.prefix, d.pair_row};
+    if (!F2) A.d[l] = Dir{d.n, d.nqp, d.q0, d.nq, f ? w32 : d.w, f ? bt32 : d.bt, d.prefix, d.pair_row};
     A1.d[l] = Dir{d.n, d.nqp, d.q0, d.nq, f1 ? w32 : d.w, f1 ? bt32 : d.bt, d.prefix, d.pair_row};
     A.nnz1[l] = A1.nnz1[l] = pl->nnz1[l];
   }
@@ -934,10 +937,10 @@ wq_status launch_staged(wq_plan_s* pl, bool mass, const double* kappa, void* val
   }
   if (precision == WQ_PREC_MIXED) {
     if (v32)
-      return mass ? staged_dispatch<true, double, float, float>(pl, kappa, vals, s)
-                  : staged_dispatch<false, double, float, float>(pl, kappa, vals, s);
-    return mass ? staged_dispatch<true, double, float, double>(pl, kappa, vals, s)
-                : staged_dispatch<false, double, float, double>(pl, kappa, vals, s);
+      return mass ? staged_dispatch<true, f2, float, float>(pl, kappa, vals, s)
+                  : staged_dispatch<false, f2, float, float>(pl, kappa, vals, s);
+    return mass ? staged_dispatch<true, f2, float, double>(pl, kappa, vals, s)
+                : staged_dispatch<false, f2, float, double>(pl, kappa, vals, s);
   }
   if (v32)
     return mass ? staged_dispatch<true, float, float, float>(pl, kappa, vals, s)
