@@ -290,6 +290,26 @@ def run_reference(args):
     return 0
 
 
+def variant_errors(plan, torch, count: int = 4096, seed: int = 77):
+    """Worst row-relative error (max |d| over a row / the row's largest FP64 entry) of each
+    reduced-precision stiffness variant against the FP64 path, on sampled rows (every
+    boundary/interior class forced in), measured live on this GPU."""
+    from wq_synth import sample_rows
+    rp = plan.pattern()[0].cpu().numpy()
+    rows = np.asarray(sample_rows(plan.n, plan.p, count, seed=seed))
+    idx = np.concatenate([np.arange(rp[r], rp[r + 1]) for r in rows])
+    starts = np.concatenate([[0], np.cumsum([rp[r + 1] - rp[r] for r in rows])[:-1]])
+    idx_d = torch.as_tensor(idx, device="cuda")
+    ref = plan.stiffness()[idx_d].cpu().numpy()
+    den = np.maximum.reduceat(np.abs(ref), starts)
+    out = {}
+    for prec, dt in (("mixed", torch.float32), ("f32x2", torch.float64), ("fp32", torch.float32)):
+        got = plan.stiffness(precision=prec, dtype=dt)[idx_d].double().cpu().numpy()
+        out[prec] = float((np.maximum.reduceat(np.abs(got - ref), starts) / den).max())
+        torch.cuda.empty_cache()
+    return out, len(rows)
+
+
 def run_ours(args):
     import torch
 
@@ -377,6 +397,8 @@ def run_ours(args):
     plan.set_algorithm(args.algo)
     refresh_ms = timed(lambda: plan.refresh(ctrl_d))
     del vals32
+    torch.cuda.empty_cache()
+    errs, err_rows = variant_errors(plan, torch)
     batch_line = run_batch_variant(wq, torch, stream) if args.batch else None
 
     # end to end through the C ABI with host buffers (pinned)
@@ -436,6 +458,17 @@ def run_ours(args):
                                "stiffness_f32x2_f64vals": nnz / (f2_ms * 1e-3),
                                "stiffness_fp32_f32vals_fused": nnz / (f32f_ms * 1e-3),
                                "stiffness_fp64_fused_assembly_only": nnz / (f64f_ms * 1e-3)},
+        "precision_variants": {
+            "mixed": {"values": "f32", "ms": mix_ms, "speedup_vs_fp64": kernel_ms / mix_ms,
+                      "max_row_rel_error_vs_fp64": errs["mixed"], "bar": 1e-6,
+                      "what": "q3, q2 mode products in double-float, q1 in FP32 (FP64 edge rows)"},
+            "f32x2": {"values": "f64", "ms": f2_ms, "speedup_vs_fp64": kernel_ms / f2_ms,
+                      "max_row_rel_error_vs_fp64": errs["f32x2"], "bar": 1e-12,
+                      "what": "double-float (pairs of floats) in all three mode products"},
+            "fp32": {"values": "f32", "ms": f32_ms, "speedup_vs_fp64": kernel_ms / f32_ms,
+                     "max_row_rel_error_vs_fp64": errs["fp32"], "bar": None,
+                     "what": "FP32 in all three mode products"},
+            "error_rows": err_rows},
         "batch": batch_line,
         "e2e": {"value": world * nnz / e2e_s, "unit": "nnz/s", "h2d_bytes_per_step": 8 * 3 * N,
                 "d2h_bytes_per_step": 8 * nnz,

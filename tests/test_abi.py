@@ -41,6 +41,17 @@ def test_binding_covers_every_declared_symbol():
     assert set(declared_functions()) <= set(_lib.SIGNATURES)
 
 
+def test_binding_enums_match_the_header():
+    """Precision, value-type and algorithm constants of the binding equal the header's."""
+    import paper_1605_01238_gb300 as wq
+    text = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    enum = {k: int(v) for k, v in re.findall(r"\b(WQ_(?:PREC|VALUES|ALGO)_[A-Z0-9]+)\s*=\s*(\d+)", text)}
+    assert {k for k in enum if k.startswith("WQ_PREC_")} == {"WQ_PREC_FP64", "WQ_PREC_FP32", "WQ_PREC_MIXED",
+                                                            "WQ_PREC_F32X2"}
+    assert wq._PREC == {"fp64": enum["WQ_PREC_FP64"], "fp32": enum["WQ_PREC_FP32"],
+                        "mixed": enum["WQ_PREC_MIXED"], "f32x2": enum["WQ_PREC_F32X2"]}
+
+
 def _create(lib, p, knots, ctrl, d=3):
     kn = [np.ascontiguousarray(k, dtype=np.float64) for k in knots]
     n_knots = (ctypes.c_int64 * 3)(*[len(k) for k in kn])
