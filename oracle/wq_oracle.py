@@ -24,7 +24,7 @@ library steps:
                                                     the rule (delta_kl, delta_km) in direction k
 * brute-force Galerkin (element-wise Gauss) ....... Eqs. (stiffness-3d), (mass-3d), used by the pins
 
-Readings where the paper is ambiguous (the same list is in the design notes):
+Readings where the paper is ambiguous:
 
 * Rule kinds (a, b): a = derivative order on the test function (folded into the
   weight), b = derivative order on the trial function evaluated at the point.
