@@ -36,19 +36,29 @@ METRIC = "WQ 3D stiffness nnz/s and % of HBM-write roofline; mixed vs FP64 at â‰
 # edge-row kernels, k_stage1) at p = 4, 64^3, from one ncu capture of
 # dram__bytes_read.sum + dram__bytes_write.sum (profiles/assembly_traffic_p4_nel64.md).
 # It is reported only while the kernel sources still hash to the captured value.
-TRAFFIC_CAPTURE = {"p": 4, "n_el": 64, "bytes": 3997.57e6 + 4354.18e6, "sources": "22537b9e9bd87d74",
+TRAFFIC_CAPTURE = {"p": 4, "n_el": 64, "bytes": 3997.57e6 + 4354.18e6, "sources": "8b34d1bd17a351ef",
                    "files": ("paper_1605_01238_gb300/csrc/wq_staged.cu", "paper_1605_01238_gb300/csrc/wq_internal.h")}
 
 
 def captured_traffic(p: int, n_el: int):
-    import hashlib
     if (p, n_el) != (TRAFFIC_CAPTURE["p"], TRAFFIC_CAPTURE["n_el"]):
         return None
+    return TRAFFIC_CAPTURE["bytes"] if kernel_source_hash() == TRAFFIC_CAPTURE["sources"] else None
+
+
+def kernel_source_hash() -> str:
+    """Hash of the kernel sources with comments and blank space removed, so that a
+    comment edit keeps a capture valid and any code change invalidates it."""
+    import hashlib
+    import re
     h = hashlib.sha256()
     for f in TRAFFIC_CAPTURE["files"]:
-        with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), f), "rb") as fh:
-            h.update(fh.read())
-    return TRAFFIC_CAPTURE["bytes"] if h.hexdigest()[:16] == TRAFFIC_CAPTURE["sources"] else None
+        with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), f)) as fh:
+            text = fh.read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", "", text)
+        h.update(re.sub(r"\s+", "", text).encode())
+    return h.hexdigest()[:16]
 
 
 def peaks():

@@ -18,6 +18,13 @@
 // cT[slot][q3][q1][q2] and writes T3 with q2 fastest (threads run over q2); K2
 // runs over i2 and writes G with the pair index p2 fastest; K1 runs over p2, so
 // neighbouring threads write neighbouring j2 blocks of the same CSR row.
+//
+// Arithmetic (template parameters Real for K3/K2, R1 for K1):
+//   FP64        double everywhere;
+//   F32X2       f2 (double-float, ~48 bits on the FP32 pipe) everywhere;
+//   MIXED       f2 in K3/K2, float in K1; K1's first and last P+1 rows of direction 1
+//               run in double from an FP64 copy of G that K2 writes for their points;
+//   FP32        float everywhere.
 #include <algorithm>
 #include <type_traits>
 #include <vector>
