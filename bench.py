@@ -36,8 +36,8 @@ METRIC = "WQ 3D stiffness nnz/s and % of HBM-write roofline; mixed vs FP64 at â‰
 # edge-row kernels, k_stage1) at p = 4, 64^3, from one ncu capture of
 # dram__bytes_read.sum + dram__bytes_write.sum (profiles/assembly_traffic_p4_nel64.md).
 # It is reported only while the kernel sources still hash to the captured value.
-TRAFFIC_CAPTURE = {"p": 4, "n_el": 64, "bytes": 3997.57e6 + 4354.18e6, "sources": "8b34d1bd17a351ef",
-                   "files": ("paper_1605_01238_gb300/csrc/wq_staged.cu", "paper_1605_01238_gb300/csrc/wq_internal.h")}
+TRAFFIC_CAPTURE = {"p": 4, "n_el": 64, "bytes": 3997.57e6 + 4354.18e6, "sources": "17c1a0e7441ac796",
+                   "files": ("paper_1605_01238_gb300/csrc/wq_staged_impl.cuh", "paper_1605_01238_gb300/csrc/wq_internal.h")}
 
 
 def captured_traffic(p: int, n_el: int):

@@ -161,7 +161,7 @@ wq_status launch_assemble_f64(wq_plan_s* pl, bool mass, const double* kappa, dou
                               cudaStream_t s);
 wq_status launch_assemble_f32(wq_plan_s* pl, bool mass, const double* kappa, void* vals,
                               int value_dtype, cudaStream_t s);
-// Staged assembly (wq_staged.cu).
+// Staged assembly (wq_staged.cu: dispatch on the degree; kernels in wq_staged_impl.cuh).
 wq_status launch_staged(wq_plan_s* pl, bool mass, const double* kappa, void* vals, int value_dtype, int precision,
                         cudaStream_t s);
 

@@ -1,959 +1,30 @@
-// Staged WQ assembly: the three mode products of Eq. (sumfactorization) as three
-// kernels over the whole mesh, with their intermediates in device memory.
-//
-//   K3  T3[p3][term][q1][q2] = sum_{q3 in Q_i3 n Q_j3} w3^{k3}(i3,q3) B3^{b3}(j3,q3) c_term(q1,q2,q3)
-//   K2  G[p3][g][q1][p2]     = sum_{classes of g} sum_{q2 in Q_i2 n Q_j2} B2^{b2}(j2,q2)
-//                               sum_{terms of the class} w2^{k2}(i2,q2) T3[p3][term][q1][q2]
-//   K1  s(i, j)              = sum_b sum_{q1 in Q_i1 n Q_j1} B1^{b}(j1,q1) sum_a w1^{(a,b)}(i1,q1) G[p3][(a,b)][q1][p2]
-//
-// with p3 = (i3, j3) and p2 = (i2, j2) running over the 1D band pairs |i - j| <= p
-// (prefix sums of the band widths index them). Every output of every stage is
-// computed exactly once, so the FP64 work is the halo-free count of the
-// factorisation; the price is writing and reading T3 and G once (a few GB at
-// p = 4, 64^3), cheap against the FP64 rate. Each stage has a path for regular
-// rows (p+1 <= i <= n-p-2: Q_i = [2i-p, 2i+p], the (point, output) pattern known
-// at compile time) and a general path for the rows next to the boundary.
-//
-// Layouts keep every access coalesced: K3 reads a transposed coefficient copy
-// cT[slot][q3][q1][q2] and writes T3 with q2 fastest (threads run over q2); K2
-// runs over i2 and writes G with the pair index p2 fastest; K1 runs over p2, so
-// neighbouring threads write neighbouring j2 blocks of the same CSR row.
-//
-// Arithmetic (template parameters Real for K3/K2, R1 for K1):
-//   FP64        double everywhere;
-//   F32X2       f2 (double-float, ~48 bits on the FP32 pipe) everywhere;
-//   MIXED       f2 in K3/K2, float in K1; K1's first and last P+1 rows of direction 1
-//               run in double from an FP64 copy of G that K2 writes for their points;
-//   FP32        float everywhere.
-#include <algorithm>
-#include <type_traits>
-#include <vector>
-
+// Entry of the staged WQ assembly (three mode-product kernels, intermediates in
+// device memory): dispatch on the degree to the per-degree translation units
+// wq_staged_p<P>.cu, which instantiate the kernels of wq_staged_impl.cuh.
 #include "wq_internal.h"
 
 namespace wq {
 
-namespace {
-
-__constant__ int sTermL[9] = {0, 0, 0, 1, 1, 1, 2, 2, 2};
-__constant__ int sTermM[9] = {0, 1, 2, 0, 1, 2, 0, 1, 2};
-// coefficient slot of each term: c_11 c_12 c_13 c_22 c_23 c_33 (c_lm = c_ml)
-__constant__ int sSlot[9] = {0, 1, 2, 1, 3, 4, 2, 4, 5};
-
-// Stage-2 classes of equal (group, b2), terms ordered as sTerm*:
-// class 0: (0,0) g3 b0; 1: (0,1) g2 b1; 2: (0,2) g2 b0; 3: (1,0),(2,0) g1 b0;
-// 4: (1,1),(2,1) g0 b1; 5: (1,2),(2,2) g0 b0. Classes come grouped by G group
-// (g3 | g2 g2 | g1 | g0 g0): one group's accumulators are live at a time, zeroed
-// at its first class and stored after its last.
-struct ClassInfo {
-  int term[2], g, b2;
-  bool first, last;
-};
-__constant__ ClassInfo sClass[6] = {{{0, -1}, 3, 0, true, true},  {{1, -1}, 2, 1, true, false},
-                                    {{2, -1}, 2, 0, false, true}, {{3, 6}, 1, 0, true, true},
-                                    {{4, 7}, 0, 1, true, false},  {{5, 8}, 0, 0, false, true}};
-
-// Class c: from compile-time tables when the class loop is unrolled (c folds to a
-// constant), from constant memory when it is rolled (double-float, whose ~15
-// instructions per multiply-add would otherwise overflow the instruction cache).
-template <bool ROLL>
-__device__ __forceinline__ ClassInfo class_info(int c) {
-  if (ROLL) return sClass[c];
-  constexpr int terms[6][2] = {{0, -1}, {1, -1}, {2, -1}, {3, 6}, {4, 7}, {5, 8}};
-  constexpr int group[6] = {3, 2, 2, 1, 0, 0};
-  constexpr int b2[6] = {0, 1, 0, 0, 1, 0};
-  constexpr bool first[6] = {true, true, false, true, true, false};
-  constexpr bool last[6] = {true, false, true, true, false, true};
-  return ClassInfo{{terms[c][0], terms[c][1]}, group[c], b2[c], first[c], last[c]};
-}
-
-// Double-float numbers (WQ_PREC_F32X2): value = hi + lo with |lo| <= ulp(hi)/2,
-// about 48 significant bits carried on the FP32 pipe, which GB300 runs at ~60x
-// its FP64 rate. Arithmetic by the error-free transformations of Knuth (two-sum)
-// and Dekker (two-product, here in its FMA form), renormalised by the fast
-// two-sum; the _rn intrinsics keep the compiler from contracting them.
-struct f2 {
-  float hi, lo;
-};
-
-__device__ __forceinline__ f2 f2_renorm(float s, float t) {  // fast two-sum, |s| >= |t|
-  const float hi = __fadd_rn(s, t);
-  return f2{hi, __fsub_rn(t, __fsub_rn(hi, s))};
-}
-
-// a * b + c
-__device__ __forceinline__ f2 f2_fma(f2 a, f2 b, f2 c) {
-  const float p = __fmul_rn(a.hi, b.hi);
-  float e = __fmaf_rn(a.hi, b.hi, -p);                         // a.hi b.hi = p + e exactly
-  e = __fmaf_rn(a.hi, b.lo, __fmaf_rn(a.lo, b.hi, e));         // cross terms (a.lo b.lo < 2^-46 |ab|)
-  const float s = __fadd_rn(p, c.hi);                          // two-sum of p and c.hi
-  const float v = __fsub_rn(s, p);
-  float t = __fadd_rn(__fsub_rn(p, __fsub_rn(s, v)), __fsub_rn(c.hi, v));
-  t = __fadd_rn(t, __fadd_rn(e, c.lo));
-  return f2_renorm(s, t);
-}
-
-__device__ __forceinline__ f2 f2_mul(f2 a, f2 b) {
-  const float p = __fmul_rn(a.hi, b.hi);
-  float e = __fmaf_rn(a.hi, b.hi, -p);
-  e = __fmaf_rn(a.hi, b.lo, __fmaf_rn(a.lo, b.hi, e));
-  return f2_renorm(p, e);
-}
-
-__device__ __forceinline__ f2 f2_from(double x) {
-  const float hi = __double2float_rn(x);
-  return f2{hi, __double2float_rn(x - (double)hi)};
-}
-
-// Arithmetic of the contractions: Real = double, float or f2.
-template <typename T>
-__device__ __forceinline__ T fmaR(T a, T b, T c);
-template <>
-__device__ __forceinline__ double fmaR<double>(double a, double b, double c) { return fma(a, b, c); }
-template <>
-__device__ __forceinline__ float fmaR<float>(float a, float b, float c) { return fmaf(a, b, c); }
-template <>
-__device__ __forceinline__ f2 fmaR<f2>(f2 a, f2 b, f2 c) { return f2_fma(a, b, c); }
-
-template <typename T>
-__device__ __forceinline__ T mulR(T a, T b) { return a * b; }
-template <>
-__device__ __forceinline__ f2 mulR<f2>(f2 a, f2 b) { return f2_mul(a, b); }
-
-template <typename T>
-__device__ __forceinline__ T zeroR() { return (T)0; }
-template <>
-__device__ __forceinline__ f2 zeroR<f2>() { return f2{0.0f, 0.0f}; }
-
-template <typename T>
-__device__ __forceinline__ T fromD(double x) { return (T)x; }
-template <>
-__device__ __forceinline__ f2 fromD<f2>(double x) { return f2_from(x); }
-
-// float -> double by re-packing the IEEE-754 fields (exact; integer instructions
-// instead of a conversion on the FP64 pipe). Float subnormals (below 1.2e-38)
-// become zero, far below the values' rounding.
-__device__ __forceinline__ double f2d_exact(float f) {
-  const unsigned u = __float_as_uint(f);
-  const unsigned e = (u >> 23) & 0xffu, sign = u & 0x80000000u, m = u & 0x7fffffu;
-  if (e == 0u) return __hiloint2double((int)sign, 0);
-  const unsigned de = e == 0xffu ? 0x7ffu : e + 896u;
-  return __hiloint2double((int)(sign | (de << 20) | (m >> 3)), (int)(m << 29));
-}
-
-template <typename T>
-__device__ __forceinline__ double toD(T x) { return (double)x; }
-template <>
-__device__ __forceinline__ double toD<f2>(f2 x) { return f2d_exact(x.hi) + f2d_exact(x.lo); }
-
-// value in an output / intermediate type O
-template <typename O, typename T>
-__device__ __forceinline__ O toOut(T x) { return (O)x; }
-template <>
-__device__ __forceinline__ double toOut<double, f2>(f2 x) { return toD(x); }
-template <>
-__device__ __forceinline__ float toOut<float, f2>(f2 x) { return __fadd_rn(x.hi, x.lo); }
-template <>
-__device__ __forceinline__ f2 toOut<f2, f2>(f2 x) { return x; }
-
-// read of a volatile shared-memory value
-template <typename T>
-__device__ __forceinline__ T vld(const volatile T* p) { return *p; }
-template <>
-__device__ __forceinline__ f2 vld<f2>(const volatile f2* p) { return f2{p->hi, p->lo}; }
-
-__device__ __forceinline__ int blo(int i, int p) { return i - p > 0 ? i - p : 0; }
-__device__ __forceinline__ int bw(int i, int p, int n) { return min(n - 1, i + p) - blo(i, p) + 1; }
-
-// Tables and coefficients come in the arithmetic type of the contractions (the
-// FP32 path reads float copies made once per call), so no conversion sits in
-// the inner loops.
-struct Dir {
-  int n, nqp;
-  const int* q0;
-  const int* nq;
-  const void* w;          // Real [4][n][NQ]
-  const void* bt;         // Real [2][n][NQ]
-  const int64_t* prefix;  // [n+1]
-  const int* pair_row;    // [nnz1]: i of each band pair
-};
-
-struct StagedArgs {
-  Dir d[3];
-  int NQ;
-  int64_t nnz1[3];
-  const void* cT;         // Real [7][nqp3][nqp1][nqp2]
-  const void* kappaT;     // NULL or Real [nqp3][nqp1][nqp2]
-  void* T3;               // Real [nnz1_3][NT][nqp1][nqp2]
-  void* G;                // Real [nnz1_3][NG][nqp1][nnz1_2]
-  void* vals;
-  // Mixed precision only: an FP64 copy of G at the q1 points that the first and
-  // last P+1 rows of direction 1 read (q1 < nbl and q1 >= hstart), and the FP64
-  // direction-1 tables, so that stage 1 runs those rows in FP64.
-  double* Gb;             // NULL or double [nnz1_3][NG][nbq][nnz1_2]
-  const double* w1d;      // double [4][n1][NQ]
-  const double* bt1d;     // double [2][n1][NQ]
-  int nbl, hstart, nbq;
-};
-
-// position of point q1 in the FP64 edge copy of G (in range for every q1 that a
-// first or last P+1 row of direction 1 reads; clamped for any other q1)
-__device__ __forceinline__ int edge_row(int q1, int nbl, int hstart, int nbq) {
-  return q1 < nbl ? q1 : min(nbq - 1, max(nbl, q1 - hstart + nbl));
-}
-
-template <typename Real>
-__device__ __forceinline__ const Real* tab(const void* p) { return reinterpret_cast<const Real*>(p); }
-
-// Loads of data that no kernel of the launch writes (tables, T3 in stage 2, G in
-// stage 1) go through the read-only path, so the compiler may move them across
-// the kernel's own stores.
-template <typename T>
-__device__ __forceinline__ T ro(const T* p) { return __ldg(p); }
-template <>
-__device__ __forceinline__ f2 ro<f2>(const f2* p) {
-  const float2 v = __ldg(reinterpret_cast<const float2*>(p));
-  return f2{v.x, v.y};
-}
-
-__global__ void k_to_float(const double* __restrict__ in, float* __restrict__ out, int64_t n) {
-  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i < n) out[i] = (float)in[i];
-}
-
-__global__ void k_to_f2(const double* __restrict__ in, f2* __restrict__ out, int64_t n) {
-  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i < n) out[i] = f2_from(in[i]);
-}
-
-// (q1, q2, q3) -> (q3, q1, q2) copy of the coefficient planes (and kappa)
-template <typename Real>
-__global__ void k_transpose_coef(const double* __restrict__ c, const double* __restrict__ kappa,
-                                 Real* __restrict__ cT, Real* __restrict__ kT, int nq1, int nq2, int nq3,
-                                 int nplanes) {
-  __shared__ Real tile[32][33];
-  const int bx = blockIdx.x * 32, by = blockIdx.y * 32;  // q1, q2 tile
-  const int plane = blockIdx.z;                          // slot * nq3 + q3
-  const int slot = plane / nq3;
-  const double* src = slot < nplanes ? c + (int64_t)plane * nq1 * nq2 : kappa + (int64_t)(plane - nplanes * nq3) * nq1 * nq2;
-  Real* dst = slot < nplanes ? cT + (int64_t)plane * nq1 * nq2 : kT + (int64_t)(plane - nplanes * nq3) * nq1 * nq2;
-  for (int k = threadIdx.y; k < 32; k += blockDim.y) {
-    const int q2 = by + k, q1 = bx + threadIdx.x;
-    if (q1 < nq1 && q2 < nq2) tile[k][threadIdx.x] = fromD<Real>(src[(int64_t)q2 * nq1 + q1]);
-  }
-  __syncthreads();
-  for (int k = threadIdx.y; k < 32; k += blockDim.y) {
-    const int q1 = bx + k, q2 = by + threadIdx.x;
-    if (q1 < nq1 && q2 < nq2) dst[(int64_t)q1 * nq2 + q2] = tile[threadIdx.x][k];
-  }
-}
-
-// K3: one thread per (q2, q1, i3); all terms and all j3 of the band. Blocks with
-// consecutive i3 (blockIdx.x) read overlapping coefficient planes back to back.
-template <int P, bool MASS, typename Real>
-__global__ void __launch_bounds__(128) k_stage3(StagedArgs A) {
-  constexpr int MAXQ = 4 * P + 1;
-  constexpr int NT = MASS ? 1 : 9;
-  constexpr int BW = 2 * P + 1;
-  const Dir& D3 = A.d[2];
-  const int nq1 = A.d[0].nqp, nq2 = A.d[1].nqp;
-  const int i3 = blockIdx.x;
-  const int64_t e = blockIdx.y * (int64_t)blockDim.x + threadIdx.x;  // point index q1 * nq2 + q2
-  const int q1 = (int)(e / nq2), q2 = (int)(e % nq2);
-  const int NQ = A.NQ;
-  const int qi3 = D3.q0[i3], ni3 = D3.nq[i3];
-  const int jlo = blo(i3, P), jhi = min(D3.n - 1, i3 + P);
-  // a3[k][jj][t] = w3^{k}(i3, qi3 + t) B3^{k & 1}(j3, qi3 + t) on the overlap [lo, hi) of Q_i3 and Q_j3
-  __shared__ Real a3[4][BW][MAXQ];
-  __shared__ int olo[BW], ohi[BW];
-  for (int e = threadIdx.x; e < 4 * BW * MAXQ; e += blockDim.x) {
-    const int t = e % MAXQ, jj = (e / MAXQ) % BW, k = e / (MAXQ * BW);
-    const int j3 = jlo + jj;
-    double v = 0.0;
-    if (j3 <= jhi && t < ni3) {
-      const int loc = qi3 + t - D3.q0[j3];
-      if (loc >= 0 && loc < D3.nq[j3])
-        v = toD(tab<Real>(D3.w)[((size_t)k * D3.n + i3) * NQ + t]) *
-            toD(tab<Real>(D3.bt)[((size_t)(k & 1) * D3.n + j3) * NQ + loc]);
-    }
-    a3[k][jj][t] = fromD<Real>(v);
-  }
-  for (int jj = threadIdx.x; jj < BW; jj += blockDim.x) {
-    const int j3 = jlo + jj;
-    if (j3 <= jhi) {
-      const int qj = D3.q0[j3];
-      olo[jj] = max(qi3, qj) - qi3;
-      ohi[jj] = min(qi3 + ni3, qj + D3.nq[j3]) - qi3;
-    }
-  }
-  __syncthreads();
-  if (q1 >= nq1) return;
-  const int64_t plane = (int64_t)nq1 * nq2;
-  const int64_t pt = (int64_t)q1 * nq2 + q2;
-  const int64_t p3base = D3.prefix[i3];
-  Real* T3 = reinterpret_cast<Real*>(A.T3);
-  const int nslots = MASS ? 1 : 6;
-  for (int s = 0; s < nslots; ++s) {
-    const int slot = MASS ? 6 : s;
-    Real c[MAXQ];
-    const Real* cs = tab<Real>(A.cT) + ((int64_t)slot * D3.nqp + qi3) * plane + pt;
-    const Real* ks = A.kappaT ? tab<Real>(A.kappaT) + (int64_t)qi3 * plane + pt : nullptr;
-    for (int t = 0; t < ni3; ++t) c[t] = ks ? mulR(cs[t * plane], ks[t * plane]) : cs[t * plane];
-    for (int term = 0; term < NT; ++term) {
-      if (!MASS && sSlot[term] != s) continue;
-      const int l = MASS ? 0 : sTermL[term], m = MASS ? 0 : sTermM[term];
-      const int k3 = MASS ? 0 : 2 * (l == 2) + (m == 2);
-      for (int jj = 0; jj <= jhi - jlo; ++jj) {
-        const Real* a = a3[k3][jj];
-        Real acc = zeroR<Real>();
-        for (int t = olo[jj]; t < ohi[jj]; ++t) acc = fmaR<Real>(a[t], c[t], acc);
-        T3[(((p3base + jj) * NT + term) * nq1 + q1) * nq2 + q2] = acc;
-      }
-    }
-  }
-}
-
-// K2: one thread per (i2, q1, p3). Regular rows of direction 2 use a compile-time
-// (t, j2) pattern; rows next to the boundary loop over the support overlaps.
-// Regular rows: threads run over (i2 in [r_lo, r_hi), then q1), neighbouring
-// threads sharing q2 points. Boundary rows [0, r_lo) and [r_hi, n2): threads run
-// over (the row, then q1), so every lane has work and the rows of one side read
-// neighbouring q2 and write neighbouring band pairs.
-template <int P, bool MASS, typename Real, bool REG, typename GOut>
-__global__ void __launch_bounds__(128) k_stage2(StagedArgs A, int r_lo, int r_hi) {
-  constexpr int BW = 2 * P + 1;
-  constexpr int NT = MASS ? 1 : 9;
-  constexpr int NG = MASS ? 1 : 4;
-  constexpr int NC = MASS ? 1 : 6;
-  constexpr int MAXQ = 4 * P + 1;
-  constexpr bool ROLL = std::is_same<Real, f2>::value;
-  constexpr int CU = ROLL ? 1 : NC;
-  const Dir& D2 = A.d[1];
-  const int nq1 = A.d[0].nqp, nq2 = D2.nqp, NQ = A.NQ;
-  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  const int64_t p3 = blockIdx.y;
-  int i2, q1;
-  if (REG) {
-    const int nreg = r_hi - r_lo;
-    if (e >= (int64_t)nreg * nq1) return;
-    i2 = r_lo + (int)(e % nreg);
-    q1 = (int)(e / nreg);
-  } else {
-    const int nb = r_lo + (D2.n - r_hi);
-    if (e >= (int64_t)nb * nq1) return;
-    const int b = (int)(e % nb);
-    q1 = (int)(e / nb);
-    i2 = b < r_lo ? b : r_hi + (b - r_lo);
-  }
-  const int64_t nnz2 = A.nnz1[1];
-  const Real* T3 = reinterpret_cast<const Real*>(A.T3) + ((p3 * NT) * nq1 + q1) * (int64_t)nq2;
-  const int64_t tstride = (int64_t)nq1 * nq2;
-  const int qi = D2.q0[i2], ni = REG ? BW : D2.nq[i2];
-  const int jlo = blo(i2, P), jhi = min(D2.n - 1, i2 + P);
-  const int64_t pbase = D2.prefix[i2];
-  // classes come grouped by G group (g3 | g2 g2 | g1 | g0 g0): one group's
-  // accumulators are live at a time, zeroed at its first class, stored after its last
-  Real acc[BW];
-#pragma unroll(CU)
-  for (int c = 0; c < NC; ++c) {
-    const ClassInfo ci = class_info<ROLL>(c);
-    if (MASS || ci.first)
-#pragma unroll
-      for (int tt = 0; tt < BW; ++tt) acc[tt] = zeroR<Real>();
-    Real h[REG ? BW : MAXQ];
-#pragma unroll
-    for (int t = 0; t < (REG ? BW : MAXQ); ++t) h[t] = zeroR<Real>();
-#pragma unroll
-    for (int k = 0; k < 2; ++k) {
-      const int term = MASS ? 0 : ci.term[k];
-      if (term < 0 || (MASS && k > 0)) continue;
-      const int l = MASS ? 0 : term / 3, m = MASS ? 0 : term % 3;
-      const int k2 = MASS ? 0 : 2 * (l == 1) + (m == 1);
-      const Real* wrow = tab<Real>(D2.w) + ((size_t)k2 * D2.n + i2) * NQ;
-      const Real* trow = T3 + term * tstride + qi;
-      if (REG) {
-#pragma unroll
-        for (int t = 0; t < BW; ++t) h[t] = fmaR<Real>(ro(wrow + t), ro(trow + t), h[t]);
-      } else {
-        for (int t = 0; t < ni; ++t) h[t] = fmaR<Real>(ro(wrow + t), ro(trow + t), h[t]);
-      }
-    }
-    const int g = MASS ? 0 : ci.g;
-    const int b2 = MASS ? 0 : ci.b2;
-    if (REG) {
-#pragma unroll
-      for (int tt = 0; tt < BW; ++tt) {
-        const int j2 = i2 - P + tt;
-        const Real* brow = tab<Real>(D2.bt) + ((size_t)b2 * D2.n + j2) * NQ + (qi - D2.q0[j2]);
-#pragma unroll
-        for (int t = 0; t < BW; ++t)
-          if (t >= 2 * tt - 2 * P && t <= 2 * tt) acc[tt] = fmaR<Real>(ro(brow + t), h[t], acc[tt]);
-      }
-    } else {
-#pragma unroll
-      for (int tt = 0; tt < BW; ++tt) {
-        const int j2 = i2 - P + tt;
-        if (j2 < jlo || j2 > jhi) continue;
-        const int qj = D2.q0[j2];
-        const int lo = max(qi, qj), hi = min(qi + ni, qj + D2.nq[j2]);
-        const Real* brow = tab<Real>(D2.bt) + ((size_t)b2 * D2.n + j2) * NQ;
-        for (int q = lo; q < hi; ++q) acc[tt] = fmaR<Real>(ro(brow + (q - qj)), h[q - qi], acc[tt]);
-      }
-    }
-    if (MASS || ci.last) {
-      GOut* dst = reinterpret_cast<GOut*>(A.G) + ((p3 * NG + g) * nq1 + q1) * nnz2 + pbase;
-#pragma unroll
-      for (int tt = 0; tt < BW; ++tt) {
-        const int j2 = i2 - P + tt;
-        if (REG || (j2 >= jlo && j2 <= jhi)) dst[j2 - jlo] = toOut<GOut>(acc[tt]);
-      }
-      if (sizeof(GOut) < sizeof(Real) && A.Gb && (q1 < A.nbl || q1 >= A.hstart)) {
-        double* dd = A.Gb + ((p3 * NG + g) * A.nbq + edge_row(q1, A.nbl, A.hstart, A.nbq)) * nnz2 + pbase;
-#pragma unroll
-        for (int tt = 0; tt < BW; ++tt) {
-          const int j2 = i2 - P + tt;
-          if (REG || (j2 >= jlo && j2 <= jhi)) dd[j2 - jlo] = toD(acc[tt]);
-        }
-      }
-    }
-  }
-}
-
-// Stage 1 for a first or last P+1 row of direction 1: Q_i1 is not the regular
-// 2P+1 window and the band is clipped. G points at (p3, group 0, row 0, p2);
-// MAPQ maps q1 into the FP64 edge copy. out + base + j1 is the value of column j1.
-template <int P, bool MASS, typename T, typename OutT, bool MAPQ>
-__device__ __forceinline__ void stage1_edge(const T* G, int64_t gstride, int64_t nnz2, const T* w, int64_t wk,
-                                            const T* bt1, int64_t bder, const Dir& D1, int i1, int n1, int NQ,
-                                            int nbl, int hstart, int nbq, OutT* out, int64_t base) {
-  constexpr int BW = 2 * P + 1;
-  constexpr int MAXQ = 4 * P + 1;
-  const int qi1 = D1.q0[i1], ni1 = D1.nq[i1];
-  T h0[MAXQ], h1[MAXQ];
-  for (int t = 0; t < ni1; ++t) {
-    const int qr = MAPQ ? edge_row(qi1 + t, nbl, hstart, nbq) : qi1 + t;
-    const T* gq = G + (int64_t)qr * nnz2;
-    if (MASS) {
-      h0[t] = mulR(w[t], gq[0]);
-    } else {
-      h0[t] = fmaR<T>(w[t], gq[0], mulR(w[t + 2 * wk], gq[2 * gstride]));
-      h1[t] = fmaR<T>(w[t + wk], gq[gstride], mulR(w[t + 3 * wk], gq[3 * gstride]));
-    }
-  }
-#pragma unroll
-  for (int tt = 0; tt < BW; ++tt) {
-    const int j1 = i1 - P + tt;
-    if (j1 < 0 || j1 >= n1) continue;
-    const int qj = D1.q0[j1];
-    const int lo = max(qi1, qj), hi = min(qi1 + ni1, qj + D1.nq[j1]);
-    const int64_t brow = (int64_t)j1 * NQ - qj;
-    T v = zeroR<T>();
-    for (int q = lo; q < hi; ++q) {
-      if (MASS)
-        v = fmaR<T>(bt1[brow + q], h0[q - qi1], v);
-      else
-        v = fmaR<T>(bt1[brow + q + bder], h1[q - qi1], fmaR<T>(bt1[brow + q], h0[q - qi1], v));
-    }
-    out[base + j1] = toOut<OutT>(v);
-  }
-}
-
-// K2 on the regular rows of direction 2 (Q_i2 = [2 i2 - P, 2 i2 + P]), with the
-// rule and B-spline tables of the block's rows in shared memory: lanes run over
-// 32 consecutive rows i2 (so the T3 reads of a warp are contiguous), the four
-// warps over pairs of q1, and the tables are read from shared memory instead of one cache
-// line per lane. Bs holds B_j2 of the trial rows i0-P .. i0+31+P aligned to the
-// regular pattern: Bs[b][j2 - i0 + P][u] is B^(b)_j2 at point 2 j2 - P + u.
-template <int P, bool MASS, typename Real, typename GOut>
-__global__ void __launch_bounds__(128) k_stage2_reg(StagedArgs A, int r_lo, int r_hi) {
-  constexpr int BW = 2 * P + 1;
-  constexpr int NT = MASS ? 1 : 9;
-  constexpr int NG = MASS ? 1 : 4;
-  constexpr int NC = MASS ? 1 : 6;
-  constexpr int NK = MASS ? 1 : 4;   // rule kinds
-  constexpr int NB = MASS ? 1 : 2;   // trial kinds
-  constexpr int RW = 32;             // rows per block
-  constexpr int NJS = RW + 2 * P;    // trial rows per block
-  constexpr bool ROLL = std::is_same<Real, f2>::value;
-  constexpr int CU = ROLL ? 1 : NC;
-  __shared__ Real Ws[NK][RW][BW];
-  __shared__ Real Bs[NB][NJS][BW];
-  const Dir& D2 = A.d[1];
-  const int nq1 = A.d[0].nqp, nq2 = D2.nqp, NQ = A.NQ, n2 = D2.n;
-  const int i0 = r_lo + blockIdx.x * RW;
-  const int64_t p3 = blockIdx.y;
-  const int lane = threadIdx.x, warp = threadIdx.y, tid = warp * 32 + lane;
-  for (int e = tid; e < NK * RW * BW; e += 128) {
-    const int t = e % BW, r = (e / BW) % RW, k = e / (BW * RW);
-    const int i2 = i0 + r;
-    Ws[k][r][t] = i2 < r_hi ? ro(tab<Real>(D2.w) + ((size_t)k * n2 + i2) * NQ + t) : zeroR<Real>();
-  }
-  for (int e = tid; e < NB * NJS * BW; e += 128) {
-    const int u = e % BW, jr = (e / BW) % NJS, b = e / (BW * NJS);
-    const int j2 = i0 - P + jr;
-    Real v = zeroR<Real>();
-    if (j2 >= 0 && j2 < n2) {
-      const int idx = u + 2 * j2 - P - D2.q0[j2];
-      if (idx >= 0 && idx < D2.nq[j2]) v = ro(tab<Real>(D2.bt) + ((size_t)b * n2 + j2) * NQ + idx);
-    }
-    Bs[b][jr][u] = v;
-  }
-  __syncthreads();
-  const int i2 = i0 + lane;
-  if (i2 >= r_hi) return;
-  const int64_t nnz2 = A.nnz1[1];
-  const int64_t pbase = D2.prefix[i2];
-  const int64_t tstride = (int64_t)nq1 * nq2;
-  const Real* T3p = reinterpret_cast<const Real*>(A.T3) + (p3 * NT) * tstride + (2 * i2 - P);
-  // volatile views: the compiler would otherwise hoist all of the row's table
-  // values out of the q1 loop into registers and spill
-  const volatile Real* Wv = &Ws[0][lane][0];
-  const volatile Real* Bv = &Bs[0][lane][0];
-  // two q1 points per iteration: every shared-memory value feeds two FMA chains
-#pragma unroll 1
-  for (int qa = 2 * warp; qa < nq1; qa += 8) {
-    const int qb = min(qa + 1, nq1 - 1);  // the last iteration may repeat qa
-    const Real* Ta = T3p + (int64_t)qa * nq2;
-    const Real* Tb = T3p + (int64_t)qb * nq2;
-    Real acc[2][BW];
-#pragma unroll(CU)
-    for (int c = 0; c < NC; ++c) {
-      const ClassInfo ci = class_info<ROLL>(c);
-      if (MASS || ci.first)
-#pragma unroll
-        for (int tt = 0; tt < BW; ++tt) acc[0][tt] = acc[1][tt] = zeroR<Real>();
-      Real h[2][BW];
-#pragma unroll
-      for (int t = 0; t < BW; ++t) h[0][t] = h[1][t] = zeroR<Real>();
-#pragma unroll
-      for (int k = 0; k < 2; ++k) {
-        const int term = MASS ? 0 : ci.term[k];
-        if (term < 0 || (MASS && k > 0)) continue;
-        const int l = MASS ? 0 : term / 3, m = MASS ? 0 : term % 3;
-        const int k2 = MASS ? 0 : 2 * (l == 1) + (m == 1);
-#pragma unroll
-        for (int t = 0; t < BW; ++t) {
-          const Real wv = vld(Wv + k2 * RW * BW + t);
-          h[0][t] = fmaR<Real>(wv, ro(Ta + term * tstride + t), h[0][t]);
-          h[1][t] = fmaR<Real>(wv, ro(Tb + term * tstride + t), h[1][t]);
-        }
-      }
-      const int g = MASS ? 0 : ci.g;
-      const int b2 = MASS ? 0 : ci.b2;
-#pragma unroll
-      for (int tt = 0; tt < BW; ++tt)
-#pragma unroll
-        for (int t = 0; t < BW; ++t)
-          if (t >= 2 * tt - 2 * P && t <= 2 * tt) {
-            const Real bv = vld(Bv + (b2 * NJS + tt) * BW + t - 2 * tt + 2 * P);
-            acc[0][tt] = fmaR<Real>(bv, h[0][t], acc[0][tt]);
-            acc[1][tt] = fmaR<Real>(bv, h[1][t], acc[1][tt]);
-          }
-      if (MASS || ci.last) {
-#pragma unroll
-        for (int v = 0; v < 2; ++v) {
-          const int q1 = v ? qb : qa;
-          if (v && qb == qa) break;
-          GOut* dst = reinterpret_cast<GOut*>(A.G) + ((p3 * NG + g) * nq1 + q1) * nnz2 + pbase;
-#pragma unroll
-          for (int tt = 0; tt < BW; ++tt) dst[tt] = toOut<GOut>(acc[v][tt]);
-          if (sizeof(GOut) < sizeof(Real) && A.Gb && (q1 < A.nbl || q1 >= A.hstart)) {
-            double* dd = A.Gb + ((p3 * NG + g) * A.nbq + edge_row(q1, A.nbl, A.hstart, A.nbq)) * nnz2 + pbase;
-#pragma unroll
-            for (int tt = 0; tt < BW; ++tt) dd[tt] = toD(acc[v][tt]);
-          }
-        }
-      }
-    }
-  }
-}
-
-// Compile-time point patterns of the first and last P+1 rows of a direction
-// (valid when the direction has n_el >= 2P+2 spans, so that the two ends do not
-// meet). Row R from the low end (H = false) or the high end (H = true) has
-// NI = 2R+P+1 points and NJ = R+P+1 band members j = jlo + jj; the overlap of Q_i
-// and Q_j is t in [e_tlo, e_thi) relative to the first point of Q_i, and
-// B_j at that point is entry t + e_toff of its table row.
-__host__ __device__ constexpr int e_ni(int P, int R) { return 2 * R + P + 1; }
-__host__ __device__ constexpr int e_nj(int P, int R) { return R + P + 1; }
-__host__ __device__ constexpr int e_s(int P, int R, int jj) { return R + P - jj; }
-__host__ __device__ constexpr int e_tlo(int P, int R, bool H, int jj) {
-  return !H ? (jj <= P ? 0 : 2 * jj - P)
-            : (e_ni(P, R) - 2 * e_s(P, R, jj) - P - 1 > 0 ? e_ni(P, R) - 2 * e_s(P, R, jj) - P - 1 : 0);
-}
-__host__ __device__ constexpr int e_thi(int P, int R, bool H, int jj) {
-  return !H ? (2 * jj + P + 1 < e_ni(P, R) ? 2 * jj + P + 1 : e_ni(P, R))
-            : e_ni(P, R) - (e_s(P, R, jj) <= P ? 0 : 2 * e_s(P, R, jj) - P);
-}
-__host__ __device__ constexpr int e_toff(int P, int R, bool H, int jj) {
-  return !H ? -(jj <= P ? 0 : 2 * jj - P) : -e_ni(P, R) + 2 * e_s(P, R, jj) + P + 1;
-}
-
-// Stage 2 for edge row R of direction 2 (i2 = R or n2-1-R) at point q1 of pair p3.
-template <int P, bool MASS, typename Real, typename GOut, int R, bool H>
-__device__ __forceinline__ void stage2_edge_row(const StagedArgs& A, int q1, int64_t p3) {
-  constexpr int NT = MASS ? 1 : 9;
-  constexpr int NG = MASS ? 1 : 4;
-  constexpr int NC = MASS ? 1 : 6;
-  constexpr int NI = e_ni(P, R), NJ = e_nj(P, R);
-  constexpr bool ROLL = std::is_same<Real, f2>::value;
-  constexpr int CU = ROLL ? 1 : NC;
-  const Dir& D2 = A.d[1];
-  const int nq1 = A.d[0].nqp, nq2 = D2.nqp, NQ = A.NQ, n2 = D2.n;
-  const int i2 = H ? n2 - 1 - R : R;
-  const int qi = H ? nq2 - NI : 0;
-  const int jlo = H ? n2 - 1 - R - P : 0;
-  const int64_t nnz2 = A.nnz1[1];
-  const Real* T3 = reinterpret_cast<const Real*>(A.T3) + ((p3 * NT) * nq1 + q1) * (int64_t)nq2 + qi;
-  const int64_t tstride = (int64_t)nq1 * nq2;
-  const int64_t pbase = D2.prefix[i2];
-  Real acc[NJ];  // one G group at a time (classes come grouped)
-#pragma unroll(CU)
-  for (int c = 0; c < NC; ++c) {
-    const ClassInfo ci = class_info<ROLL>(c);
-    if (MASS || ci.first)
-#pragma unroll
-      for (int jj = 0; jj < NJ; ++jj) acc[jj] = zeroR<Real>();
-    Real h[NI];
-#pragma unroll
-    for (int t = 0; t < NI; ++t) h[t] = zeroR<Real>();
-#pragma unroll
-    for (int k = 0; k < 2; ++k) {
-      const int term = MASS ? 0 : ci.term[k];
-      if (term < 0 || (MASS && k > 0)) continue;
-      const int l = MASS ? 0 : term / 3, m = MASS ? 0 : term % 3;
-      const int k2 = MASS ? 0 : 2 * (l == 1) + (m == 1);
-      const Real* wrow = tab<Real>(D2.w) + ((size_t)k2 * n2 + i2) * NQ;
-      const Real* trow = T3 + term * tstride;
-#pragma unroll
-      for (int t = 0; t < NI; ++t) h[t] = fmaR<Real>(ro(wrow + t), ro(trow + t), h[t]);
-    }
-    const int g = MASS ? 0 : ci.g;
-    const int b2 = MASS ? 0 : ci.b2;
-#pragma unroll
-    for (int jj = 0; jj < NJ; ++jj) {
-      const Real* brow = tab<Real>(D2.bt) + ((size_t)b2 * n2 + jlo + jj) * NQ + e_toff(P, R, H, jj);
-#pragma unroll
-      for (int t = e_tlo(P, R, H, jj); t < e_thi(P, R, H, jj); ++t)
-        acc[jj] = fmaR<Real>(ro(brow + t), h[t], acc[jj]);
-    }
-    if (MASS || ci.last) {
-      GOut* dst = reinterpret_cast<GOut*>(A.G) + ((p3 * NG + g) * nq1 + q1) * nnz2 + pbase;
-#pragma unroll
-      for (int jj = 0; jj < NJ; ++jj) dst[jj] = toOut<GOut>(acc[jj]);
-      if (sizeof(GOut) < sizeof(Real) && A.Gb && (q1 < A.nbl || q1 >= A.hstart)) {
-        double* dd = A.Gb + ((p3 * NG + g) * A.nbq + edge_row(q1, A.nbl, A.hstart, A.nbq)) * nnz2 + pbase;
-#pragma unroll
-        for (int jj = 0; jj < NJ; ++jj) dd[jj] = toD(acc[jj]);
-      }
-    }
-  }
-}
-
-// K2 on one edge row of direction 2 (R from the low or the high end) with its
-// compile-time point pattern; threads over (p3, q1), so a warp shares one pattern
-// and every lane has work. One instantiation per edge row keeps each row's
-// registers to itself.
-template <int P, bool MASS, typename Real, typename GOut, int R, bool H>
-__global__ void __launch_bounds__(128) k_stage2_edge(StagedArgs A, int64_t np3) {
-  const int nq1 = A.d[0].nqp;
-  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;  // p3 * nq1 + q1
-  if (e >= np3 * nq1) return;
-  stage2_edge_row<P, MASS, Real, GOut, R, H>(A, (int)(e % nq1), e / nq1);
-}
-
-template <int P, bool MASS, typename Real, typename GOut, int B = 0>
-static void launch_stage2_edge(const StagedArgs& A, int nq1, int64_t np3, cudaStream_t s) {
-  k_stage2_edge<P, MASS, Real, GOut, (B <= P ? B : B - P - 1), (B > P)>
-      <<<(unsigned)((np3 * nq1 + 127) / 128), 128, 0, s>>>(A, np3);
-  if constexpr (B + 1 < 2 * P + 2) launch_stage2_edge<P, MASS, Real, GOut, B + 1>(A, nq1, np3, s);
-}
-
-// K1: one thread per (p2, i1, p3): the 2P+1 values of row (i1, i2, i3) in the
-// column block (j2, j3). A block covers 32 consecutive p2 and 4 consecutive i1, so
-// the G rows of overlapping supports are read from L1.
-// EDGE64: the first and last P+1 rows of direction 1 run in FP64 from the edge
-// copy of G (mixed precision), where the large, sign-alternating WQ weights near
-// the boundary amplify FP32 rounding.
-template <int P, bool MASS, typename Real, typename OutT, bool EDGE64>
-__global__ void __launch_bounds__(128) k_stage1(StagedArgs A) {
-  constexpr int BW = 2 * P + 1;
-  constexpr int NG = MASS ? 1 : 4;
-  const Dir& D1 = A.d[0];
-  const Dir& D2 = A.d[1];
-  const Dir& D3 = A.d[2];
-  const int64_t p2 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  const int i1 = blockIdx.y * blockDim.y + threadIdx.y;
-  const int64_t p3 = blockIdx.z;
-  const int64_t nnz2 = A.nnz1[1];
-  const int n1 = D1.n, n2 = D2.n, n3 = D3.n, nq1 = D1.nqp, NQ = A.NQ;
-  if (p2 >= nnz2 || i1 >= n1) return;
-  const int i2 = D2.pair_row[p2], j2 = blo(i2, P) + (int)(p2 - D2.prefix[i2]);
-  const int i3 = D3.pair_row[p3], j3 = blo(i3, P) + (int)(p3 - D3.prefix[i3]);
-  const int qi1 = D1.q0[i1];
-  const bool reg = i1 >= P + 1 && i1 <= n1 - P - 2;
-  const Real* G = reinterpret_cast<const Real*>(A.G) + ((p3 * NG) * nq1) * nnz2 + p2;
-  const int64_t gstride = (int64_t)nq1 * nnz2;  // next group
-  const int64_t N1 = D1.prefix[n1], N2 = D2.prefix[n2];
-  const int bw1 = bw(i1, P, n1), bw2 = bw(i2, P, n2), bw3 = bw(i3, P, n3);
-  const int jlo1 = blo(i1, P);
-  const int64_t row = D3.prefix[i3] * N2 * N1 + (int64_t)bw3 * (D2.prefix[i2] * N1 + (int64_t)bw2 * D1.prefix[i1]);
-  const int64_t base = row + ((int64_t)(j3 - blo(i3, P)) * bw2 + (j2 - blo(i2, P))) * bw1;  // + (j1 - jlo1)
-  OutT* out = reinterpret_cast<OutT*>(A.vals);
-  const Real* w = tab<Real>(D1.w) + (size_t)i1 * NQ;   // kind k at + k * n1 * NQ
-  const Real* bt1 = tab<Real>(D1.bt);
-  const int64_t wk = (int64_t)n1 * NQ;
-  const int64_t bder = (int64_t)n1 * NQ;          // B' table after B
-  Real s[BW];
-#pragma unroll
-  for (int tt = 0; tt < BW; ++tt) s[tt] = zeroR<Real>();
-  if (reg) {
-#pragma unroll
-    for (int t = 0; t <= 2 * P; ++t) {
-      const Real* gq = G + (int64_t)(qi1 + t) * nnz2;
-      Real h0, h1 = zeroR<Real>();
-      if (MASS) {
-        h0 = mulR(w[t], gq[0]);
-      } else {
-        h0 = fmaR<Real>(w[t], gq[0], mulR(w[t + 2 * wk], gq[2 * gstride]));
-        h1 = fmaR<Real>(w[t + wk], gq[gstride], mulR(w[t + 3 * wk], gq[3 * gstride]));
-      }
-#pragma unroll
-      for (int tt = 0; tt < BW; ++tt) {
-        if (t >= 2 * tt - 2 * P && t <= 2 * tt) {
-          const int j1 = i1 - P + tt;
-          const int64_t idx = (int64_t)j1 * NQ + (qi1 + t - D1.q0[j1]);
-          if (MASS)
-            s[tt] = fmaR<Real>(bt1[idx], h0, s[tt]);
-          else
-            s[tt] = fmaR<Real>(bt1[idx + bder], h1, fmaR<Real>(bt1[idx], h0, s[tt]));
-        }
-      }
-    }
-#pragma unroll
-    for (int tt = 0; tt < BW; ++tt) out[base + tt] = toOut<OutT>(s[tt]);  // j1 - jlo1 = tt for regular rows
-  } else if (EDGE64 && A.Gb) {
-    const double* Gd = A.Gb + ((p3 * NG) * A.nbq) * nnz2 + p2;
-    stage1_edge<P, MASS, double, OutT, true>(Gd, (int64_t)A.nbq * nnz2, nnz2, A.w1d + (size_t)i1 * NQ, wk, A.bt1d,
-                                             bder, D1, i1, n1, NQ, A.nbl, A.hstart, A.nbq, out, base - jlo1);
-  } else {
-    stage1_edge<P, MASS, Real, OutT, false>(G, gstride, nnz2, w, wk, bt1, bder, D1, i1, n1, NQ, 0, 0, 0, out,
-                                            base - jlo1);
-  }
-}
-
-__global__ void k_pair_rows(const int64_t* __restrict__ prefix, int n, int* __restrict__ pair_row) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  for (int64_t k = prefix[i]; k < prefix[i + 1]; ++k) pair_row[k] = i;
-}
-
-}  // namespace
-
-// Scratch of the staged path, allocated on first use and owned by the plan.
-static wq_status staged_scratch(wq_plan_s* pl, size_t t3, size_t g, size_t gb, bool need_f32, cudaStream_t s) {
-  t3 = std::max<size_t>(16, t3);
-  g = std::max<size_t>(16, g);
-  if (pl->stg_a_bytes < t3 || pl->stg_b_bytes < g) {
-    if (pl->stg_a) cudaFree(pl->stg_a);
-    if (pl->stg_b) cudaFree(pl->stg_b);
-    pl->stg_a = pl->stg_b = nullptr;
-    pl->stg_a_bytes = pl->stg_b_bytes = 0;
-    cudaError_t e = cudaMalloc(&pl->stg_a, t3);
-    if (e == cudaSuccess) e = cudaMalloc(&pl->stg_b, g);
-    if (e != cudaSuccess) {
-      cudaGetLastError();
-      if (pl->stg_a) cudaFree(pl->stg_a);
-      pl->stg_a = nullptr;
-      return set_error(WQ_ERR_OOM, "staged assembly scratch (T3, G) does not fit in device memory");
-    }
-    pl->stg_a_bytes = t3;
-    pl->stg_b_bytes = g;
-  }
-  if (pl->stg_c_bytes < gb) {
-    if (pl->stg_c) cudaFree(pl->stg_c);
-    pl->stg_c = nullptr;
-    pl->stg_c_bytes = 0;
-    cudaError_t e = cudaMalloc(&pl->stg_c, gb);
-    if (e != cudaSuccess) {
-      cudaGetLastError();
-      pl->stg_c = nullptr;
-      return set_error(WQ_ERR_OOM, "staged assembly scratch (FP64 edge copy of G) does not fit in device memory");
-    }
-    pl->stg_c_bytes = gb;
-  }
-  if (!pl->coefT) {
-    cudaError_t e = cudaMalloc(&pl->coefT, sizeof(double) * 8 * (size_t)pl->n_qp_total);
-    if (e != cudaSuccess) return wq::cuda_error(e, "transposed coefficient allocation");
-  }
-  if (need_f32)
-    for (int l = 0; l < 3; ++l)
-      if (!pl->dir[l].tab32) {
-        const size_t nt = (size_t)6 * pl->dir[l].n * pl->nq_max;  // 4 rule kinds + 2 basis tables
-        cudaError_t e = cudaMalloc(&pl->dir[l].tab32, sizeof(float) * nt);
-        if (e != cudaSuccess) return wq::cuda_error(e, "float table allocation");
-      }
-  for (int l = 1; l < 3; ++l)
-    if (!pl->dir[l].pair_row) {
-      cudaError_t e = cudaMalloc(&pl->dir[l].pair_row, sizeof(int) * (size_t)std::max<int64_t>(1, pl->nnz1[l]));
-      if (e != cudaSuccess) return wq::cuda_error(e, "pair index allocation");
-      k_pair_rows<<<(pl->dir[l].n + 127) / 128, 128, 0, s>>>(pl->dir[l].prefix, pl->dir[l].n, pl->dir[l].pair_row);
-      count_launch();
-    }
-  return WQ_OK;
-}
-
-// The q1 points that the first and last p+1 rows of direction 1 read: [0, nbl) and
-// [hstart, nqp) (Q_i = points inside the support of B_i; the whole range when the
-// two ends meet).
-static void edge_points(const wq_plan_s* pl, int* nbl, int* hstart, int* nbq) {
-  const int p = pl->p, ne = pl->dir[0].n_el, nqp = (int)pl->nqp[0], n1 = (int)pl->n[0];
-  const int il = std::min(p, n1 - 1), ih = std::max(n1 - p - 1, 0);
-  const int hi = std::min(ne, il + 1), lo = std::max(0, ih - p);
-  *nbl = (hi == ne ? nqp - 1 : 2 * hi + p - 2) + 1;
-  *hstart = lo == 0 ? 0 : 2 * lo + p;
-  if (*hstart <= *nbl) *nbl = *hstart = nqp;
-  *nbq = *nbl + (nqp - *hstart);
-}
-
-// Real: arithmetic of stages 3 and 2 (and T3); R1: arithmetic of stage 1 (and G).
-template <int P, bool MASS, typename Real, typename R1, typename OutT>
-static wq_status staged_t(wq_plan_s* pl, const double* kappa, void* vals, cudaStream_t s) {
-  const int NT = MASS ? 1 : 9, NG = MASS ? 1 : 4;
-  constexpr bool EDGE64 = sizeof(R1) < sizeof(Real);
-  int nbl = 0, hstart = 0, nbq = 0;
-  if (EDGE64) edge_points(pl, &nbl, &hstart, &nbq);
-  wq_status st = staged_scratch(pl, (size_t)pl->nnz1[2] * NT * pl->nqp[0] * pl->nqp[1] * sizeof(Real),
-                                (size_t)pl->nnz1[2] * NG * pl->nqp[0] * pl->nnz1[1] * sizeof(R1),
-                                (size_t)pl->nnz1[2] * NG * nbq * pl->nnz1[1] * sizeof(double),
-                                sizeof(Real) == sizeof(float) || sizeof(R1) == sizeof(float), s);
-  if (st != WQ_OK) return st;
-  constexpr bool F2 = std::is_same<Real, f2>::value, F2_1 = std::is_same<R1, f2>::value;
-  static_assert(!F2_1 || F2, "double-float stage 1 needs double-float stages 3 and 2");
-  StagedArgs A, A1;  // A: tables in Real (stages 3, 2); A1: tables in R1 (stage 1)
-  for (int l = 0; l < 3; ++l) {
-    DirData& d = pl->dir[l];
-    const void* w32 = d.w;
-    const void* bt32 = d.bt;
-    if (F2) {
-      const int64_t nw = (int64_t)4 * d.n * pl->nq_max, nb = (int64_t)2 * d.n * pl->nq_max;
-      if (!d.tabf2) {
-        cudaError_t e = cudaMalloc(&d.tabf2, sizeof(f2) * (size_t)(nw + nb));
-        if (e != cudaSuccess) return wq::cuda_error(e, "double-float table allocation");
-      }
-      f2* t = reinterpret_cast<f2*>(d.tabf2);
-      k_to_f2<<<(unsigned)((nw + 255) / 256), 256, 0, s>>>(d.w, t, nw);
-      k_to_f2<<<(unsigned)((nb + 255) / 256), 256, 0, s>>>(d.bt, t + nw, nb);
-      count_launch(2);
-      A.d[l] = Dir{d.n, d.nqp, d.q0, d.nq, t, t + nw, d.prefix, d.pair_row};
-      A.nnz1[l] = A1.nnz1[l] = pl->nnz1[l];
-      if (F2_1) {
-        A1.d[l] = A.d[l];
-        continue;
-      }
-    }
-    if (sizeof(Real) == sizeof(float) || sizeof(R1) == sizeof(float)) {
-      const int64_t nw = (int64_t)4 * d.n * pl->nq_max, nb = (int64_t)2 * d.n * pl->nq_max;
-      k_to_float<<<(unsigned)((nw + 255) / 256), 256, 0, s>>>(d.w, d.tab32, nw);
-      k_to_float<<<(unsigned)((nb + 255) / 256), 256, 0, s>>>(d.bt, d.tab32 + nw, nb);
-      count_launch(2);
-      w32 = d.tab32;
-      bt32 = d.tab32 + nw;
-    }
-    const bool f = sizeof(Real) == sizeof(float), f1 = sizeof(R1) == sizeof(float);
-    if (!F2) A.d[l] = Dir{d.n, d.nqp, d.q0, d.nq, f ? w32 : d.w, f ? bt32 : d.bt, d.prefix, d.pair_row};
-    A1.d[l] = Dir{d.n, d.nqp, d.q0, d.nq, f1 ? w32 : d.w, f1 ? bt32 : d.bt, d.prefix, d.pair_row};
-    A.nnz1[l] = A1.nnz1[l] = pl->nnz1[l];
-  }
-  A.NQ = A1.NQ = pl->nq_max;
-  const int nq1 = (int)pl->nqp[0], nq2 = (int)pl->nqp[1], nq3 = (int)pl->nqp[2];
-  const int64_t NQP = pl->n_qp_total;
-  Real* cT = reinterpret_cast<Real*>(pl->coefT);
-  A.cT = A1.cT = cT;
-  A.kappaT = A1.kappaT = kappa ? cT + 7 * NQP : nullptr;
-  A.T3 = A1.T3 = pl->stg_a;
-  A.G = A1.G = pl->stg_b;
-  A.vals = A1.vals = vals;
-  A.Gb = A1.Gb = EDGE64 ? reinterpret_cast<double*>(pl->stg_c) : nullptr;
-  A.w1d = A1.w1d = pl->dir[0].w;
-  A.bt1d = A1.bt1d = pl->dir[0].bt;
-  A.nbl = A1.nbl = nbl;
-  A.hstart = A1.hstart = hstart;
-  A.nbq = A1.nbq = nbq;
-  // transposed coefficients (the slots this matrix uses) and kappa, in Real
-  {
-    dim3 blk(32, 8), grd((nq1 + 31) / 32, (nq2 + 31) / 32, 7 * nq3 + (kappa ? nq3 : 0));
-    k_transpose_coef<Real><<<grd, blk, 0, s>>>(pl->coef, kappa, cT, cT + 7 * NQP, nq1, nq2, nq3, 7);
-  }
-  const int n1 = (int)pl->n[0], n2 = (int)pl->n[1], n3 = (int)pl->n[2];
-  k_stage3<P, MASS, Real><<<dim3(n3, (unsigned)(((int64_t)nq1 * nq2 + 127) / 128)), 128, 0, s>>>(A);
-  int r_lo = P + 1, r_hi = n2 - P - 1;  // regular rows [r_lo, r_hi)
-  if (r_hi <= r_lo) r_lo = r_hi = n2;   // no regular rows: every row takes the boundary path
-  const int64_t np3 = pl->nnz1[2];
-  // Regular rows: k_stage2_reg (tables in shared memory, 32 rows per block) unless
-  // the FP64 pipe, not L1, bounds the flat mapping (FP64, P <= 4: measured at 97%
-  // of the DFMA rate) and 32-row blocks would leave more than 4% of lanes idle.
-  const int nreg = r_hi - r_lo;
-  const bool flat = std::is_same<Real, double>::value && P <= 4 && 32 * ((nreg + 31) / 32) * 100 > 104 * nreg;
-  if (nreg > 0 && flat)
-    k_stage2<P, MASS, Real, true, R1>
-        <<<dim3((unsigned)(((int64_t)nreg * nq1 + 127) / 128), (unsigned)np3), 128, 0, s>>>(A, r_lo, r_hi);
-  else if (nreg > 0)
-    k_stage2_reg<P, MASS, Real, R1>
-        <<<dim3((unsigned)((nreg + 31) / 32), (unsigned)np3), dim3(32, 4), 0, s>>>(A, r_lo, r_hi);
-  const int nb = r_lo + (n2 - r_hi);
-  const bool edge2 = pl->dir[1].n_el >= 2 * P + 2;  // edge rows with compile-time patterns
-  if (edge2)
-    launch_stage2_edge<P, MASS, Real, R1>(A, nq1, np3, s);
-  else
-    k_stage2<P, MASS, Real, false, R1>
-        <<<dim3((unsigned)(((int64_t)nb * nq1 + 127) / 128), (unsigned)np3), 128, 0, s>>>(A, r_lo, r_hi);
-  k_stage1<P, MASS, R1, OutT, EDGE64>
-      <<<dim3((unsigned)((pl->nnz1[1] + 31) / 32), (n1 + 3) / 4, (unsigned)np3), dim3(32, 4), 0, s>>>(A1);
-  count_launch(3 + (r_hi > r_lo ? 1 : 0) + (edge2 ? 2 * P + 2 : 1));
-  WQ_CUDA_TRY(cudaGetLastError(), "staged assembly launch");
-  return WQ_OK;
-}
-
-template <bool MASS, typename Real, typename R1, typename OutT>
-static wq_status staged_dispatch(wq_plan_s* pl, const double* kappa, void* vals, cudaStream_t s) {
-  switch (pl->p) {
-    case 2: return staged_t<2, MASS, Real, R1, OutT>(pl, kappa, vals, s);
-    case 3: return staged_t<3, MASS, Real, R1, OutT>(pl, kappa, vals, s);
-    case 4: return staged_t<4, MASS, Real, R1, OutT>(pl, kappa, vals, s);
-    case 5: return staged_t<5, MASS, Real, R1, OutT>(pl, kappa, vals, s);
-    case 6: return staged_t<6, MASS, Real, R1, OutT>(pl, kappa, vals, s);
-    case 7: return staged_t<7, MASS, Real, R1, OutT>(pl, kappa, vals, s);
-    case 8: return staged_t<8, MASS, Real, R1, OutT>(pl, kappa, vals, s);
-    default: return set_error(WQ_ERR_UNSUPPORTED, "degree out of range");
-  }
-}
+wq_status launch_staged_p2(wq_plan_s*, bool, const double*, void*, int, int, cudaStream_t);
+wq_status launch_staged_p3(wq_plan_s*, bool, const double*, void*, int, int, cudaStream_t);
+wq_status launch_staged_p4(wq_plan_s*, bool, const double*, void*, int, int, cudaStream_t);
+wq_status launch_staged_p5(wq_plan_s*, bool, const double*, void*, int, int, cudaStream_t);
+wq_status launch_staged_p6(wq_plan_s*, bool, const double*, void*, int, int, cudaStream_t);
+wq_status launch_staged_p7(wq_plan_s*, bool, const double*, void*, int, int, cudaStream_t);
+wq_status launch_staged_p8(wq_plan_s*, bool, const double*, void*, int, int, cudaStream_t);
 
 wq_status launch_staged(wq_plan_s* pl, bool mass, const double* kappa, void* vals, int value_dtype, int precision,
                         cudaStream_t s) {
-  const bool v32 = value_dtype == WQ_VALUES_F32;
-  if (precision == WQ_PREC_FP64)
-    return mass ? staged_dispatch<true, double, double, double>(pl, kappa, vals, s)
-                : staged_dispatch<false, double, double, double>(pl, kappa, vals, s);
-  if (precision == WQ_PREC_F32X2) {
-    if (v32)
-      return mass ? staged_dispatch<true, f2, f2, float>(pl, kappa, vals, s)
-                  : staged_dispatch<false, f2, f2, float>(pl, kappa, vals, s);
-    return mass ? staged_dispatch<true, f2, f2, double>(pl, kappa, vals, s)
-                : staged_dispatch<false, f2, f2, double>(pl, kappa, vals, s);
+  switch (pl->p) {
+    case 2: return launch_staged_p2(pl, mass, kappa, vals, value_dtype, precision, s);
+    case 3: return launch_staged_p3(pl, mass, kappa, vals, value_dtype, precision, s);
+    case 4: return launch_staged_p4(pl, mass, kappa, vals, value_dtype, precision, s);
+    case 5: return launch_staged_p5(pl, mass, kappa, vals, value_dtype, precision, s);
+    case 6: return launch_staged_p6(pl, mass, kappa, vals, value_dtype, precision, s);
+    case 7: return launch_staged_p7(pl, mass, kappa, vals, value_dtype, precision, s);
+    case 8: return launch_staged_p8(pl, mass, kappa, vals, value_dtype, precision, s);
+    default: return set_error(WQ_ERR_UNSUPPORTED, "degree out of range");
   }
-  if (precision == WQ_PREC_MIXED) {
-    if (v32)
-      return mass ? staged_dispatch<true, f2, float, float>(pl, kappa, vals, s)
-                  : staged_dispatch<false, f2, float, float>(pl, kappa, vals, s);
-    return mass ? staged_dispatch<true, f2, float, double>(pl, kappa, vals, s)
-                : staged_dispatch<false, f2, float, double>(pl, kappa, vals, s);
-  }
-  if (v32)
-    return mass ? staged_dispatch<true, float, float, float>(pl, kappa, vals, s)
-                : staged_dispatch<false, float, float, float>(pl, kappa, vals, s);
-  return mass ? staged_dispatch<true, float, float, double>(pl, kappa, vals, s)
-              : staged_dispatch<false, float, float, double>(pl, kappa, vals, s);
 }
 
 }  // namespace wq
