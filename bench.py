@@ -1,15 +1,26 @@
 """Benchmark: WQ 3D stiffness assembly throughput (nnz/s) on one or more GB300s.
 
 One step = the whole path from control points already resident in HBM to the
-CSR stiffness matrix: every set-up kernel of the plan (points, B-spline tables,
-exact integrals, WQ rules, CSR pattern, coefficients; wq_plan_refresh) followed
-by the fused sum-factorised FP64 assembly (wq_assemble_stiffness). Workload:
-p = 4, 64 elements per direction (N_DOF = 68^3, nnz = 592^3), degree-4 spline
-cube with control points at the Greville abscissae plus a seeded +-0.05 h
-perturbation. Every step writes 1.66 GB of values and 0.83 GB of column
-indices, far more than the 126 MB L2, so no L2 flush is inserted.
+CSR stiffness matrix: every set-up kernel of the plan (wq_plan_refresh: points,
+B-spline tables, exact integrals, WQ rules, CSR pattern, coefficients) followed
+by the staged sum-factorised FP64 assembly (wq_assemble_stiffness: three mode
+products over the whole mesh, Eq. (sumfactorization)).
+
+Default workload: the largest single-GPU case of the degree sweep at about 1M
+DOF, p = 8 with 93 elements per direction (N_DOF = 101^3, nnz = 1645^3 =
+4.45e9, 35.6 GB of FP64 values), a degree-8 spline cube with control points at
+the Greville abscissae plus a seeded +-0.05 h perturbation. Each step writes
+35.6 GB of values and 17.8 GB of column indices, far more than the 126 MB L2,
+so no L2 flush is inserted.
+
+The same JSON line carries the precision study on p = 5, 128^3 (N_DOF = 133^3,
+nnz = 2.94e9): FP64 against every reduced-precision mode, with the speed-up and
+the worst row-relative and Frobenius error against the FP64 values on sampled
+rows; the p = 4, 64^3 assembly; the 64-patch batched launch; the end-to-end
+call with host buffers; and the CPU oracle on the host cores.
 
   python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+                  [--workload sweep8|sweep2..sweep6|p5_128|p4_64|small]
 
 Under torchrun each rank assembles its own independent copy of the workload
 (weak scaling, no data-path collective); rank 0 prints one JSON line.
@@ -33,9 +44,9 @@ sys.path.insert(0, ROOT)
 METRIC = "WQ 3D stiffness nnz/s and % of HBM-write roofline; mixed vs FP64 at ≤1e-6 error"
 
 # DRAM traffic of one FP64 staged stiffness assembly (k_stage3, k_stage2 and its
-# edge-row kernels, k_stage1) at p = 4, 64^3, from one ncu capture of
-# dram__bytes_read.sum + dram__bytes_write.sum (profiles/assembly_traffic_p4_nel64.md).
-# It is reported only while the kernel sources still hash to the captured value.
+# edge-row kernels, k_stage1), from one ncu capture of dram__bytes_read.sum +
+# dram__bytes_write.sum per workload. It is reported only while the kernel
+# sources still hash to the captured value.
 TRAFFIC_CAPTURE = {"p": 4, "n_el": 64, "bytes": 3997.57e6 + 4354.18e6, "sources": "17c1a0e7441ac796",
                    "files": ("paper_1605_01238_gb300/csrc/wq_staged_impl.cuh", "paper_1605_01238_gb300/csrc/wq_internal.h")}
 
@@ -114,6 +125,55 @@ def algorithmic_flops(n: tuple, p: int, mass: bool = False) -> float:
         s2 = d1[0] * nnz1[2] * sum(9 * a + 6 * b for a, b in zip(d2[1], d2[2]))
         s1 = nnz1[1] * nnz1[2] * sum(4 * a + 2 * b for a, b in zip(d1[1], d1[2]))
     return 2.0 * (s1 + s2 + s3)
+
+
+# ---------------------------------------------------------------------------
+# Workloads: seeded perturbed spline cubes (Section 7.2's single-patch tests).
+
+WORKLOADS = {
+    "sweep8": "degree sweep at ~1M DOF, p=8 (largest single-GPU case)",
+    "sweep6": "degree sweep at ~1M DOF, p=6",
+    "sweep5": "degree sweep at ~1M DOF, p=5",
+    "sweep4": "degree sweep at ~1M DOF, p=4",
+    "sweep3": "degree sweep at ~1M DOF, p=3",
+    "sweep2": "degree sweep at ~1M DOF, p=2",
+    "p5_128": "precision workload, p=5",
+    "p4_64": "p=4 mesh",
+    "small": "p=2 mesh",
+}
+
+
+def make_workload(name: str):
+    import wq_synth as ws
+    if name.startswith("sweep"):
+        return ws.workload_sweep(int(name[5:]))
+    return {"p5_128": ws.workload_p5_128, "p4_64": ws.workload_p4_64, "small": ws.workload_small}[name]()
+
+
+def workload_sizes(patch):
+    """(n per direction, N_DOF, nnz) of a patch, from its knot vectors (Section 3:
+    nnz = prod_l sum_i |I_{l,i}|)."""
+    n = patch.n
+    nnz = 1
+    for nl in n:
+        nnz *= sum(_dir_census(nl, patch.p)[3])
+    return n, int(np.prod(n)), int(nnz)
+
+
+def workload_config(name: str, patch, n_gpus: int) -> dict:
+    """The `config` object of a bench line; both arms print the same one."""
+    n, n_dof, nnz = workload_sizes(patch)
+    ne = patch.n_el
+    els = f"{ne[0]}^3" if ne[0] == ne[1] == ne[2] else "x".join(map(str, ne))
+    return {"workload": f"WQ stiffness, {WORKLOADS.get(name, name)}: p={patch.p}, {els} elements, "
+                        f"N_DOF={n_dof}, nnz={nnz} per GPU",
+            "p": patch.p, "n_el": list(ne), "n_dof": n_dof, "nnz_per_gpu": nnz,
+            "geometry": f"degree-{patch.p} spline cube, Greville control points + seeded U[-0.05h, 0.05h] "
+                        f"(seed {patch.meta.get('seed')})",
+            "step": "plan refresh (points, tables, integrals, rules, CSR pattern, coefficients) "
+                    "+ FP64 stiffness assembly",
+            "l2": f"no flush: each step writes {12 * nnz / 1e9:.1f} GB (values + columns) > 126 MB L2",
+            "parallelism": f"{n_gpus} independent patches, one per GPU"}
 
 
 class ClockSampler:
@@ -222,6 +282,19 @@ def cpu_oracle_sample(patch, seconds: float, seed: int, which: str = "stiffness"
             "setup_seconds": setup_s}
 
 
+def timed(torch, stream, fn, reps: int = 3) -> float:
+    """Mean CUDA-event milliseconds of fn() on `stream` after one warm-up call."""
+    fn()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(reps):
+        fn()
+    b.record(stream)
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / reps
+
+
 def run_batch_variant(wq, torch, stream, count: int = 64):
     """64 seeded cubes (n_el in [8, 48]^3, p in {2, 3, 4, 5}), stiffness + mass, one
     persistent graph-captured launch, tiles from the autotuner."""
@@ -234,16 +307,7 @@ def run_batch_variant(wq, torch, stream, count: int = 64):
     S = [torch.empty(pl.nnz, dtype=torch.float64, device="cuda") for pl in plans]
     M = [torch.empty(pl.nnz, dtype=torch.float64, device="cuda") for pl in plans]
     batch = wq.Batch(plans, stiffness=S, mass=M)
-    batch.launch()
-    torch.cuda.synchronize()
-    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    reps = 3
-    a.record(stream)
-    for _ in range(reps):
-        batch.launch()
-    b.record(stream)
-    torch.cuda.synchronize()
-    ms = a.elapsed_time(b) / reps
+    ms = timed(torch, stream, batch.launch)
     out = {"patches": count, "nnz_written": batch.nnz_total, "work_items": batch.n_items, "grid": batch.grid,
            "ms_per_launch": ms, "nnz_per_s": batch.nnz_total / (ms * 1e-3), "tiles": {str(k): v for k, v in tiles.items()},
            "note": "stiffness + mass of every patch, FP64, one graph launch"}
@@ -255,13 +319,110 @@ def run_batch_variant(wq, torch, stream, count: int = 64):
     return out
 
 
+def sampled_errors(plan, torch, variants, count: int = 4096, seed: int = 77):
+    """Worst row-relative error (max |d| over a row / the row's largest FP64 entry) and
+    Frobenius error (||d||_F / ||a||_F over the sampled rows) of reduced-precision
+    stiffness variants against the FP64 path, on sampled rows (every boundary/interior
+    class forced in), measured live on this GPU. variants: name -> (precision, dtype)."""
+    from wq_synth import sample_rows
+    rp = plan.pattern()[0].cpu().numpy()
+    rows = np.asarray(sample_rows(plan.n, plan.p, count, seed=seed))
+    idx = np.concatenate([np.arange(rp[r], rp[r + 1]) for r in rows])
+    starts = np.concatenate([[0], np.cumsum([rp[r + 1] - rp[r] for r in rows])[:-1]])
+    idx_d = torch.as_tensor(idx, device="cuda")
+    ref = plan.stiffness()[idx_d].cpu().numpy()
+    torch.cuda.empty_cache()
+    den = np.maximum.reduceat(np.abs(ref), starts)
+    out = {}
+    for name, (prec, dt) in variants.items():
+        got = plan.stiffness(precision=prec, dtype=dt)[idx_d].double().cpu().numpy()
+        d = got - ref
+        out[name] = {"max_row_rel": float((np.maximum.reduceat(np.abs(d), starts) / den).max()),
+                     "frobenius_rel": float(np.linalg.norm(d) / np.linalg.norm(ref))}
+        torch.cuda.empty_cache()
+    return out, len(rows)
+
+
+PRECISION_MODES = {
+    # name: (precision, value dtype, what)
+    "mixed": ("mixed", "f32", "q3, q2 mode products in double-float, q1 in FP32 (FP64 edge rows)"),
+    "mixed_f64vals": ("mixed", "f64", "as mixed, FP64 values"),
+    "f32x2": ("f32x2", "f64", "double-float (pairs of floats) in all three mode products"),
+    "fp32": ("fp32", "f32", "FP32 in all three mode products"),
+}
+
+
+def precision_study(wq, torch, stream, name: str = "p5_128"):
+    """FP64 against every reduced-precision mode on one workload: assembly time,
+    speed-up and errors against the FP64 values on sampled rows."""
+    patch = make_workload(name)
+    plan = wq.Plan(patch.p, patch.knots, patch.ctrl)
+    nnz = plan.nnz
+    v64 = torch.empty(nnz, dtype=torch.float64, device="cuda")
+    v32 = torch.empty(nnz, dtype=torch.float32, device="cuda")
+    dts = {"f64": torch.float64, "f32": torch.float32}
+    fp64_ms = timed(torch, stream, lambda: plan.stiffness(out=v64))
+    modes = {}
+    for mode, (prec, vd, what) in PRECISION_MODES.items():
+        out = v64 if vd == "f64" else v32
+        ms = timed(torch, stream, lambda: plan.stiffness(out=out, dtype=dts[vd], precision=prec))
+        modes[mode] = {"values": vd, "ms": ms, "nnz_per_s": nnz / (ms * 1e-3), "speedup_vs_fp64": fp64_ms / ms,
+                       "what": what}
+    del v64, v32
+    torch.cuda.empty_cache()
+    errs, rows = sampled_errors(plan, torch, {m: (PRECISION_MODES[m][0], dts[PRECISION_MODES[m][1]])
+                                              for m in PRECISION_MODES})
+    for m, e in errs.items():
+        modes[m].update(e)
+    modes["mixed"]["bar"] = 1e-6
+    modes["mixed_f64vals"]["bar"] = 1e-6
+    modes["f32x2"]["bar"] = 1e-12
+    plan.close()
+    torch.cuda.empty_cache()
+    n, n_dof, _ = workload_sizes(patch)
+    return {"workload": f"p={patch.p}, {patch.n_el[0]}^3 elements, N_DOF={n_dof}, nnz={nnz}",
+            "fp64": {"ms": fp64_ms, "nnz_per_s": nnz / (fp64_ms * 1e-3)},
+            "modes": modes, "error_rows": rows,
+            "error_reference": "FP64 path on the same GPU (itself within 1e-12 of the oracle)"}
+
+
+def assembly_only(wq, torch, stream, name: str):
+    patch = make_workload(name)
+    plan = wq.Plan(patch.p, patch.knots, patch.ctrl)
+    v = torch.empty(plan.nnz, dtype=torch.float64, device="cuda")
+    ms = timed(torch, stream, lambda: plan.stiffness(out=v))
+    out = {"workload": f"p={patch.p}, {patch.n_el[0]}^3 elements, nnz={plan.nnz}", "fp64_ms": ms,
+           "fp64_nnz_per_s": plan.nnz / (ms * 1e-3),
+           "flop_per_nnz": algorithmic_flops(plan.n, patch.p) / plan.nnz}
+    plan.close()
+    del v
+    torch.cuda.empty_cache()
+    return out
+
+
+def host_buffer(torch, count: int):
+    """A float64 host array of `count` elements, page-locked with cudaHostRegister
+    (exact size; torch's pinned allocator rounds up to a power of two)."""
+    arr = np.empty(count, dtype=np.float64)
+    try:
+        cr = torch._C._cudart
+        ok = cr.cudaHostRegister(arr.ctypes.data, arr.nbytes, 0) == cr.cudaError.success
+    except Exception:
+        ok = False
+    return arr, ok
+
+
+def release_host_buffer(torch, arr, registered: bool) -> None:
+    if registered:
+        torch._C._cudart.cudaHostUnregister(arr.ctypes.data)
+
+
 def run_reference(args):
     """--impl reference: the CPU oracle, as it stands, on the machine's host cores."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
-    from wq_synth import workload_p4_64
-    patch = workload_p4_64()
+    patch = make_workload(args.workload)
     from oracle import Oracle3D, rows_c
     from wq_synth import sample_rows
     threads = os.cpu_count() or 1
@@ -271,17 +432,14 @@ def run_reference(args):
     rows_c(orc, probe, "stiffness", threads=threads)
     per_row = (time.perf_counter() - t0) / len(probe)
     per_step = max(threads, int(args.ref_step_seconds / max(per_row, 1e-6)))
-    rates = []
     total_nnz, total_s = 0, 0.0
     for step in range(args.warmup + args.steps):
         rows = sample_rows(orc.n, orc.p, per_step, seed=9000 + step)
         t0 = time.perf_counter()
         vals = rows_c(orc, rows, "stiffness", threads=threads)
         dt = time.perf_counter() - t0
-        nnz = sum(len(v) for v in vals)
         if step >= args.warmup:
-            rates.append(nnz / dt)
-            total_nnz += nnz
+            total_nnz += sum(len(v) for v in vals)
             total_s += dt
     value = total_nnz / total_s
     line = {
@@ -289,45 +447,22 @@ def run_reference(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic (seeded perturbed spline cube)",
-        "config": {"workload": "WQ stiffness, p=4, 64^3 elements, N_DOF=68^3, nnz=592^3", "p": 4,
-                   "n_el": 64, "n_dof": int(np.prod(orc.n)), "nnz": int(np.prod([sum(len(I) for I in d.I)
-                                                                                 for d in orc.dirs]))},
+        "config": workload_config(args.workload, patch, args.gpus),
         "cpu_baseline": {"value": value, "unit": "nnz/s", "cores": threads, "kind": "oracle",
-                         "sample": f"{per_step} seeded rows per step (C nested WQ sums, all terms)"},
+                         "sample": f"{per_step} seeded rows per step of the same workload (C nested WQ sums, "
+                                   f"all nine terms)"},
         "e2e": {"value": value, "unit": "nnz/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
     return 0
 
 
-def variant_errors(plan, torch, count: int = 4096, seed: int = 77):
-    """Worst row-relative error (max |d| over a row / the row's largest FP64 entry) of each
-    reduced-precision stiffness variant against the FP64 path, on sampled rows (every
-    boundary/interior class forced in), measured live on this GPU."""
-    from wq_synth import sample_rows
-    rp = plan.pattern()[0].cpu().numpy()
-    rows = np.asarray(sample_rows(plan.n, plan.p, count, seed=seed))
-    idx = np.concatenate([np.arange(rp[r], rp[r + 1]) for r in rows])
-    starts = np.concatenate([[0], np.cumsum([rp[r + 1] - rp[r] for r in rows])[:-1]])
-    idx_d = torch.as_tensor(idx, device="cuda")
-    ref = plan.stiffness()[idx_d].cpu().numpy()
-    den = np.maximum.reduceat(np.abs(ref), starts)
-    out = {}
-    for prec, dt in (("mixed", torch.float32), ("f32x2", torch.float64), ("fp32", torch.float32)):
-        got = plan.stiffness(precision=prec, dtype=dt)[idx_d].double().cpu().numpy()
-        out[prec] = float((np.maximum.reduceat(np.abs(got - ref), starts) / den).max())
-        torch.cuda.empty_cache()
-    return out, len(rows)
-
-
 def run_ours(args):
     import torch
 
     import paper_1605_01238_gb300 as wq
-    from wq_synth import perturbed_cube, workload_p4_64
     rank, world, local, dist = dist_setup(args.gpus)
-    patch = workload_p4_64() if (args.p, args.nel) == (4, 64) else \
-        perturbed_cube(args.p, args.nel, seed=1605 + 1)
+    patch = make_workload(args.workload)
     p = patch.p
     plan = wq.Plan(p, patch.knots, patch.ctrl)
     plan.set_algorithm(args.algo)
@@ -372,56 +507,41 @@ def run_ours(args):
     kernel_ms = statistics.mean(a.elapsed_time(b) for a, b in kev)
     plan.sync_check()
     value = aggregate_value(world, nnz, ms_step)
+    config = workload_config(args.workload, patch, args.gpus)
     if args.steps_only:
         if rank == 0:
             print(json.dumps({"metric": METRIC, "value": value, "unit": "nnz/s", "ms_per_step": ms_step,
-                              "assembly_ms": kernel_ms, "p": p, "n_el": args.nel, "nnz": nnz, "algo": args.algo,
+                              "assembly_ms": kernel_ms, "config": config, "algo": args.algo,
                               "gpu_launches": int(launches)}), flush=True)
         plan.close()
         if dist is not None:
             dist.destroy_process_group()
         return 0
 
-    # variants (not part of the headline): assembly alone, mass, FP32 contractions
-    def timed(fn, reps=5):
-        fn()
-        torch.cuda.synchronize()
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        for _ in range(reps):
-            fn()
-        b.record(stream)
-        torch.cuda.synchronize()
-        return a.elapsed_time(b) / reps
+    # variants on the headline workload (not part of the headline value)
+    mass_ms = timed(torch, stream, lambda: plan.mass(out=vals))
+    refresh_ms = timed(torch, stream, lambda: plan.refresh(ctrl_d))
 
-    mass_ms = timed(lambda: plan.mass(out=vals))
-    vals32 = torch.empty(nnz, dtype=torch.float32, device="cuda")
-    f32_ms = timed(lambda: plan.stiffness(out=vals32, dtype=torch.float32, precision="fp32"))
-    f32_f64_ms = timed(lambda: plan.stiffness(out=vals, precision="fp32"))
-    mix_ms = timed(lambda: plan.stiffness(out=vals32, dtype=torch.float32, precision="mixed"))
-    mix_f64_ms = timed(lambda: plan.stiffness(out=vals, precision="mixed"))
-    f2_ms = timed(lambda: plan.stiffness(out=vals, precision="f32x2"))
-    plan.set_algorithm("fused")
-    f32f_ms = timed(lambda: plan.stiffness(out=vals32, dtype=torch.float32, precision="fp32"))
-    f64f_ms = timed(lambda: plan.stiffness(out=vals))
-    plan.set_algorithm(args.algo)
-    refresh_ms = timed(lambda: plan.refresh(ctrl_d))
-    del vals32
-    torch.cuda.empty_cache()
-    errs, err_rows = variant_errors(plan, torch)
-    batch_line = run_batch_variant(wq, torch, stream) if args.batch else None
-
-    # end to end through the C ABI with host buffers (pinned)
+    # end to end through the C ABI with host buffers (page-locked)
     h_ctrl = torch.as_tensor(patch.ctrl.reshape(-1)).pin_memory()
-    h_vals = torch.empty(nnz, dtype=torch.float64).pin_memory()
+    h_vals, registered = host_buffer(torch, nnz)
     plan.assemble_host("stiffness", h_ctrl, vals, h_vals)
     barrier(dist)
     t0 = time.perf_counter()
-    e2e_steps = max(1, min(args.steps, 5))
+    e2e_steps = max(1, min(args.steps, 3))
     for _ in range(e2e_steps):
         plan.assemble_host("stiffness", h_ctrl, vals, h_vals)
     e2e_s = (time.perf_counter() - t0) / e2e_steps
     e2e_s = max_over_ranks(dist, e2e_s)
+    release_host_buffer(torch, h_vals, registered)
+    del h_vals
+    plan.close()
+    del vals, ctrl_d
+    torch.cuda.empty_cache()
+
+    precision = precision_study(wq, torch, stream) if args.precision else None
+    extra_p4 = assembly_only(wq, torch, stream, "p4_64") if args.precision else None
+    batch_line = run_batch_variant(wq, torch, stream) if args.batch else None
 
     pk, pk_kind = peaks()
     flops = algorithmic_flops(plan.n, p)
@@ -434,54 +554,27 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": "nnz/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic (seeded perturbed degree-4 spline cube, Greville + U[-0.05h, 0.05h])",
-        "config": {"workload": f"WQ stiffness, p={p}, {args.nel}^3 elements, N_DOF={N}, nnz={nnz} per GPU",
-                   "p": p, "n_el": args.nel, "n_dof": N, "nnz_per_gpu": nnz,
-                   "step": "plan refresh (points, tables, integrals, rules, CSR pattern, coefficients) "
-                           "+ FP64 stiffness assembly",
-                   "l2": "no flush: each step writes 2.5 GB (values + columns) > 126 MB L2",
-                   "parallelism": f"{world} independent patches, one per GPU"},
+        "data": f"synthetic (seeded perturbed degree-{p} spline cube, Greville + U[-0.05h, 0.05h])",
+        "config": config,
         "roofline": {"bound": "alu", "achieved": achieved_tf, "peak": peak_tf, "unit": "TFLOP/s",
                      "frac": achieved_tf / peak_tf,
-                     "traffic": captured_traffic(p, args.nel) if args.algo in ("auto", "staged") else None,
+                     "traffic": captured_traffic(p, patch.n_el[0]) if args.algo in ("auto", "staged") else None,
                      "kernel": (f"wq_assemble_stiffness, FP64, p={p}: k_stage3, k_stage2 (regular rows + "
                                 f"{2 * p + 2} edge-row kernels), k_stage1" if args.algo in ("auto", "staged")
                                 else f"k_assemble<{p},stiffness,fp64> (fused)"),
                      "flops_per_launch": flops,
                      "note": f"FP64 FMA pipe: {fpn:.1f} algorithmic flop/nnz (exact census of the factorisation "
-                             f"for this mesh); peak = 152 SMs x 2 DFMA/clk "
-                             f"x {pk.get('sm_max_mhz', 2070.0):.0f} MHz (derived; a DFMA probe measured "
-                             "1.20 TFLOP/s)"},
+                             f"for this mesh), divided by the call's CUDA-event time; peak = 152 SMs x 2 "
+                             f"DFMA/clk x {pk.get('sm_max_mhz', 2070.0):.0f} MHz (derived from unit counts "
+                             "and clocks; a DFMA probe measured 1.20 TFLOP/s)"},
         "hbm_write": {"achieved_gbs": write_gbs, "peak_gbs": hbm, "frac": write_gbs / hbm,
                       "peak_kind": f"{pk_kind} copy bandwidth"},
-        "breakdown_ms": {"assembly": kernel_ms, "refresh": refresh_ms, "mass_fp64": mass_ms,
-                         "stiffness_fp32_f32vals": f32_ms, "stiffness_fp32_f64vals": f32_f64_ms,
-                         "stiffness_mixed_f32vals": mix_ms, "stiffness_mixed_f64vals": mix_f64_ms,
-                         "stiffness_f32x2_f64vals": f2_ms,
-                         "stiffness_fp32_f32vals_fused": f32f_ms, "stiffness_fp64_fused": f64f_ms},
-        "variants_nnz_per_s": {"stiffness_fp64_assembly_only": nnz / (kernel_ms * 1e-3),
-                               "mass_fp64_assembly_only": nnz / (mass_ms * 1e-3),
-                               "stiffness_fp32_f32vals": nnz / (f32_ms * 1e-3),
-                               "stiffness_fp32_f64vals": nnz / (f32_f64_ms * 1e-3),
-                               "stiffness_mixed_f32vals": nnz / (mix_ms * 1e-3),
-                               "stiffness_mixed_f64vals": nnz / (mix_f64_ms * 1e-3),
-                               "stiffness_f32x2_f64vals": nnz / (f2_ms * 1e-3),
-                               "stiffness_fp32_f32vals_fused": nnz / (f32f_ms * 1e-3),
-                               "stiffness_fp64_fused_assembly_only": nnz / (f64f_ms * 1e-3)},
-        "precision_variants": {
-            "mixed": {"values": "f32", "ms": mix_ms, "speedup_vs_fp64": kernel_ms / mix_ms,
-                      "max_row_rel_error_vs_fp64": errs["mixed"], "bar": 1e-6,
-                      "what": "q3, q2 mode products in double-float, q1 in FP32 (FP64 edge rows)"},
-            "f32x2": {"values": "f64", "ms": f2_ms, "speedup_vs_fp64": kernel_ms / f2_ms,
-                      "max_row_rel_error_vs_fp64": errs["f32x2"], "bar": 1e-12,
-                      "what": "double-float (pairs of floats) in all three mode products"},
-            "fp32": {"values": "f32", "ms": f32_ms, "speedup_vs_fp64": kernel_ms / f32_ms,
-                     "max_row_rel_error_vs_fp64": errs["fp32"], "bar": None,
-                     "what": "FP32 in all three mode products"},
-            "error_rows": err_rows},
+        "breakdown_ms": {"assembly": kernel_ms, "refresh": refresh_ms, "mass_fp64": mass_ms},
+        "precision_study": precision,
+        "p4_64": extra_p4,
         "batch": batch_line,
         "e2e": {"value": world * nnz / e2e_s, "unit": "nnz/s", "h2d_bytes_per_step": 8 * 3 * N,
-                "d2h_bytes_per_step": 8 * nnz,
+                "d2h_bytes_per_step": 8 * nnz, "host_values_page_locked": registered,
                 "call": "wq_assemble_host: H2D control points, refresh, assemble, D2H values"},
         "gpu_launches": int(launches), "clocks": clocks,
     }
@@ -494,7 +587,6 @@ def run_ours(args):
                                           f"{cb['setup_seconds']:.1f} s not included"}
     if rank == 0:
         print(json.dumps(line), flush=True)
-    plan.close()
     if dist is not None:
         dist.destroy_process_group()
     return 0
@@ -506,16 +598,17 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="sweep8", choices=sorted(WORKLOADS))
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
-    ap.add_argument("--ref-step-seconds", type=float, default=4.0,
+    ap.add_argument("--ref-step-seconds", type=float, default=2.0,
                     help="CPU seconds of oracle work per step of --impl reference")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--p", type=int, default=4, help="degree (default: the p=4 workload)")
-    ap.add_argument("--nel", type=int, default=64, help="elements per direction (default 64)")
     ap.add_argument("--algo", default="auto", choices=["auto", "fused", "staged"],
                     help="assembly algorithm: one fused kernel, or three staged kernels")
     ap.add_argument("--no-batch", dest="batch", action="store_false",
                     help="skip the 64-patch batched launch variant")
+    ap.add_argument("--no-precision", dest="precision", action="store_false",
+                    help="skip the precision study and the p=4 assembly")
     ap.add_argument("--steps-only", action="store_true",
                     help="time the steps only (no variants, e2e or CPU baseline); for profiler captures")
     args = ap.parse_args()

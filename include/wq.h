@@ -257,18 +257,21 @@ wq_status wq_get_coefficients(wq_plan_t plan, double* h_coef);
  *   h_knots    host double[n_knots]: the knot vector (validated as in wq_plan_create)
  *   d_w        device double[4 * n * nq_stride], caller-owned output (kind-major)
  *   d_q0, d_nq device int32[n], caller-owned outputs
- *   nq_stride  row stride of d_w: at least max_i |Q_i| (at most 4p+1)
+ *   nq_stride  row stride of d_w: at least max_i |Q_i| and at most 4p+1 (outside
+ *              that range the call returns WQ_ERR_INVALID_ARG)
  * It calls no cudaMalloc, cudaFree or allocating library routine. Its
  * intermediate tables live in one fixed device array of
  * WQ_RULES_NOALLOC_SCRATCH_BYTES (5.9 MB) that every GPU loading the
  * library holds until the process exits; knot vectors with more than
  * WQ_RULES_NOALLOC_MAX_N basis functions are rejected with WQ_ERR_INVALID_ARG.
- * The first call on a device looks up that array's device address
- * (cudaGetSymbolAddress); make that first call before any stream capture. Every
+ * Every call looks up that array's address in the current device's context
+ * (cudaGetSymbolAddress), copies the knot vector from pageable host memory and
+ * synchronises `stream` before it returns, so it must never be called on a stream
+ * that is being captured into a CUDA graph. Every
  * call shares the one array and clears the parts it reads before writing them;
  * two calls that run at the same time on one device (other threads or streams)
- * race on it, so serialise them. The call synchronises `stream` before it returns
- * (to report a rule breakdown as WQ_ERR_SINGULAR_RULE). */
+ * race on it, so serialise them. The synchronisation at the end reports a rule
+ * breakdown as WQ_ERR_SINGULAR_RULE. */
 #define WQ_RULES_NOALLOC_MAX_N 1024
 #define WQ_RULES_NOALLOC_SCRATCH_BYTES 5903872
 wq_status wq_rules_noalloc(int p, int64_t n_knots, const double* h_knots, double* d_w, int32_t* d_q0,

@@ -20,7 +20,6 @@
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
-#include <mutex>
 #include <vector>
 
 #include "wq_internal.h"
@@ -1049,24 +1048,14 @@ static_assert(kNoAllocMaxN == WQ_RULES_NOALLOC_MAX_N, "scratch limit and its dec
 // obtained by cudaGetSymbolAddress below.
 static __device__ __align__(256) unsigned char g_rules_scratch[kNoAlloc.total];
 
-static std::mutex g_scratch_mutex;
-static void* g_scratch_addr[64] = {nullptr};
-
-// Device address of g_rules_scratch on the current device, looked up once per
-// device (the first call on a device does this set-up).
+// Device address of g_rules_scratch in the current device's context, looked up
+// on every call: a cached address would outlive a cudaDeviceReset, after which
+// the module is loaded again and the array may sit elsewhere.
 static wq_status scratch_address(unsigned char** out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return cuda_error(e, "no CUDA device");
-  if (dev < 0 || dev >= 64) return set_error(WQ_ERR_UNSUPPORTED, "device index above 63");
-  std::lock_guard<std::mutex> lock(g_scratch_mutex);
-  if (!g_scratch_addr[dev]) {
-    void* ptr = nullptr;
-    e = cudaGetSymbolAddress(&ptr, g_rules_scratch);
-    if (e != cudaSuccess) return cuda_error(e, "cudaGetSymbolAddress of the rule scratch");
-    g_scratch_addr[dev] = ptr;
-  }
-  *out = static_cast<unsigned char*>(g_scratch_addr[dev]);
+  void* ptr = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&ptr, g_rules_scratch);
+  if (e != cudaSuccess) return cuda_error(e, "cudaGetSymbolAddress of the rule scratch");
+  *out = static_cast<unsigned char*>(ptr);
   return WQ_OK;
 }
 
@@ -1091,7 +1080,7 @@ extern "C" wq_status wq_rules_noalloc(int p, int64_t n_knots, const double* h_kn
     int qe = hi == n_el ? nqp - 1 : 2 * hi + p - 2;
     nqmax = std::max(nqmax, qe - qs + 1);
   }
-  if (nq_stride < nqmax || nq_stride > wq::kMaxQ)
+  if (nq_stride < nqmax || nq_stride > 4 * p + 1)
     return set_error(WQ_ERR_INVALID_ARG, "nq_stride must lie between max |Q_i| and 4p+1");
   unsigned char* base = nullptr;
   wq_status st = wq::scratch_address(&base);

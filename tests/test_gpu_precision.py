@@ -4,7 +4,8 @@ sampled rows (which include the near-boundary rows, where the WQ weights are lar
 Reports the worst row-relative max-entry error and the Frobenius error of the sampled
 rows.
 
-"mixed" (first two mode products in FP64, the last one in FP32) is held to 1e-6
+"mixed" (first two mode products in double-float, the last one in FP32 with its first
+and last p+1 rows of direction 1 in FP64) is held to 1e-6
 row-relative. All-FP32 is held to 1e-5: its error is dominated by the FP32
 accumulation of the q3 contraction over weights that reach a few hundred times the
 row's largest entry near the boundary, so it is reported, and bounded, but it is not

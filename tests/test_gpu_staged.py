@@ -81,7 +81,8 @@ def test_staged_fp32(wq):
 @pytest.mark.parametrize("p", [2, 3, 4, 5, 6, 8])
 @pytest.mark.parametrize("which", ["stiffness", "mass"])
 def test_staged_mixed_precision(wq, p, which):
-    """FP64 for the q3 and q2 mode products, FP32 for the q1 one: 1e-6 row-relative."""
+    """Double-float for the q3 and q2 mode products, FP32 for the q1 one (FP64 for the first
+    and last p+1 rows of direction 1): 1e-6 row-relative."""
     patch = perturbed_cube(p, (2 * p + 5, p + 4, p + 3), seed=40 + p)
     plan = wq.Plan(patch.p, patch.knots, patch.ctrl)
     kappa = random_field(int(np.prod(plan.n_qp)), seed=90 + p, kind="positive")

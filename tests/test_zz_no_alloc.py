@@ -73,3 +73,16 @@ def test_noalloc_rejects_knot_vectors_beyond_its_scratch():
     st = lib.wq_rules_noalloc(p, len(kv), ctypes.c_void_p(kv.ctypes.data), dummy, dummy, dummy, 4 * p + 1, None)
     assert st == 1 and n > 1024
     assert b"1024" in lib.wq_last_error()
+
+
+def test_noalloc_rejects_a_row_stride_above_4p_plus_1():
+    """The row stride of the output may not exceed 4p+1 (the largest |Q_i| of degree p)."""
+    from paper_1605_01238_gb300 import _lib
+    from wq_synth import open_knot_vector, uniform_breaks
+    lib = _lib.load()
+    p = 2
+    kv = np.ascontiguousarray(open_knot_vector(uniform_breaks(10), p))
+    dummy = ctypes.c_void_p(1)
+    st = lib.wq_rules_noalloc(p, len(kv), ctypes.c_void_p(kv.ctypes.data), dummy, dummy, dummy, 4 * p + 2, None)
+    assert st == 1
+    assert b"4p+1" in lib.wq_last_error()
