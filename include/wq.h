@@ -28,6 +28,17 @@
  *    thread. Errors found on the device (det DF <= 0, a breakdown of a rule
  *    solve, a timed-out wait) are recorded in a device error word and reported
  *    by wq_sync_check() or by the next synchronous call.
+ *  - Device memory: wq_plan_create allocates the plan's tables, coefficients and
+ *    CSR pattern. The staged assembly and the adjoint need scratch that their
+ *    first call in each mode allocates (or wq_plan_reserve, ahead of time);
+ *    after that no call allocates. Every plan-owned allocation goes through the
+ *    allocator of wq_options when one is given, else cudaMalloc.
+ *  - Fault injection (testing): the environment variable WQ_FAULT, a
+ *    comma-separated list of steps, makes the host path fail at each named
+ *    step with WQ_ERR_INJECTED: "alloc" (every plan-owned device allocation),
+ *    "h2d" (every host-to-device copy), "solve" (the WQ rule step of a plan
+ *    set-up), "geometry" (the coefficient step). A failed wq_plan_create frees
+ *    everything it had allocated. Nothing is injected on the device.
  */
 #ifndef WQ_H
 #define WQ_H
@@ -50,7 +61,8 @@ typedef enum wq_status {
   WQ_ERR_OOM = 5,            /* device allocation failed */
   WQ_ERR_CUDA = 6,           /* a CUDA runtime call failed (or no device) */
   WQ_ERR_TIMEOUT = 7,        /* a bounded device wait gave up */
-  WQ_ERR_INJECTED = 8        /* failure injected on the host for testing */
+  WQ_ERR_INJECTED = 8,       /* failure injected on the host for testing (WQ_FAULT, below) */
+  WQ_ERR_NONFINITE = 9       /* checked mode: an assembled value is NaN or infinite */
 } wq_status;
 
 /* Value type of the output array. */
@@ -69,6 +81,54 @@ enum {
                                 bits), all three mode products on the FP32 pipe; staged only */
 };
 
+/* Default sentinels of the assembly calls: use the plan's wq_options value. */
+#define WQ_VALUES_DEFAULT (-1)
+#define WQ_PREC_DEFAULT (-1)
+
+/* ---- options -----------------------------------------------------------------
+ * Plan options (the paper has none: these are the library's configuration).
+ * wq_options_init fills the defaults; a NULL options pointer means the defaults.
+ *   size         sizeof(wq_options) as compiled by the caller (set by wq_options_init)
+ *   value_dtype  value type used by assembly calls that pass WQ_VALUES_DEFAULT
+ *                (default WQ_VALUES_F64)
+ *   precision    WQ_PREC_* used by assembly calls that pass WQ_PREC_DEFAULT
+ *                (default WQ_PREC_FP64)
+ *   algorithm    WQ_ALGO_* (default WQ_ALGO_AUTO), as wq_plan_set_algorithm
+ *   tile         fused-kernel tile extents {t1, t2}, as wq_plan_set_tiles; {0, 0} =
+ *                the tune cache's entry for the plan's degree, else the defaults
+ *   checked      1: every assembly call first checks that d_vals (nnz values) and
+ *                d_kappa (N_QP doubles) each lie inside one allocation of the
+ *                plan's device (the driver's address-range query) and returns
+ *                WQ_ERR_INVALID_ARG without launching anything otherwise; after
+ *                the assembly it scans the values, synchronises `stream` and
+ *                returns WQ_ERR_NONFINITE if one is NaN or infinite, or the error
+ *                the device recorded. For debugging: it synchronises every call.
+ *   tune_cache   NULL, or the path of a text file of "p t1 t2" lines (the format
+ *                paper_1605_01238_gb300/tune.py writes), read once at creation
+ *   alloc, free  NULL (cudaMalloc / cudaFree), or the caller's device allocator:
+ *                alloc(bytes, stream, ctx) returns a device pointer of the
+ *                current device, aligned to 256 bytes, or NULL when out of
+ *                memory (reported as WQ_ERR_OOM); free(ptr, stream, ctx) releases
+ *                one. `stream` is the stream of the call that needs the memory
+ *                (NULL when wq_destroy releases the plan, after it has
+ *                synchronised the device). Both or neither must be given.
+ *   alloc_ctx    passed through to alloc and free
+ */
+typedef struct wq_options {
+  size_t size;
+  int value_dtype;
+  int precision;
+  int algorithm;
+  int tile[2];
+  int checked;
+  const char* tune_cache;
+  void* (*alloc)(size_t bytes, void* stream, void* ctx);
+  void (*free)(void* ptr, void* stream, void* ctx);
+  void* alloc_ctx;
+} wq_options;
+
+wq_status wq_options_init(wq_options* opt);
+
 /* ---- plan ------------------------------------------------------------------
  * wq_plan_create: builds everything that depends only on the mesh and the
  * geometry (Algorithm 1 and Algorithm 2, plus the CSR pattern):
@@ -85,14 +145,20 @@ enum {
  *   n_knots  host int64[3]: length of each full knot vector (= n_l + p + 1)
  *   h_knots  host double*[3]: the three full open knot vectors
  *   h_ctrl   host double[N_DOF*3]: control points, xyz interleaved, i1 fastest
+ *   opt      NULL (defaults) or the plan's options (copied; see wq_options)
  *   stream   CUDA stream for the set-up work
  * The call copies its host inputs; they may be freed on return. It
  * synchronises `stream` once at the end to report device-side errors.
  */
 wq_status wq_plan_create(wq_plan_t* plan, int d, int p, const int64_t n_knots[3],
-                         const double* const h_knots[3], const double* h_ctrl, void* stream);
+                         const double* const h_knots[3], const double* h_ctrl, const wq_options* opt,
+                         void* stream);
 
-/* Releases every device and host resource of a plan. NULL is accepted. */
+/* Releases every device and host resource of a plan. NULL is accepted. With a
+ * caller allocator it first synchronises the device, so that no queued work
+ * still uses memory handed back to that allocator. wq_plan_destroy is the
+ * same call under its older name. */
+wq_status wq_destroy(wq_plan_t plan);
 wq_status wq_plan_destroy(wq_plan_t plan);
 
 /* Sizes: n[3] functions per direction, n_qp[3] points per direction, the number
@@ -128,10 +194,13 @@ wq_status wq_plan_refresh(wq_plan_t plan, const double* ctrl, int ctrl_on_device
  *            coefficient field multiplying c_lm (resp. c) at every point
  *            (Eq. (mass2): c absorbs the PDE coefficient)
  *   d_vals   device array of nnz values of type value_dtype, caller-owned
- *   value_dtype  WQ_VALUES_F64 or WQ_VALUES_F32
- *   precision    WQ_PREC_FP64 (requires WQ_VALUES_F64), WQ_PREC_FP32, WQ_PREC_MIXED or
- *                WQ_PREC_F32X2
- * Asynchronous on `stream`; no allocation, no synchronisation. */
+ *   value_dtype  WQ_VALUES_F64, WQ_VALUES_F32 or WQ_VALUES_DEFAULT (the plan's option)
+ *   precision    WQ_PREC_FP64 (requires WQ_VALUES_F64), WQ_PREC_FP32, WQ_PREC_MIXED,
+ *                WQ_PREC_F32X2 or WQ_PREC_DEFAULT (the plan's option)
+ * Asynchronous on `stream`, without synchronisation (unless the plan is in
+ * checked mode). The first staged call in a precision mode allocates that mode's
+ * plan-owned scratch (see WQ_ALGO_STAGED and wq_plan_reserve); later calls
+ * allocate nothing. */
 wq_status wq_assemble_stiffness(wq_plan_t plan, const double* d_kappa, void* d_vals,
                                 int value_dtype, int precision, void* stream);
 wq_status wq_assemble_mass(wq_plan_t plan, const double* d_kappa, void* d_vals,
@@ -154,6 +223,12 @@ wq_status wq_assemble_mass(wq_plan_t plan, const double* d_kappa, void* d_vals,
 enum { WQ_ALGO_FUSED = 0, WQ_ALGO_STAGED = 1, WQ_ALGO_AUTO = 2 };
 wq_status wq_plan_set_algorithm(wq_plan_t plan, int algorithm);
 
+/* Allocates now, on `stream`, the plan-owned scratch that the first assembly call
+ * in (precision, value_dtype) would allocate (the stiffness scratch, which also
+ * covers the mass matrix), and with adjoint = 1 the scratch of wq_adjoint, so
+ * that the assembly and adjoint calls that follow allocate nothing. */
+wq_status wq_plan_reserve(wq_plan_t plan, int precision, int value_dtype, int adjoint, void* stream);
+
 /* Tile extents of the assembly kernels: each block assembles at most t1 x t2
  * rows in directions 1 x 2 for one i3 (the three mode products of
  * Eq. (sumfactorization) share their intermediates inside a tile). t1 = t2 = 0
@@ -161,6 +236,8 @@ wq_status wq_plan_set_algorithm(wq_plan_t plan, int algorithm);
  * not fit in shared memory makes the assembly calls return WQ_ERR_UNSUPPORTED.
  * The autotuner (paper_1605_01238_gb300/tune.py) picks them per degree. */
 wq_status wq_plan_set_tiles(wq_plan_t plan, int t1, int t2);
+/* The plan's current tile extents (0, 0 = the defaults). */
+wq_status wq_plan_get_tiles(wq_plan_t plan, int* t1, int* t2);
 
 /* End-to-end call with host buffers: copies h_ctrl (NULL = keep) to the device,
  * refreshes the plan, assembles S (which = 0) or M (which = 1) in FP64 into the
@@ -205,11 +282,14 @@ wq_status wq_adjoint(wq_plan_t plan, int which, const double* d_kappa, const dou
  *                entry skips that patch's stiffness matrix)
  *   d_mass       same for the mass matrices
  * Each plan's tile extents (wq_plan_set_tiles) are read at creation. The outputs
- * are fixed at creation; wq_batch_launch replays the graph on `stream`. */
+ * are fixed at creation; wq_batch_launch replays the graph on `stream`. The batch
+ * allocates its own work list with cudaMalloc (not through the plans' allocators). */
 typedef struct wq_batch_s* wq_batch_t;
 wq_status wq_batch_create(wq_batch_t* batch, int count, const wq_plan_t* plans, void* const* d_stiffness,
                           void* const* d_mass, void* stream);
 wq_status wq_batch_launch(wq_batch_t batch, void* stream);
+/* The same call under the name of the library's interface description. */
+wq_status wq_batch_assemble(wq_batch_t batch, void* stream);
 /* Work items, total nonzeros written per launch and the persistent grid size. */
 wq_status wq_batch_info(wq_batch_t batch, int64_t* n_items, int64_t* nnz_total, int* grid);
 wq_status wq_batch_destroy(wq_batch_t batch);

@@ -13,13 +13,15 @@ import ctypes
 
 import numpy as np
 
-from ._lib import WqError, check, load
+from ._lib import ALLOC_FN, FREE_FN, Options, WqError, check, load
 
-__all__ = ["Plan", "Batch", "bilinear", "WqError", "launch_count", "load", "VALUES_F64", "VALUES_F32", "PREC_FP64", "PREC_FP32"]
+__all__ = ["Plan", "Batch", "bilinear", "WqError", "launch_count", "load", "TorchAllocator", "VALUES_F64",
+           "VALUES_F32", "PREC_FP64", "PREC_FP32"]
 
 VALUES_F64, VALUES_F32 = 0, 1
 PREC_FP64, PREC_FP32, PREC_MIXED, PREC_F32X2 = 0, 1, 2, 3
 _PREC = {"fp64": PREC_FP64, "fp32": PREC_FP32, "mixed": PREC_MIXED, "f32x2": PREC_F32X2}
+_ALGO = {"fused": 0, "staged": 1, "auto": 2}
 
 
 def _torch():
@@ -57,14 +59,48 @@ def launch_count() -> int:
     return int(load().wq_launch_count())
 
 
+class TorchAllocator:
+    """Plan-owned device memory from torch's caching allocator (the wq_options
+    allocator callbacks), so that a plan draws on the same pool as the rest of a
+    torch program. `live` maps each outstanding pointer to its size."""
+
+    def __init__(self):
+        torch = _torch()
+        self.live = {}
+
+        def _alloc(size, stream, ctx):
+            try:
+                ptr = torch.cuda.caching_allocator_alloc(int(size), stream=int(stream or 0))
+            except Exception:
+                return None
+            self.live[ptr] = int(size)
+            return ptr
+
+        def _free(ptr, stream, ctx):
+            try:
+                self.live.pop(ptr, None)
+                torch.cuda.caching_allocator_delete(ptr)
+            except Exception:
+                pass
+
+        self.alloc_fn = ALLOC_FN(_alloc)
+        self.free_fn = FREE_FN(_free)
+
+
 class Plan:
     """Mesh- and geometry-dependent data of one 3D patch (wq_plan_create).
 
     p: degree (2..8); knots: three full open knot vectors; ctrl: (N_DOF, 3)
-    control points with direction 1 fastest.
+    control points with direction 1 fastest. Options (wq_options): algorithm
+    ("auto", "staged", "fused"), precision and dtype (the defaults of the
+    assembly calls), tiles ((t1, t2) of the fused kernel), checked (range-checked
+    buffers and finite values, synchronising), tune_cache (a "p t1 t2" text file)
+    and allocator (a TorchAllocator, or any object with alloc_fn / free_fn
+    ctypes callbacks; None = cudaMalloc).
     """
 
-    def __init__(self, p: int, knots, ctrl, stream=None):
+    def __init__(self, p: int, knots, ctrl, stream=None, *, algorithm=None, precision=None, dtype=None,
+                 tiles=None, checked: bool = False, tune_cache=None, allocator=None):
         lib = load()
         self._knots = [np.ascontiguousarray(k, dtype=np.float64) for k in knots]
         if len(self._knots) != 3:
@@ -72,9 +108,27 @@ class Plan:
         ctrl = np.ascontiguousarray(ctrl, dtype=np.float64).reshape(-1, 3)
         n_knots = (ctypes.c_int64 * 3)(*[len(k) for k in self._knots])
         kptrs = (ctypes.c_void_p * 3)(*[k.ctypes.data for k in self._knots])
+        opt = Options()
+        check(lib.wq_options_init(ctypes.byref(opt)))
+        if algorithm is not None:
+            opt.algorithm = _ALGO[algorithm]
+        if precision is not None:
+            opt.precision = _PREC[precision] if isinstance(precision, str) else int(precision)
+        if dtype is not None:
+            opt.value_dtype = VALUES_F32 if dtype == _torch().float32 else VALUES_F64
+        if tiles is not None:
+            opt.tile[0], opt.tile[1] = int(tiles[0]), int(tiles[1])
+        opt.checked = 1 if checked else 0
+        if tune_cache is not None:
+            opt.tune_cache = str(tune_cache).encode()
+        self._allocator = allocator
+        if allocator is not None:
+            opt.alloc, opt.free = allocator.alloc_fn, allocator.free_fn
+        self.value_dtype = opt.value_dtype
+        self.precision = opt.precision
         h = ctypes.c_void_p()
         check(lib.wq_plan_create(ctypes.byref(h), 3, int(p), n_knots, kptrs,
-                                 ctypes.c_void_p(ctrl.ctypes.data), _stream(stream)))
+                                 ctypes.c_void_p(ctrl.ctypes.data), ctypes.byref(opt), _stream(stream)))
         self._h = h
         pp = ctypes.c_int()
         n = (ctypes.c_int64 * 3)()
@@ -93,7 +147,7 @@ class Plan:
     # -- lifetime
     def close(self) -> None:
         if getattr(self, "_h", None):
-            load().wq_plan_destroy(self._h)
+            load().wq_destroy(self._h)
             self._h = None
 
     def __del__(self):
@@ -150,20 +204,38 @@ class Plan:
     def set_algorithm(self, algorithm: str) -> None:
         """"fused" (one kernel, tiles in shared memory), "staged" (three kernels,
         intermediates in device memory) or "auto" (the default: staged)."""
-        check(load().wq_plan_set_algorithm(self._h, {"fused": 0, "staged": 1, "auto": 2}[algorithm]))
+        check(load().wq_plan_set_algorithm(self._h, _ALGO[algorithm]))
+
+    def reserve(self, precision=None, dtype=None, adjoint: bool = False, stream=None) -> None:
+        """Allocate now the scratch that the first assembly in (precision, dtype), and
+        with adjoint=True the first adjoint, would allocate (wq_plan_reserve)."""
+        torch = _torch()
+        vdt = -1 if dtype is None else (VALUES_F32 if dtype == torch.float32 else VALUES_F64)
+        prec = -1 if precision is None else (_PREC[precision] if isinstance(precision, str) else int(precision))
+        check(load().wq_plan_reserve(self._h, prec, vdt, 1 if adjoint else 0, _stream(stream)))
 
     def set_tiles(self, t1: int = 0, t2: int = 0) -> None:
         """Assembly tile extents in directions 1 and 2 (0, 0 = defaults)."""
         check(load().wq_plan_set_tiles(self._h, int(t1), int(t2)))
 
+    def tiles(self) -> tuple:
+        """The plan's tile extents (0, 0 = defaults)."""
+        a, b = ctypes.c_int(), ctypes.c_int()
+        check(load().wq_plan_get_tiles(self._h, ctypes.byref(a), ctypes.byref(b)))
+        return a.value, b.value
+
     # -- assembly
     def _assemble(self, fn, kappa, out, dtype, precision, stream):
         torch = _torch()
-        dtype = dtype or torch.float64
+        if dtype is None:
+            dtype = torch.float32 if self.value_dtype == VALUES_F32 else torch.float64
         vdt = VALUES_F64 if dtype == torch.float64 else VALUES_F32 if dtype == torch.float32 else None
         if vdt is None:
             raise ValueError("dtype must be torch.float64 or torch.float32")
-        prec = _PREC[precision] if isinstance(precision, str) else int(precision)
+        if precision is None:
+            prec = self.precision
+        else:
+            prec = _PREC[precision] if isinstance(precision, str) else int(precision)
         if out is None:
             out = torch.empty(self.nnz, dtype=dtype, device="cuda")
         vp = _dev_ptr(out, dtype, self.nnz, "out")
@@ -173,11 +245,11 @@ class Plan:
         check(fn(self._h, ctypes.c_void_p(kp), ctypes.c_void_p(vp), vdt, prec, _stream(stream)))
         return out
 
-    def stiffness(self, kappa=None, out=None, dtype=None, precision="fp64", stream=None):
+    def stiffness(self, kappa=None, out=None, dtype=None, precision=None, stream=None):
         """CSR values of the WQ stiffness matrix (Eq. (stiff)) in the plan's order."""
         return self._assemble(load().wq_assemble_stiffness, kappa, out, dtype, precision, stream)
 
-    def mass(self, kappa=None, out=None, dtype=None, precision="fp64", stream=None):
+    def mass(self, kappa=None, out=None, dtype=None, precision=None, stream=None):
         """CSR values of the WQ mass matrix (Eq. (Mass_approx))."""
         return self._assemble(load().wq_assemble_mass, kappa, out, dtype, precision, stream)
 
@@ -280,7 +352,7 @@ class Batch:
         self.n_items, self.nnz_total, self.grid = n_items.value, nnz.value, grid.value
 
     def launch(self, stream=None) -> None:
-        check(load().wq_batch_launch(self._h, _stream(stream)))
+        check(load().wq_batch_assemble(self._h, _stream(stream)))
 
     def close(self) -> None:
         if getattr(self, "_h", None):

@@ -11,13 +11,27 @@ c_int, c_i64, c_vp, c_dp = ctypes.c_int, ctypes.c_int64, ctypes.c_void_p, ctypes
 
 STATUS = {0: "WQ_OK", 1: "WQ_ERR_INVALID_ARG", 2: "WQ_ERR_UNSUPPORTED", 3: "WQ_ERR_SINGULAR_RULE",
           4: "WQ_ERR_BAD_GEOMETRY", 5: "WQ_ERR_OOM", 6: "WQ_ERR_CUDA", 7: "WQ_ERR_TIMEOUT",
-          8: "WQ_ERR_INJECTED"}
+          8: "WQ_ERR_INJECTED", 9: "WQ_ERR_NONFINITE"}
+
+# void* alloc(size_t bytes, void* stream, void* ctx); void free(void* ptr, void* stream, void* ctx)
+ALLOC_FN = ctypes.CFUNCTYPE(c_vp, ctypes.c_size_t, c_vp, c_vp)
+FREE_FN = ctypes.CFUNCTYPE(None, c_vp, c_vp, c_vp)
+
+
+class Options(ctypes.Structure):
+    """struct wq_options of include/wq.h."""
+    _fields_ = [("size", ctypes.c_size_t), ("value_dtype", c_int), ("precision", c_int), ("algorithm", c_int),
+                ("tile", c_int * 2), ("checked", c_int), ("tune_cache", ctypes.c_char_p),
+                ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_ctx", c_vp)]
 
 # name -> (restype, argtypes)
 SIGNATURES = {
+    "wq_options_init": (c_int, [ctypes.POINTER(Options)]),
     "wq_plan_create": (c_int, [ctypes.POINTER(c_vp), c_int, c_int, ctypes.POINTER(c_i64),
-                               ctypes.POINTER(c_vp), c_vp, c_vp]),
+                               ctypes.POINTER(c_vp), c_vp, ctypes.POINTER(Options), c_vp]),
+    "wq_destroy": (c_int, [c_vp]),
     "wq_plan_destroy": (c_int, [c_vp]),
+    "wq_plan_reserve": (c_int, [c_vp, c_int, c_int, c_int, c_vp]),
     "wq_plan_info": (c_int, [c_vp, ctypes.POINTER(c_int), ctypes.POINTER(c_i64), ctypes.POINTER(c_i64),
                              ctypes.POINTER(c_i64), ctypes.POINTER(c_i64)]),
     "wq_plan_pattern": (c_int, [c_vp, ctypes.POINTER(c_vp), ctypes.POINTER(c_vp)]),
@@ -37,10 +51,12 @@ SIGNATURES = {
     "wq_adjoint": (c_int, [c_vp, c_int, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp]),
     "wq_batch_create": (c_int, [ctypes.POINTER(c_vp), c_int, c_vp, c_vp, c_vp, c_vp]),
     "wq_batch_launch": (c_int, [c_vp, c_vp]),
+    "wq_batch_assemble": (c_int, [c_vp, c_vp]),
     "wq_batch_info": (c_int, [c_vp, ctypes.POINTER(c_i64), ctypes.POINTER(c_i64), ctypes.POINTER(c_int)]),
     "wq_batch_destroy": (c_int, [c_vp]),
     "wq_plan_set_algorithm": (c_int, [c_vp, c_int]),
     "wq_plan_set_tiles": (c_int, [c_vp, c_int, c_int]),
+    "wq_plan_get_tiles": (c_int, [c_vp, ctypes.POINTER(c_int), ctypes.POINTER(c_int)]),
     "wq_rules_noalloc": (c_int, [c_int, c_i64, c_vp, c_vp, c_vp, c_vp, c_int, c_vp]),
 }
 

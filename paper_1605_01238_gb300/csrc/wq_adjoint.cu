@@ -199,6 +199,22 @@ static size_t adjoint_scratch_doubles(const wq_plan_s* pl, size_t* off) {
   return o;
 }
 
+namespace wq {
+
+// Plan-owned fields of the adjoint, allocated on first use (or by wq_plan_reserve).
+wq_status reserve_adjoint(wq_plan_s* pl, cudaStream_t s) {
+  if (pl->adj_scratch && pl->jac) return WQ_OK;
+  size_t off[7];
+  const size_t need = adjoint_scratch_doubles(pl, off);
+  wq_status st = WQ_OK;
+  if (!pl->adj_scratch) st = plan_alloc(pl, (void**)&pl->adj_scratch, need * sizeof(double), s, "adjoint fields");
+  if (st == WQ_OK && !pl->jac)
+    st = plan_alloc(pl, (void**)&pl->jac, 9 * (size_t)pl->n_qp_total * sizeof(double), s, "adjoint Jacobian");
+  return st;
+}
+
+}  // namespace wq
+
 extern "C" wq_status wq_adjoint(wq_plan_t plan, int which, const double* d_kappa, const double* d_lambda,
                                 const double* d_u, double* h_J, double* d_grad_kappa, double* d_grad_ctrl,
                                 void* stream) {
@@ -209,13 +225,19 @@ extern "C" wq_status wq_adjoint(wq_plan_t plan, int which, const double* d_kappa
   const int64_t N = pl->n_rows, NQP = pl->n_qp_total;
   const int n1 = (int)pl->n[0], n2 = (int)pl->n[1], n3 = (int)pl->n[2];
   const int q1 = (int)pl->nqp[0], q2 = (int)pl->nqp[1], q3 = (int)pl->nqp[2];
-  size_t off[7];
-  const size_t need = adjoint_scratch_doubles(pl, off);
-  if (!pl->adj_scratch) {
-    cudaError_t e = cudaMalloc(&pl->adj_scratch, need * sizeof(double));
-    if (e == cudaSuccess) e = cudaMalloc(&pl->jac, 9 * (size_t)NQP * sizeof(double));
-    if (e != cudaSuccess) return wq::cuda_error(e, "adjoint scratch allocation");
+  if (pl->opt.checked) {
+    const size_t nb = sizeof(double) * (size_t)N, qb = sizeof(double) * (size_t)NQP;
+    wq_status sc = wq::check_device_range(pl, d_lambda, nb, "d_lambda");
+    if (sc == WQ_OK) sc = wq::check_device_range(pl, d_u, nb, "d_u");
+    if (sc == WQ_OK && d_kappa) sc = wq::check_device_range(pl, d_kappa, qb, "d_kappa");
+    if (sc == WQ_OK && d_grad_kappa) sc = wq::check_device_range(pl, d_grad_kappa, qb, "d_grad_kappa");
+    if (sc == WQ_OK && d_grad_ctrl) sc = wq::check_device_range(pl, d_grad_ctrl, 3 * nb, "d_grad_ctrl");
+    if (sc != WQ_OK) return sc;
   }
+  size_t off[7];
+  adjoint_scratch_doubles(pl, off);
+  wq_status st0 = wq::reserve_adjoint(pl, s);
+  if (st0 != WQ_OK) return st0;
   double* U = pl->adj_scratch + off[0];
   double* L = pl->adj_scratch + off[1];
   double* Gb = pl->adj_scratch + off[2];

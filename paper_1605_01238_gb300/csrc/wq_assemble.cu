@@ -601,23 +601,75 @@ wq_status launch_assemble_f32(wq_plan_s* pl, bool mass, const double* kappa, voi
 
 }  // namespace wq
 
+namespace wq {
+
+// Checked mode: flags a NaN or infinite value in the error word.
+template <typename T>
+__global__ void k_check_finite(const T* __restrict__ v, int64_t n, int* err) {
+  bool bad = false;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    bad |= !isfinite(v[i]);
+  if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(err, kErrNonFinite);
+}
+
+}  // namespace wq
+
 using wq::set_error;
+
+static wq_status read_error(wq_plan_t plan, cudaStream_t s) { return wq_sync_check(plan, (void*)s); }
 
 static wq_status assemble(wq_plan_t plan, bool mass, const double* kappa, void* vals, int value_dtype, int precision,
                           void* stream) {
   if (!plan || !vals) return set_error(WQ_ERR_INVALID_ARG, "NULL argument");
+  if (value_dtype == WQ_VALUES_DEFAULT) value_dtype = plan->opt.value_dtype;
+  if (precision == WQ_PREC_DEFAULT) precision = plan->opt.precision;
   if (value_dtype != WQ_VALUES_F64 && value_dtype != WQ_VALUES_F32)
     return set_error(WQ_ERR_INVALID_ARG, "unknown value dtype");
   cudaStream_t s = (cudaStream_t)stream;
   if (precision == WQ_PREC_FP64 && value_dtype != WQ_VALUES_F64)
     return set_error(WQ_ERR_INVALID_ARG, "FP64 contractions write FP64 values");
+  if (precision < WQ_PREC_FP64 || precision > WQ_PREC_F32X2) return set_error(WQ_ERR_UNSUPPORTED, "unknown precision");
+  const size_t vbytes = (value_dtype == WQ_VALUES_F64 ? sizeof(double) : sizeof(float)) * (size_t)plan->nnz;
+  if (plan->opt.checked) {
+    wq_status st = wq::check_device_range(plan, vals, vbytes, "d_vals");
+    if (st == WQ_OK && kappa) st = wq::check_device_range(plan, kappa, sizeof(double) * plan->n_qp_total, "d_kappa");
+    if (st != WQ_OK) return st;
+  }
   const bool staged = plan->algorithm == WQ_ALGO_STAGED || plan->algorithm == WQ_ALGO_AUTO;
+  wq_status st;
   if (precision == WQ_PREC_MIXED || precision == WQ_PREC_F32X2 ||
       ((precision == WQ_PREC_FP64 || precision == WQ_PREC_FP32) && staged))
-    return wq::launch_staged(plan, mass, kappa, vals, value_dtype, precision, s);
-  if (precision == WQ_PREC_FP64) return wq::launch_assemble_f64(plan, mass, kappa, (double*)vals, s);
-  if (precision == WQ_PREC_FP32) return wq::launch_assemble_f32(plan, mass, kappa, vals, value_dtype, s);
-  return set_error(WQ_ERR_UNSUPPORTED, "unknown precision");
+    st = wq::launch_staged(plan, mass, kappa, vals, value_dtype, precision, s);
+  else if (precision == WQ_PREC_FP64)
+    st = wq::launch_assemble_f64(plan, mass, kappa, (double*)vals, s);
+  else
+    st = wq::launch_assemble_f32(plan, mass, kappa, vals, value_dtype, s);
+  if (st != WQ_OK || !plan->opt.checked) return st;
+  if (value_dtype == WQ_VALUES_F64)
+    wq::k_check_finite<double><<<304, 256, 0, s>>>((const double*)vals, plan->nnz, plan->err);
+  else
+    wq::k_check_finite<float><<<304, 256, 0, s>>>((const float*)vals, plan->nnz, plan->err);
+  wq::count_launch();
+  WQ_CUDA_TRY(cudaGetLastError(), "value check launch");
+  return read_error(plan, s);
+}
+
+extern "C" wq_status wq_plan_reserve(wq_plan_t plan, int precision, int value_dtype, int adjoint, void* stream) {
+  if (!plan) return set_error(WQ_ERR_INVALID_ARG, "NULL plan");
+  if (value_dtype == WQ_VALUES_DEFAULT) value_dtype = plan->opt.value_dtype;
+  if (precision == WQ_PREC_DEFAULT) precision = plan->opt.precision;
+  if (value_dtype != WQ_VALUES_F64 && value_dtype != WQ_VALUES_F32)
+    return set_error(WQ_ERR_INVALID_ARG, "unknown value dtype");
+  if (precision < WQ_PREC_FP64 || precision > WQ_PREC_F32X2) return set_error(WQ_ERR_UNSUPPORTED, "unknown precision");
+  if (precision == WQ_PREC_FP64 && value_dtype != WQ_VALUES_F64)
+    return set_error(WQ_ERR_INVALID_ARG, "FP64 contractions write FP64 values");
+  cudaStream_t s = (cudaStream_t)stream;
+  const bool staged = plan->algorithm == WQ_ALGO_STAGED || plan->algorithm == WQ_ALGO_AUTO;
+  wq_status st = WQ_OK;
+  if (staged || precision == WQ_PREC_MIXED || precision == WQ_PREC_F32X2)
+    st = wq::launch_staged(plan, false, nullptr, nullptr, value_dtype, precision, s);
+  if (st == WQ_OK && adjoint) st = wq::reserve_adjoint(plan, s);
+  return st;
 }
 
 extern "C" wq_status wq_plan_set_tiles(wq_plan_t plan, int t1, int t2) {
@@ -626,6 +678,13 @@ extern "C" wq_status wq_plan_set_tiles(wq_plan_t plan, int t1, int t2) {
     return set_error(WQ_ERR_INVALID_ARG, "tile extents must both be 0 (default) or in 1..64");
   plan->tile[0] = t1;
   plan->tile[1] = t2;
+  return WQ_OK;
+}
+
+extern "C" wq_status wq_plan_get_tiles(wq_plan_t plan, int* t1, int* t2) {
+  if (!plan || !t1 || !t2) return set_error(WQ_ERR_INVALID_ARG, "NULL argument");
+  *t1 = plan->tile[0];
+  *t2 = plan->tile[1];
   return WQ_OK;
 }
 
@@ -804,6 +863,8 @@ extern "C" wq_status wq_batch_launch(wq_batch_t batch, void* stream) {
   wq::count_launch();
   return WQ_OK;
 }
+
+extern "C" wq_status wq_batch_assemble(wq_batch_t batch, void* stream) { return wq_batch_launch(batch, stream); }
 
 extern "C" wq_status wq_batch_info(wq_batch_t batch, int64_t* n_items, int64_t* nnz_total, int* grid) {
   if (!batch) return set_error(WQ_ERR_INVALID_ARG, "NULL batch");

@@ -38,6 +38,7 @@ extern "C" const char* wq_status_string(wq_status status) {
     case WQ_ERR_CUDA: return "WQ_ERR_CUDA";
     case WQ_ERR_TIMEOUT: return "WQ_ERR_TIMEOUT";
     case WQ_ERR_INJECTED: return "WQ_ERR_INJECTED";
+    case WQ_ERR_NONFINITE: return "WQ_ERR_NONFINITE";
   }
   return "WQ_ERR_UNKNOWN";
 }

@@ -21,6 +21,7 @@ enum : int {
   kErrSingularRule = 1,
   kErrBadGeometry = 2,
   kErrTimeout = 4,
+  kErrNonFinite = 8,
 };
 
 // ---------------------------------------------------------------------------
@@ -143,6 +144,7 @@ struct wq_plan_s {
   void* stg_b = nullptr;          // staged: G
   void* stg_c = nullptr;          // staged, mixed precision: FP64 edge copy of G
   size_t stg_a_bytes = 0, stg_b_bytes = 0, stg_c_bytes = 0;
+  wq_options opt{};               // options given at creation (defaults filled in)
 };
 
 namespace wq {
@@ -151,6 +153,18 @@ namespace wq {
 wq_status set_error(wq_status st, const std::string& msg);
 wq_status cuda_error(cudaError_t e, const char* what);
 void count_launch(int k = 1);
+
+// Plan-owned device memory: the caller's allocator of wq_options, else cudaMalloc.
+// plan_alloc honours WQ_FAULT=alloc; plan_free accepts NULL.
+wq_status plan_alloc(wq_plan_s* pl, void** ptr, size_t bytes, cudaStream_t s, const char* what);
+void plan_free(wq_plan_s* pl, void* ptr, cudaStream_t s);
+
+// True when the comma-separated list in WQ_FAULT names `step` (host-side fault
+// injection for tests).
+bool fault(const char* step);
+
+// Checked mode: `bytes` from `p` lie inside one device allocation of the plan's device.
+wq_status check_device_range(const wq_plan_s* pl, const void* p, size_t bytes, const char* what);
 
 // Plan-building steps (wq_plan.cu).
 wq_status run_setup(wq_plan_s* pl, cudaStream_t s, bool with_pattern);
@@ -162,8 +176,11 @@ wq_status launch_assemble_f64(wq_plan_s* pl, bool mass, const double* kappa, dou
 wq_status launch_assemble_f32(wq_plan_s* pl, bool mass, const double* kappa, void* vals,
                               int value_dtype, cudaStream_t s);
 // Staged assembly (wq_staged.cu: dispatch on the degree; kernels in wq_staged_impl.cuh).
+// vals = NULL: allocate the mode's scratch only (wq_plan_reserve).
 wq_status launch_staged(wq_plan_s* pl, bool mass, const double* kappa, void* vals, int value_dtype, int precision,
                         cudaStream_t s);
+// Adjoint fields (wq_adjoint.cu).
+wq_status reserve_adjoint(wq_plan_s* pl, cudaStream_t s);
 
 }  // namespace wq
 

@@ -630,6 +630,7 @@ static size_t coef_smem(int p) {
 }
 
 wq_status run_coefficients(wq_plan_s* pl, cudaStream_t s, double* jac) {
+  if (fault("geometry")) return set_error(WQ_ERR_INJECTED, "injected failure at the coefficient step");
   DeltaArgs da;
   da.n1 = (int)pl->n[0];
   da.n2 = (int)pl->n[1];
@@ -702,6 +703,7 @@ wq_status run_setup(wq_plan_s* pl, cudaStream_t s, bool with_pattern) {
   k_greville<<<dim3((max_n + tb - 1) / tb, 3), tb, 0, s>>>(A);
   count_launch(8);
   WQ_CUDA_TRY(cudaGetLastError(), "set-up kernels");
+  if (fault("solve")) return set_error(WQ_ERR_INJECTED, "injected failure at the WQ rule step");
   if (with_pattern) {
     PatternArgs pa;
     pa.p = p;
@@ -760,30 +762,110 @@ static bool knots_ok(const double* xi, int64_t len, int p, std::string* why) {
 
 static void free_plan(wq_plan_s* pl) {
   if (!pl) return;
+  // a caller allocator may hand the memory out again at once: let queued work finish
+  if (pl->opt.free) cudaDeviceSynchronize();
   for (int l = 0; l < 3; ++l) {
     wq::DirData& d = pl->dir[l];
     void* ptrs[] = {d.knots, d.x, d.x_dd, d.first, d.q0, d.nq, d.bt_dd, d.bt, d.bp, d.gb, d.integ, d.w, d.prefix,
                     d.greville, d.pair_row, d.tab32, d.tabf2, d.recip};
-    for (void* q : ptrs)
-      if (q) cudaFree(q);
+    for (void* q : ptrs) wq::plan_free(pl, q, nullptr);
   }
   void* ptrs[] = {pl->ctrl, pl->ctrl_delta, pl->coef, pl->row_ptr, pl->col, pl->gauss, pl->err, pl->jac,
                   pl->adj_scratch, pl->coefT, pl->stg_a, pl->stg_b, pl->stg_c};
-  for (void* q : ptrs)
-    if (q) cudaFree(q);
+  for (void* q : ptrs) wq::plan_free(pl, q, nullptr);
   delete pl;
 }
 
-static wq_status dev_alloc(void** ptr, size_t bytes, const char* what) {
-  if (std::getenv("WQ_FAULT") && std::strcmp(std::getenv("WQ_FAULT"), "alloc") == 0)
-    return set_error(WQ_ERR_INJECTED, std::string("injected allocation failure: ") + what);
-  cudaError_t e = cudaMalloc(ptr, bytes ? bytes : 16);
+namespace wq {
+
+bool fault(const char* step) {
+  const char* env = std::getenv("WQ_FAULT");
+  if (!env || !*env) return false;
+  const size_t n = std::strlen(step);
+  for (const char* c = env; *c;) {
+    const char* e = std::strchr(c, ',');
+    const size_t len = e ? (size_t)(e - c) : std::strlen(c);
+    if (len == n && std::strncmp(c, step, n) == 0) return true;
+    if (!e) break;
+    c = e + 1;
+  }
+  return false;
+}
+
+wq_status plan_alloc(wq_plan_s* pl, void** ptr, size_t bytes, cudaStream_t s, const char* what) {
+  *ptr = nullptr;
+  if (fault("alloc")) return set_error(WQ_ERR_INJECTED, std::string("injected allocation failure: ") + what);
+  if (bytes == 0) bytes = 16;
+  if (pl->opt.alloc) {
+    void* q = pl->opt.alloc(bytes, (void*)s, pl->opt.alloc_ctx);
+    if (!q) return set_error(WQ_ERR_OOM, std::string("the caller's allocator returned NULL: ") + what);
+    if (reinterpret_cast<uintptr_t>(q) % 256 != 0) {
+      pl->opt.free(q, (void*)s, pl->opt.alloc_ctx);
+      return set_error(WQ_ERR_INVALID_ARG, std::string("the caller's allocator returned memory not aligned to "
+                                                       "256 bytes: ") + what);
+    }
+    *ptr = q;
+    return WQ_OK;
+  }
+  cudaError_t e = cudaMalloc(ptr, bytes);
   if (e == cudaErrorMemoryAllocation) {
     cudaGetLastError();
+    *ptr = nullptr;
     return set_error(WQ_ERR_OOM, std::string("device allocation failed: ") + what);
   }
-  if (e != cudaSuccess) return wq::cuda_error(e, what);
+  if (e != cudaSuccess) {
+    *ptr = nullptr;
+    return cuda_error(e, what);
+  }
   return WQ_OK;
+}
+
+void plan_free(wq_plan_s* pl, void* ptr, cudaStream_t s) {
+  if (!ptr) return;
+  if (pl->opt.free)
+    pl->opt.free(ptr, (void*)s, pl->opt.alloc_ctx);
+  else
+    cudaFree(ptr);
+}
+
+// cuMemGetAddressRange through the runtime's driver entry point (no link-time
+// dependency on the driver library).
+typedef int (*AddressRangeFn)(unsigned long long* base, size_t* size, unsigned long long ptr);
+
+wq_status check_device_range(const wq_plan_s* pl, const void* p, size_t bytes, const char* what) {
+  static AddressRangeFn fn = nullptr;
+  if (!fn) {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuMemGetAddressRange", &f, 12000, cudaEnableDefault, &q);
+    if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !f)
+      return set_error(WQ_ERR_UNSUPPORTED, "checked mode: the driver's address-range query is unavailable");
+    fn = reinterpret_cast<AddressRangeFn>(f);
+  }
+  cudaPointerAttributes at;
+  cudaError_t e = cudaPointerGetAttributes(&at, p);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return set_error(WQ_ERR_INVALID_ARG, std::string("checked mode: not a device pointer: ") + what);
+  }
+  if (at.type != cudaMemoryTypeDevice || at.device != pl->device)
+    return set_error(WQ_ERR_INVALID_ARG, std::string("checked mode: not device memory of the plan's device: ") + what);
+  unsigned long long base = 0;
+  size_t size = 0;
+  if (fn(&base, &size, reinterpret_cast<unsigned long long>(p)) != 0)
+    return set_error(WQ_ERR_INVALID_ARG, std::string("checked mode: no device allocation holds ") + what);
+  const unsigned long long a = reinterpret_cast<unsigned long long>(p);
+  if (a + bytes > base + size)
+    return set_error(WQ_ERR_INVALID_ARG, std::string("checked mode: ") + what + " needs " + std::to_string(bytes) +
+                                             " bytes but its allocation ends " + std::to_string(base + size - a) +
+                                             " bytes after it");
+  return WQ_OK;
+}
+
+}  // namespace wq
+
+static wq_status dev_alloc(wq_plan_s* pl, void** ptr, size_t bytes, cudaStream_t s, const char* what) {
+  return wq::plan_alloc(pl, ptr, bytes, s, what);
 }
 
 static wq_status read_error_word(wq_plan_s* pl, cudaStream_t s) {
@@ -794,13 +876,70 @@ static wq_status read_error_word(wq_plan_s* pl, cudaStream_t s) {
   if (h & wq::kErrBadGeometry) return set_error(WQ_ERR_BAD_GEOMETRY, "det DF <= 0 or not finite at a quadrature point");
   if (h & wq::kErrSingularRule) return set_error(WQ_ERR_SINGULAR_RULE, "a WQ rule system broke down");
   if (h & wq::kErrTimeout) return set_error(WQ_ERR_TIMEOUT, "a bounded device wait gave up");
+  if (h & wq::kErrNonFinite) return set_error(WQ_ERR_NONFINITE, "an assembled value is NaN or infinite");
+  return WQ_OK;
+}
+
+extern "C" wq_status wq_options_init(wq_options* opt) {
+  if (!opt) return set_error(WQ_ERR_INVALID_ARG, "NULL options");
+  *opt = wq_options{};
+  opt->size = sizeof(wq_options);
+  opt->value_dtype = WQ_VALUES_F64;
+  opt->precision = WQ_PREC_FP64;
+  opt->algorithm = WQ_ALGO_AUTO;
+  return WQ_OK;
+}
+
+// Tile extents for degree p from a text cache of "p t1 t2" lines ('#' starts a comment).
+static bool read_tune_cache(const char* path, int p, int* t1, int* t2) {
+  FILE* f = std::fopen(path, "r");
+  if (!f) return false;
+  char line[256];
+  bool found = false;
+  while (std::fgets(line, sizeof line, f)) {
+    int q, a, b;
+    if (line[0] == '#') continue;
+    if (std::sscanf(line, "%d %d %d", &q, &a, &b) == 3 && q == p && a >= 1 && a <= 64 && b >= 1 && b <= 64) {
+      *t1 = a;
+      *t2 = b;
+      found = true;
+    }
+  }
+  std::fclose(f);
+  return found;
+}
+
+static wq_status validate_options(const wq_options* o) {
+  if (o->size != sizeof(wq_options))
+    return set_error(WQ_ERR_INVALID_ARG, "wq_options.size does not match this library (call wq_options_init)");
+  if (o->value_dtype != WQ_VALUES_F64 && o->value_dtype != WQ_VALUES_F32)
+    return set_error(WQ_ERR_INVALID_ARG, "wq_options.value_dtype is not a value type");
+  if (o->precision < WQ_PREC_FP64 || o->precision > WQ_PREC_F32X2)
+    return set_error(WQ_ERR_INVALID_ARG, "wq_options.precision is not a precision mode");
+  if (o->precision == WQ_PREC_FP64 && o->value_dtype != WQ_VALUES_F64)
+    return set_error(WQ_ERR_INVALID_ARG, "FP64 contractions write FP64 values");
+  if (o->algorithm != WQ_ALGO_FUSED && o->algorithm != WQ_ALGO_STAGED && o->algorithm != WQ_ALGO_AUTO)
+    return set_error(WQ_ERR_INVALID_ARG, "wq_options.algorithm is not an algorithm");
+  if (o->tile[0] < 0 || o->tile[1] < 0 || o->tile[0] > 64 || o->tile[1] > 64 || (o->tile[0] == 0) != (o->tile[1] == 0))
+    return set_error(WQ_ERR_INVALID_ARG, "wq_options.tile must be {0, 0} or in 1..64");
+  if (o->checked != 0 && o->checked != 1) return set_error(WQ_ERR_INVALID_ARG, "wq_options.checked must be 0 or 1");
+  if ((o->alloc == nullptr) != (o->free == nullptr))
+    return set_error(WQ_ERR_INVALID_ARG, "wq_options.alloc and wq_options.free come together");
   return WQ_OK;
 }
 
 extern "C" wq_status wq_plan_create(wq_plan_t* out, int d, int p, const int64_t n_knots[3],
-                                    const double* const h_knots[3], const double* h_ctrl, void* stream) {
+                                    const double* const h_knots[3], const double* h_ctrl, const wq_options* opt,
+                                    void* stream) {
   if (!out || !n_knots || !h_knots || !h_ctrl) return set_error(WQ_ERR_INVALID_ARG, "NULL argument");
   *out = nullptr;
+  wq_options o;
+  wq_options_init(&o);
+  if (opt) {
+    wq_status vs = validate_options(opt);
+    if (vs != WQ_OK) return vs;
+    o = *opt;
+  }
   if (d != 3) return set_error(WQ_ERR_UNSUPPORTED, "only d = 3 is supported");
   if (p < 2 || p > wq::kMaxP) return set_error(WQ_ERR_INVALID_ARG, "degree must be in 2..8");
   int64_t n[3];
@@ -820,8 +959,14 @@ extern "C" wq_status wq_plan_create(wq_plan_t* out, int d, int p, const int64_t 
   cudaStream_t s = (cudaStream_t)stream;
 
   wq_plan_s* pl = new wq_plan_s();
+  pl->opt = o;
   pl->p = p;
   pl->device = dev;
+  pl->algorithm = o.algorithm;
+  pl->tile[0] = o.tile[0];
+  pl->tile[1] = o.tile[1];
+  if (o.tile[0] == 0 && o.tune_cache) read_tune_cache(o.tune_cache, p, &pl->tile[0], &pl->tile[1]);
+  pl->opt.tune_cache = nullptr;  // the path is not kept
   pl->n_rows = N;
   int64_t nnz = 1;
   int nqmax = 0;
@@ -849,7 +994,7 @@ extern "C" wq_status wq_plan_create(wq_plan_t* out, int d, int p, const int64_t 
   wq_status st = WQ_OK;
 #define ALLOC(ptr, bytes, what)                                  \
   do {                                                           \
-    st = dev_alloc((void**)&(ptr), (size_t)(bytes), what);       \
+    st = dev_alloc(pl, (void**)&(ptr), (size_t)(bytes), s, what); \
     if (st != WQ_OK) {                                           \
       free_plan(pl);                                             \
       return st;                                                 \
@@ -886,6 +1031,7 @@ extern "C" wq_status wq_plan_create(wq_plan_t* out, int d, int p, const int64_t 
     free_plan(pl);
     return code;
   };
+  if (wq::fault("h2d")) return fail(set_error(WQ_ERR_INJECTED, "injected failure of the knot copy"));
   for (int l = 0; l < 3; ++l) {
     cudaError_t e = cudaMemcpyAsync(pl->dir[l].knots, h_knots[l], sizeof(double) * n_knots[l],
                                     cudaMemcpyHostToDevice, s);
@@ -906,10 +1052,12 @@ extern "C" wq_status wq_plan_create(wq_plan_t* out, int d, int p, const int64_t 
   return WQ_OK;
 }
 
-extern "C" wq_status wq_plan_destroy(wq_plan_t plan) {
+extern "C" wq_status wq_destroy(wq_plan_t plan) {
   free_plan(plan);
   return WQ_OK;
 }
+
+extern "C" wq_status wq_plan_destroy(wq_plan_t plan) { return wq_destroy(plan); }
 
 extern "C" wq_status wq_plan_info(wq_plan_t plan, int* p, int64_t n[3], int64_t n_qp[3], int64_t* n_rows,
                                   int64_t* nnz) {
@@ -933,6 +1081,11 @@ extern "C" wq_status wq_plan_pattern(wq_plan_t plan, const int64_t** d_row_ptr, 
 
 static wq_status copy_ctrl(wq_plan_t plan, const double* ctrl, int on_device, cudaStream_t s) {
   if (!ctrl) return WQ_OK;
+  if (!on_device && wq::fault("h2d")) return set_error(WQ_ERR_INJECTED, "injected failure of the control point copy");
+  if (on_device && plan->opt.checked) {
+    wq_status st = wq::check_device_range(plan, ctrl, sizeof(double) * 3 * plan->n_rows, "control points");
+    if (st != WQ_OK) return st;
+  }
   cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
   WQ_CUDA_TRY(cudaMemcpyAsync(plan->ctrl, ctrl, sizeof(double) * 3 * plan->n_rows, kind, s), "control point copy");
   return WQ_OK;

@@ -158,6 +158,15 @@ __device__ __forceinline__ float toOut<float, f2>(f2 x) { return __fadd_rn(x.hi,
 template <>
 __device__ __forceinline__ f2 toOut<f2, f2>(f2 x) { return x; }
 
+// an intermediate stored as S, read into arithmetic type T (double-float T3 read by
+// the FP32 part of stage 2 is rounded to the nearest float)
+template <typename T, typename S>
+__device__ __forceinline__ T fromStore(S x) { return (T)x; }
+template <>
+__device__ __forceinline__ float fromStore<float, f2>(f2 x) { return __fadd_rn(x.hi, x.lo); }
+template <>
+__device__ __forceinline__ f2 fromStore<f2, f2>(f2 x) { return x; }
+
 // read of a volatile shared-memory value
 template <typename T>
 __device__ __forceinline__ T vld(const volatile T* p) { return *p; }
@@ -463,11 +472,13 @@ __device__ __forceinline__ void stage1_edge(const T* G, int64_t gstride, int64_t
 // K2 on the regular rows of direction 2 (Q_i2 = [2 i2 - P, 2 i2 + P]), with the
 // rule and B-spline tables of the block's rows in shared memory: lanes run over
 // 32 consecutive rows i2 (so the T3 reads of a warp are contiguous), the four
-// warps over pairs of q1, and the tables are read from shared memory instead of one cache
-// line per lane. Bs holds B_j2 of the trial rows i0-P .. i0+31+P aligned to the
-// regular pattern: Bs[b][j2 - i0 + P][u] is B^(b)_j2 at point 2 j2 - P + u.
-template <int P, bool MASS, typename Real, typename GOut>
-__global__ void __launch_bounds__(128) k_stage2_reg(StagedArgs A, int r_lo, int r_hi) {
+// warps over pairs of q1 in [q_lo, q_hi), and the tables are read from shared memory
+// instead of one cache line per lane. Bs holds B_j2 of the trial rows i0-P .. i0+31+P
+// aligned to the regular pattern: Bs[b][j2 - i0 + P][u] is B^(b)_j2 at point 2 j2 - P + u.
+// TIn is the stored type of T3 (the mixed mode runs this kernel in FP32 on double-float
+// T3 for the points q1 that no first or last P+1 row of direction 1 reads).
+template <int P, bool MASS, typename Real, typename GOut, typename TIn = Real>
+__global__ void __launch_bounds__(128) k_stage2_reg(StagedArgs A, int r_lo, int r_hi, int q_lo, int q_hi) {
   constexpr int BW = 2 * P + 1;
   constexpr int NT = MASS ? 1 : 9;
   constexpr int NG = MASS ? 1 : 4;
@@ -506,17 +517,17 @@ __global__ void __launch_bounds__(128) k_stage2_reg(StagedArgs A, int r_lo, int 
   const int64_t nnz2 = A.nnz1[1];
   const int64_t pbase = D2.prefix[i2];
   const int64_t tstride = (int64_t)nq1 * nq2;
-  const Real* T3p = reinterpret_cast<const Real*>(A.T3) + (p3 * NT) * tstride + (2 * i2 - P);
+  const TIn* T3p = reinterpret_cast<const TIn*>(A.T3) + (p3 * NT) * tstride + (2 * i2 - P);
   // volatile views: the compiler would otherwise hoist all of the row's table
   // values out of the q1 loop into registers and spill
   const volatile Real* Wv = &Ws[0][lane][0];
   const volatile Real* Bv = &Bs[0][lane][0];
   // two q1 points per iteration: every shared-memory value feeds two FMA chains
 #pragma unroll 1
-  for (int qa = 2 * warp; qa < nq1; qa += 8) {
-    const int qb = min(qa + 1, nq1 - 1);  // the last iteration may repeat qa
-    const Real* Ta = T3p + (int64_t)qa * nq2;
-    const Real* Tb = T3p + (int64_t)qb * nq2;
+  for (int qa = q_lo + 2 * warp; qa < q_hi; qa += 8) {
+    const int qb = min(qa + 1, q_hi - 1);  // the last iteration may repeat qa
+    const TIn* Ta = T3p + (int64_t)qa * nq2;
+    const TIn* Tb = T3p + (int64_t)qb * nq2;
     Real acc[2][BW];
 #pragma unroll(CU)
     for (int c = 0; c < NC; ++c) {
@@ -536,8 +547,8 @@ __global__ void __launch_bounds__(128) k_stage2_reg(StagedArgs A, int r_lo, int 
 #pragma unroll
         for (int t = 0; t < BW; ++t) {
           const Real wv = vld(Wv + k2 * RW * BW + t);
-          h[0][t] = fmaR<Real>(wv, ro(Ta + term * tstride + t), h[0][t]);
-          h[1][t] = fmaR<Real>(wv, ro(Tb + term * tstride + t), h[1][t]);
+          h[0][t] = fmaR<Real>(wv, fromStore<Real>(ro(Ta + term * tstride + t)), h[0][t]);
+          h[1][t] = fmaR<Real>(wv, fromStore<Real>(ro(Tb + term * tstride + t)), h[1][t]);
         }
       }
       const int g = MASS ? 0 : ci.g;
@@ -757,48 +768,45 @@ static wq_status staged_scratch(wq_plan_s* pl, size_t t3, size_t g, size_t gb, b
   t3 = std::max<size_t>(16, t3);
   g = std::max<size_t>(16, g);
   if (pl->stg_a_bytes < t3 || pl->stg_b_bytes < g) {
-    if (pl->stg_a) cudaFree(pl->stg_a);
-    if (pl->stg_b) cudaFree(pl->stg_b);
+    plan_free(pl, pl->stg_a, s);
+    plan_free(pl, pl->stg_b, s);
     pl->stg_a = pl->stg_b = nullptr;
     pl->stg_a_bytes = pl->stg_b_bytes = 0;
-    cudaError_t e = cudaMalloc(&pl->stg_a, t3);
-    if (e == cudaSuccess) e = cudaMalloc(&pl->stg_b, g);
-    if (e != cudaSuccess) {
-      cudaGetLastError();
-      if (pl->stg_a) cudaFree(pl->stg_a);
+    wq_status st = plan_alloc(pl, &pl->stg_a, t3, s, "staged assembly scratch (T3)");
+    if (st == WQ_OK) st = plan_alloc(pl, &pl->stg_b, g, s, "staged assembly scratch (G)");
+    if (st != WQ_OK) {
+      plan_free(pl, pl->stg_a, s);
       pl->stg_a = nullptr;
-      return set_error(WQ_ERR_OOM, "staged assembly scratch (T3, G) does not fit in device memory");
+      return st;
     }
     pl->stg_a_bytes = t3;
     pl->stg_b_bytes = g;
   }
   if (pl->stg_c_bytes < gb) {
-    if (pl->stg_c) cudaFree(pl->stg_c);
+    plan_free(pl, pl->stg_c, s);
     pl->stg_c = nullptr;
     pl->stg_c_bytes = 0;
-    cudaError_t e = cudaMalloc(&pl->stg_c, gb);
-    if (e != cudaSuccess) {
-      cudaGetLastError();
-      pl->stg_c = nullptr;
-      return set_error(WQ_ERR_OOM, "staged assembly scratch (FP64 edge copy of G) does not fit in device memory");
-    }
+    wq_status st = plan_alloc(pl, &pl->stg_c, gb, s, "staged assembly scratch (FP64 edge copy of G)");
+    if (st != WQ_OK) return st;
     pl->stg_c_bytes = gb;
   }
   if (!pl->coefT) {
-    cudaError_t e = cudaMalloc(&pl->coefT, sizeof(double) * 8 * (size_t)pl->n_qp_total);
-    if (e != cudaSuccess) return wq::cuda_error(e, "transposed coefficient allocation");
+    wq_status st = plan_alloc(pl, (void**)&pl->coefT, sizeof(double) * 8 * (size_t)pl->n_qp_total, s,
+                              "transposed coefficients");
+    if (st != WQ_OK) return st;
   }
   if (need_f32)
     for (int l = 0; l < 3; ++l)
       if (!pl->dir[l].tab32) {
         const size_t nt = (size_t)6 * pl->dir[l].n * pl->nq_max;  // 4 rule kinds + 2 basis tables
-        cudaError_t e = cudaMalloc(&pl->dir[l].tab32, sizeof(float) * nt);
-        if (e != cudaSuccess) return wq::cuda_error(e, "float table allocation");
+        wq_status st = plan_alloc(pl, (void**)&pl->dir[l].tab32, sizeof(float) * nt, s, "float tables");
+        if (st != WQ_OK) return st;
       }
   for (int l = 1; l < 3; ++l)
     if (!pl->dir[l].pair_row) {
-      cudaError_t e = cudaMalloc(&pl->dir[l].pair_row, sizeof(int) * (size_t)std::max<int64_t>(1, pl->nnz1[l]));
-      if (e != cudaSuccess) return wq::cuda_error(e, "pair index allocation");
+      wq_status st = plan_alloc(pl, (void**)&pl->dir[l].pair_row,
+                                sizeof(int) * (size_t)std::max<int64_t>(1, pl->nnz1[l]), s, "pair index");
+      if (st != WQ_OK) return st;
       k_pair_rows<<<(pl->dir[l].n + 127) / 128, 128, 0, s>>>(pl->dir[l].prefix, pl->dir[l].n, pl->dir[l].pair_row);
       count_launch();
     }
@@ -840,8 +848,8 @@ static wq_status staged_t(wq_plan_s* pl, const double* kappa, void* vals, cudaSt
     if (F2) {
       const int64_t nw = (int64_t)4 * d.n * pl->nq_max, nb = (int64_t)2 * d.n * pl->nq_max;
       if (!d.tabf2) {
-        cudaError_t e = cudaMalloc(&d.tabf2, sizeof(f2) * (size_t)(nw + nb));
-        if (e != cudaSuccess) return wq::cuda_error(e, "double-float table allocation");
+        wq_status st = plan_alloc(pl, &d.tabf2, sizeof(f2) * (size_t)(nw + nb), s, "double-float tables");
+        if (st != WQ_OK) return st;
       }
       f2* t = reinterpret_cast<f2*>(d.tabf2);
       k_to_f2<<<(unsigned)((nw + 255) / 256), 256, 0, s>>>(d.w, t, nw);
@@ -882,6 +890,7 @@ static wq_status staged_t(wq_plan_s* pl, const double* kappa, void* vals, cudaSt
   A.nbl = A1.nbl = nbl;
   A.hstart = A1.hstart = hstart;
   A.nbq = A1.nbq = nbq;
+  if (!vals) return WQ_OK;  // wq_plan_reserve: scratch only
   // transposed coefficients (the slots this matrix uses) and kappa, in Real
   {
     dim3 blk(32, 8), grd((nq1 + 31) / 32, (nq2 + 31) / 32, 7 * nq3 + (kappa ? nq3 : 0));
@@ -902,7 +911,7 @@ static wq_status staged_t(wq_plan_s* pl, const double* kappa, void* vals, cudaSt
         <<<dim3((unsigned)(((int64_t)nreg * nq1 + 127) / 128), (unsigned)np3), 128, 0, s>>>(A, r_lo, r_hi);
   else if (nreg > 0)
     k_stage2_reg<P, MASS, Real, R1>
-        <<<dim3((unsigned)((nreg + 31) / 32), (unsigned)np3), dim3(32, 4), 0, s>>>(A, r_lo, r_hi);
+        <<<dim3((unsigned)((nreg + 31) / 32), (unsigned)np3), dim3(32, 4), 0, s>>>(A, r_lo, r_hi, 0, nq1);
   const int nb = r_lo + (n2 - r_hi);
   const bool edge2 = pl->dir[1].n_el >= 2 * P + 2;  // edge rows with compile-time patterns
   if (edge2)

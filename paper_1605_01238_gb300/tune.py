@@ -2,16 +2,16 @@
 
 For each degree it builds a seeded perturbed spline cube, times the FP64 stiffness
 assembly for every candidate (t1, t2) that fits in shared memory, and keeps the
-fastest. Results are cached as JSON {"p": [t1, t2], ...}; load_tiles() reads the
-cache and apply_tiles() sets each plan's tiles from it.
+fastest. Results are cached as a text file of "p t1 t2" lines, the format that
+wq_options.tune_cache reads at plan creation; load_tiles() reads the cache and
+apply_tiles() sets each plan's tiles from it.
 """
 from __future__ import annotations
 
-import json
 import os
 
 CANDIDATES = [(8, 2), (8, 4), (12, 4), (16, 2), (16, 4), (24, 2), (24, 4), (32, 2), (32, 4), (16, 6), (12, 6)]
-DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "wq_gb300_tiles.json")
+DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "wq_gb300_tiles.txt")
 
 
 def tune(degrees=(2, 3, 4, 5), n_el: int = 24, reps: int = 3, cache: str | None = DEFAULT_CACHE,
@@ -46,17 +46,31 @@ def tune(degrees=(2, 3, 4, 5), n_el: int = 24, reps: int = 3, cache: str | None 
             print(f"p={p}: " + ", ".join(f"{k}: {v:.3f} ms" for k, v in sorted(timings.items(), key=lambda x: x[1])))
         plan.close()
     if cache:
-        os.makedirs(os.path.dirname(cache), exist_ok=True)
-        with open(cache, "w") as f:
-            json.dump(best, f)
+        save_tiles(best, cache)
     return best
+
+
+def save_tiles(tiles: dict, cache: str = DEFAULT_CACHE) -> None:
+    """Write {p: (t1, t2)} as "p t1 t2" lines."""
+    d = os.path.dirname(cache)
+    if d:
+        os.makedirs(d, exist_ok=True)
+    with open(cache, "w") as f:
+        f.write("# p t1 t2: fused-assembly tile extents per degree\n")
+        for p, (t1, t2) in sorted((int(k), v) for k, v in tiles.items()):
+            f.write(f"{p} {int(t1)} {int(t2)}\n")
 
 
 def load_tiles(cache: str = DEFAULT_CACHE) -> dict:
     if not os.path.exists(cache):
         return {}
+    out = {}
     with open(cache) as f:
-        return {int(k): tuple(v) for k, v in json.load(f).items()}
+        for line in f:
+            parts = line.split("#", 1)[0].split()
+            if len(parts) == 3:
+                out[int(parts[0])] = (int(parts[1]), int(parts[2]))
+    return out
 
 
 def apply_tiles(plans, tiles: dict) -> None:

@@ -58,7 +58,7 @@ def _create(lib, p, knots, ctrl, d=3):
     kp = (ctypes.c_void_p * 3)(*[k.ctypes.data for k in kn])
     h = ctypes.c_void_p()
     ctrl = np.ascontiguousarray(ctrl, dtype=np.float64)
-    st = lib.wq_plan_create(ctypes.byref(h), d, p, n_knots, kp, ctypes.c_void_p(ctrl.ctypes.data), None)
+    st = lib.wq_plan_create(ctypes.byref(h), d, p, n_knots, kp, ctypes.c_void_p(ctrl.ctypes.data), None, None)
     return st, h
 
 
@@ -107,3 +107,72 @@ def test_python_plan_fails_loudly_without_device():
     patch = perturbed_cube(2, 3, seed=1)
     with pytest.raises((wq.WqError, RuntimeError)):
         wq.Plan(2, patch.knots, patch.ctrl)
+
+
+def test_interface_names_of_the_boundary():
+    """The entry points the library's interface description names are declared."""
+    names = declared_functions()
+    for name in ("wq_options_init", "wq_plan_create", "wq_plan_info", "wq_plan_pattern", "wq_assemble_stiffness",
+                 "wq_assemble_mass", "wq_adjoint", "wq_batch_create", "wq_batch_assemble", "wq_sync_check",
+                 "wq_last_error", "wq_destroy", "wq_plan_reserve"):
+        assert name in names, name
+
+
+def test_options_init_fills_the_defaults(lib):
+    from paper_1605_01238_gb300._lib import Options
+    o = Options()
+    assert lib.wq_options_init(ctypes.byref(o)) == 0
+    assert o.size == ctypes.sizeof(Options)
+    assert (o.value_dtype, o.precision, o.algorithm, o.tile[0], o.tile[1], o.checked) == (0, 0, 2, 0, 0, 0)
+    assert not o.alloc and not o.free and not o.tune_cache
+    assert lib.wq_options_init(None) == 1
+
+
+def _create_opt(lib, opt):
+    from wq_synth import perturbed_cube
+    patch = perturbed_cube(2, 3, seed=1)
+    kn = [np.ascontiguousarray(k, dtype=np.float64) for k in patch.knots]
+    n_knots = (ctypes.c_int64 * 3)(*[len(k) for k in kn])
+    kp = (ctypes.c_void_p * 3)(*[k.ctypes.data for k in kn])
+    h = ctypes.c_void_p()
+    ctrl = np.ascontiguousarray(patch.ctrl)
+    return lib.wq_plan_create(ctypes.byref(h), 3, 2, n_knots, kp, ctypes.c_void_p(ctrl.ctypes.data),
+                              ctypes.byref(opt), None)
+
+
+@pytest.mark.parametrize("field,value,needle", [
+    ("size", 8, b"size"), ("value_dtype", 5, b"value_dtype"), ("precision", 9, b"precision"),
+    ("algorithm", 7, b"algorithm"), ("checked", 2, b"checked")])
+def test_invalid_options_are_rejected_before_any_device_work(lib, field, value, needle):
+    from paper_1605_01238_gb300._lib import Options
+    o = Options()
+    lib.wq_options_init(ctypes.byref(o))
+    setattr(o, field, value)
+    assert _create_opt(lib, o) == 1
+    assert needle in lib.wq_last_error()
+
+
+def test_options_reject_fp32_values_under_fp64_and_lone_allocators(lib):
+    from paper_1605_01238_gb300._lib import ALLOC_FN, Options
+    o = Options()
+    lib.wq_options_init(ctypes.byref(o))
+    o.value_dtype = 1
+    assert _create_opt(lib, o) == 1
+    o = Options()
+    lib.wq_options_init(ctypes.byref(o))
+    o.tile[0] = 8                                                     # the other extent left at 0
+    assert _create_opt(lib, o) == 1
+    o = Options()
+    lib.wq_options_init(ctypes.byref(o))
+    o.alloc = ALLOC_FN(lambda size, stream, ctx: None)                # alloc without free
+    assert _create_opt(lib, o) == 1
+    assert b"alloc" in lib.wq_last_error()
+
+
+def test_tune_cache_round_trip(tmp_path):
+    from paper_1605_01238_gb300 import tune
+    path = str(tmp_path / "tiles.txt")
+    tune.save_tiles({4: (12, 4), 2: (16, 2)}, path)
+    text = open(path).read()
+    assert "4 12 4" in text and "2 16 2" in text
+    assert tune.load_tiles(path) == {2: (16, 2), 4: (12, 4)}
