@@ -147,6 +147,9 @@ def make_workload(name: str):
     import wq_synth as ws
     if name.startswith("sweep"):
         return ws.workload_sweep(int(name[5:]))
+    if name.startswith("cube_"):               # cube_<p>_<n_el>: a smaller case of the same family
+        _, p, ne = name.split("_")
+        return ws.perturbed_cube(int(p), int(ne), seed=1605 + 2)
     return {"p5_128": ws.workload_p5_128, "p4_64": ws.workload_p4_64, "small": ws.workload_small}[name]()
 
 
@@ -347,6 +350,8 @@ PRECISION_MODES = {
     # name: (precision, value dtype, what)
     "mixed": ("mixed", "f32", "q3, q2 mode products in double-float, q1 in FP32 (FP64 edge rows)"),
     "mixed_f64vals": ("mixed", "f64", "as mixed, FP64 values"),
+    "tf32x3": ("tf32x3", "f32", "as mixed, the regular rows of the q1 mode product as 3xTF32 mma.sync "
+                                "(tensor cores), FP32 accumulation"),
     "f32x2": ("f32x2", "f64", "double-float (pairs of floats) in all three mode products"),
     "fp32": ("fp32", "f32", "FP32 in all three mode products"),
 }
@@ -376,6 +381,7 @@ def precision_study(wq, torch, stream, name: str = "p5_128"):
         modes[m].update(e)
     modes["mixed"]["bar"] = 1e-6
     modes["mixed_f64vals"]["bar"] = 1e-6
+    modes["tf32x3"]["bar"] = 1e-6
     modes["f32x2"]["bar"] = 1e-12
     plan.close()
     torch.cuda.empty_cache()
@@ -400,21 +406,6 @@ def assembly_only(wq, torch, stream, name: str):
     return out
 
 
-def host_buffer(torch, count: int):
-    """A float64 host array of `count` elements, page-locked with cudaHostRegister
-    (exact size; torch's pinned allocator rounds up to a power of two)."""
-    arr = np.empty(count, dtype=np.float64)
-    try:
-        cr = torch._C._cudart
-        ok = cr.cudaHostRegister(arr.ctypes.data, arr.nbytes, 0) == cr.cudaError.success
-    except Exception:
-        ok = False
-    return arr, ok
-
-
-def release_host_buffer(torch, arr, registered: bool) -> None:
-    if registered:
-        torch._C._cudart.cudaHostUnregister(arr.ctypes.data)
 
 
 def run_reference(args):
@@ -524,7 +515,8 @@ def run_ours(args):
 
     # end to end through the C ABI with host buffers (page-locked)
     h_ctrl = torch.as_tensor(patch.ctrl.reshape(-1)).pin_memory()
-    h_vals, registered = host_buffer(torch, nnz)
+    hbuf = wq.HostBuffer(nnz)        # page-locked, exactly nnz doubles (wq_host_alloc)
+    h_vals = hbuf.array
     plan.assemble_host("stiffness", h_ctrl, vals, h_vals)
     barrier(dist)
     t0 = time.perf_counter()
@@ -533,8 +525,8 @@ def run_ours(args):
         plan.assemble_host("stiffness", h_ctrl, vals, h_vals)
     e2e_s = (time.perf_counter() - t0) / e2e_steps
     e2e_s = max_over_ranks(dist, e2e_s)
-    release_host_buffer(torch, h_vals, registered)
     del h_vals
+    hbuf.close()
     plan.close()
     del vals, ctrl_d
     torch.cuda.empty_cache()
@@ -574,8 +566,9 @@ def run_ours(args):
         "p4_64": extra_p4,
         "batch": batch_line,
         "e2e": {"value": world * nnz / e2e_s, "unit": "nnz/s", "h2d_bytes_per_step": 8 * 3 * N,
-                "d2h_bytes_per_step": 8 * nnz, "host_values_page_locked": registered,
-                "call": "wq_assemble_host: H2D control points, refresh, assemble, D2H values"},
+                "d2h_bytes_per_step": 8 * nnz, "host_values": "page-locked (wq_host_alloc)",
+                "call": "wq_assemble_host: H2D control points, refresh, slab-by-slab assembly with the "
+                        "D2H copy of each slab's values overlapping the next slab"},
         "gpu_launches": int(launches), "clocks": clocks,
     }
     if rank == 0 and not args.no_cpu_baseline:
@@ -598,7 +591,8 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="sweep8", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="sweep8",
+                    help="sweep8 (default), sweep2..sweep6, p5_128, p4_64, small, or cube_<p>_<n_el>")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-step-seconds", type=float, default=2.0,
                     help="CPU seconds of oracle work per step of --impl reference")

@@ -73,12 +73,17 @@ enum { WQ_VALUES_F64 = 0, WQ_VALUES_F32 = 1 };
 enum {
   WQ_PREC_FP64 = 0,          /* FP64 FMA throughout */
   WQ_PREC_FP32 = 1,          /* FP32 FMA, FP32 intermediates */
-  WQ_PREC_MIXED = 2,         /* double-float (see below) for the first two mode products
-                                (contracting q3, q2), FP32 for the last one (q1, half of the
-                                work) except its first and last p+1 rows of direction 1, which
-                                run in FP64; <= 1e-6 row-relative; staged only */
-  WQ_PREC_F32X2 = 3          /* double-float: every value a pair of floats (~48 significant
+  WQ_PREC_MIXED = 2,         /* double-float (see below) for the first mode product (contracting
+                                q3); the second (q2) in double-float for the first and last p+1
+                                rows of direction 2 and for the points q1 that the first and last
+                                p+1 rows of direction 1 read, FP32 elsewhere; the last (q1) in
+                                FP32 except its first and last p+1 rows of direction 1, which run
+                                in FP64; <= 1e-6 row-relative; staged only */
+  WQ_PREC_F32X2 = 3,         /* double-float: every value a pair of floats (~48 significant
                                 bits), all three mode products on the FP32 pipe; staged only */
+  WQ_PREC_TF32X3 = 4         /* as WQ_PREC_MIXED, with the regular rows of the last mode product
+                                on the tensor cores: 3xTF32 products (each operand split into two
+                                TF32 parts), FP32 accumulation; <= 1e-6 row-relative; staged only */
 };
 
 /* Default sentinels of the assembly calls: use the plan's wq_options value. */
@@ -113,6 +118,11 @@ enum {
  *                (NULL when wq_destroy releases the plan, after it has
  *                synchronised the device). Both or neither must be given.
  *   alloc_ctx    passed through to alloc and free
+ *   scratch_limit  0 (default: the staged assembly keeps the intermediates of the
+ *                whole mesh), or the most bytes of staged scratch (T3, G and the FP64
+ *                edge copy of G) to hold at once: the mode products then run slab by
+ *                slab of direction 3, each slab at least one row i3 (which can need
+ *                more than the limit)
  */
 typedef struct wq_options {
   size_t size;
@@ -125,6 +135,7 @@ typedef struct wq_options {
   void* (*alloc)(size_t bytes, void* stream, void* ctx);
   void (*free)(void* ptr, void* stream, void* ctx);
   void* alloc_ctx;
+  size_t scratch_limit;
 } wq_options;
 
 wq_status wq_options_init(wq_options* opt);
@@ -178,6 +189,33 @@ wq_status wq_plan_pattern(wq_plan_t plan, const int64_t** d_row_ptr, const int32
  * and must be pinned for the copy to be asynchronous). */
 wq_status wq_plan_set_geometry(wq_plan_t plan, const double* ctrl, int ctrl_on_device,
                                void* stream);
+
+/* NURBS geometry (the paper's parametrisations are "spline or NURBS", Section 3):
+ * with weights w_i > 0 the map is F = sum_i w_i C_i B_i / W, W = sum_i w_i B_i, and
+ * DF, det DF and c_lm follow the rational map; the basis functions stay the
+ * B-splines pushed forward (R_i = B_i o F^{-1}, Section 3), so the stiffness and
+ * mass matrices keep their form. With nurbs_basis = 1 the basis functions are the
+ * NURBS w_i B_i / W instead, for which the mass entry is w_i w_j times the B-spline
+ * entry with c = det DF / W^2 (the denominator absorbed by c, as stated after
+ * Eq. (mass2)); the stiffness then needs terms this library does not assemble, and
+ * wq_assemble_stiffness returns WQ_ERR_UNSUPPORTED.
+ *   w            NULL (a spline map again), or double[N_DOF] weights, i1 fastest;
+ *                host (checked positive) or device memory (on_device = 1), copied
+ *   nurbs_basis  0 or 1 (1 requires weights)
+ * Recomputes the coefficients on `stream`. The first call allocates the plan-owned
+ * copy of the weights. A point where W <= 0 is reported as WQ_ERR_BAD_GEOMETRY by
+ * the next synchronous call. wq_adjoint does not handle a rational map. */
+wq_status wq_plan_set_weights(wq_plan_t plan, const double* w, int on_device, int nurbs_basis, void* stream);
+
+/* Coefficient tensor of the operator -div(K grad u) (Eq. (coef_stiff) with K:
+ * c_lm = det DF (DF^{-1} K DF^{-T})_lm; "c incorporates the coefficient of the
+ * equation", after Eq. (mass2)).
+ *   d_K  NULL (K = I again), or device double[6][N_QP]: K11 K12 K13 K22 K23 K33 at
+ *        every point (q1 fastest), symmetric positive definite (not checked), copied
+ * Recomputes the coefficients on `stream`; the first call allocates the plan-owned
+ * copy. A scalar field d_kappa of the assembly calls still multiplies the result.
+ * wq_adjoint does not handle a tensor. */
+wq_status wq_plan_set_tensor(wq_plan_t plan, const double* d_K, void* stream);
 
 /* Re-runs in place on `stream` every set-up kernel that depends on the knots or
  * the control points (points, tables, integrals, rules, CSR pattern and
@@ -242,10 +280,18 @@ wq_status wq_plan_get_tiles(wq_plan_t plan, int* t1, int* t2);
 /* End-to-end call with host buffers: copies h_ctrl (NULL = keep) to the device,
  * refreshes the plan, assembles S (which = 0) or M (which = 1) in FP64 into the
  * caller's device staging array d_vals (nnz doubles) and copies the values to
- * h_vals (nnz doubles; pinned memory makes the copies asynchronous). Returns
- * after `stream` has finished the copy back. */
+ * h_vals (nnz doubles). With the staged algorithm the assembly runs in slabs of
+ * direction 3 and each slab's values (a contiguous range of the CSR rows) are
+ * copied back on a plan-owned copy stream while the next slab is assembled;
+ * page-locked h_vals (wq_host_alloc) makes those copies asynchronous. Returns after
+ * both streams have finished. */
 wq_status wq_assemble_host(wq_plan_t plan, int which, const double* h_ctrl, double* d_vals,
                            double* h_vals, void* stream);
+
+/* Page-locked host memory for the end-to-end call (cudaHostAlloc of exactly
+ * `bytes`; wq_host_free releases it). */
+wq_status wq_host_alloc(size_t bytes, void** h_ptr);
+wq_status wq_host_free(void* h_ptr);
 
 /* ---- adjoint ------------------------------------------------------------------
  * J = lambda^T S u (which = 1), lambda^T M u (which = 2) or both (which = 3), for

@@ -18,7 +18,11 @@ library steps:
 * exact univariate integrals I^{(a,b)} ............ Eq. (integrals); element-wise Gauss (Algorithm 1)
 * WQ rules, four kinds, minimum Euclidean norm .... Eqs. (quadrule), (exact), (support); Algorithm 2;
                                                     Remark "computation of quadrature weights"
-* coefficients c_lm and c ......................... Eq. (coef_stiff) and Eq. (mass2)
+* coefficients c_lm and c ......................... Eq. (coef_stiff) and Eq. (mass2); a
+                                                    coefficient tensor K in c_lm =
+                                                    det DF (DF^{-1} K DF^{-T})_lm and NURBS
+                                                    geometry / basis denominators (the
+                                                    sentence after Eq. (mass2))
 * WQ mass / stiffness entries ..................... Eq. (Mass_approx), Eq. (massquadrature) and
                                                     Eq. (stiff) with the term (l, m) integrated by
                                                     the rule (delta_kl, delta_km) in direction k
@@ -37,6 +41,13 @@ Readings where the paper is ambiguous:
   the right-hand side is consistent, so the last equation is dropped and the
   minimum-norm solution of the remaining full-row-rank system is taken.
 * det DF must be positive at every quadrature point (Eq. (mass2) uses det DF).
+* NURBS: with weights w_i the geometry is F = sum_i w_i C_i B_i / W, W = sum_i w_i B_i.
+  The basis functions stay R_i = B_i o F^{-1} (Section 3 defines them so), so only
+  DF changes. With NURBS basis functions R_i = (w_i B_i / W) o F^{-1} the mass entry
+  is w_i w_j times the B-spline entry with c = det DF / W^2: the denominator is
+  absorbed by c, as the sentence after Eq. (mass2) states. (The stiffness with NURBS
+  basis functions would need the lower-order terms of the quotient rule, which the
+  paper does not treat; it is not provided.)
 
 Parity unpinned: none of the functions below lacks a pin; entries on curved
 (perturbed) geometry are pinned only through the invariants (row sums of the
@@ -427,20 +438,82 @@ def jacobians(dirs: list, ctrl: np.ndarray) -> np.ndarray:
     return out
 
 
-def coefficients(dirs: list, ctrl: np.ndarray, kappa: np.ndarray | None = None) -> np.ndarray:
+def _active(d) -> tuple:
+    """First basis function s - p of the span s holding each point (x in [xi_s, xi_{s+1}),
+    the last span for the right end) and the p+1 values B^{(b)}_{s-p+t}(x_q): (first[nqp],
+    vals[2, nqp, p+1])."""
+    p = d.p
+    s = np.clip(np.searchsorted(d.xi, d.x, side="right") - 1, p, d.n - 1)
+    first = s - p
+    cols = first[:, None] + np.arange(p + 1)[None, :]
+    vals = np.stack([d.B[b][cols, np.arange(d.nqp)[:, None]] for b in (0, 1)])
+    return first, vals
+
+
+def rational_jacobians(dirs: list, ctrl: np.ndarray, weights: np.ndarray, with_map: bool = False) -> tuple:
+    """DF and W at every point of the tensor grid for the NURBS map
+    F = sum_i w_i C_i B_i / W, W = sum_i w_i B_i: arrays (nqp3, nqp2, nqp1, 3, 3) and
+    (nqp3, nqp2, nqp1). Point by point over the (p+1)^3 functions active there,
+    F first and then DF = sum_i w_i (C_i - F) x grad B_i / W (the quotient rule with
+    sum_i w_i grad B_i = grad W); the differences C_i - F stay small, so the O(1/h)
+    gradients do not cancel in the sum."""
+    p = dirs[0].p
+    n1, n2, n3 = (d.n for d in dirs)
+    C = np.asarray(ctrl, dtype=np.float64).reshape(n3, n2, n1, 3)
+    w = np.asarray(weights, dtype=np.float64).reshape(n3, n2, n1)
+    (f1, v1), (f2, v2), (f3, v3) = (_active(d) for d in dirs)
+    t = np.arange(p + 1)
+    I3 = (f3[:, None] + t)[:, None, None, :, None, None]
+    I2 = (f2[:, None] + t)[None, :, None, None, :, None]
+    I1 = (f1[:, None] + t)[None, None, :, None, None, :]
+    Cw = C[I3, I2, I1]                                   # (q3, q2, q1, t3, t2, t1, 3)
+    ww = w[I3, I2, I1]                                   # (q3, q2, q1, t3, t2, t1)
+    def tens(b1, b2, b3):
+        return (v3[b3][:, None, None, :, None, None] * v2[b2][None, :, None, None, :, None] *
+                v1[b1][None, None, :, None, None, :])
+    B0 = tens(0, 0, 0)
+    Wq = np.einsum("abcxyz,abcxyz->abc", ww, B0)
+    F = np.einsum("abcxyz,abcxyzr->abcr", ww * B0, Cw) / Wq[..., None]
+    D = Cw - F[:, :, :, None, None, None, :]
+    grads = [tens(1, 0, 0), tens(0, 1, 0), tens(0, 0, 1)]
+    J = np.empty(Wq.shape + (3, 3))
+    for c in range(3):
+        J[..., :, c] = np.einsum("abcxyz,abcxyzr->abcr", ww * grads[c], D) / Wq[..., None]
+    return (J, Wq, F) if with_map else (J, Wq)
+
+
+def coefficients(dirs: list, ctrl: np.ndarray, kappa: np.ndarray | None = None,
+                 weights: np.ndarray | None = None, K: np.ndarray | None = None,
+                 nurbs_basis: bool = False) -> np.ndarray:
     """coef[7, nqp3, nqp2, nqp1]: c_11, c_12, c_13, c_22, c_23, c_33 of
-    det DF * DF^{-1} DF^{-T} (Eq. (coef_stiff)) and c = det DF (Eq. (mass2)),
-    each times kappa when kappa (same grid) is given."""
-    J = jacobians(dirs, ctrl)
+    det DF * DF^{-1} K DF^{-T} (Eq. (coef_stiff), K = I unless the symmetric tensor
+    field K[6, ...] = K11 K12 K13 K22 K23 K33 is given) and c = det DF (Eq. (mass2);
+    det DF / W^2 for NURBS basis functions), each times kappa when kappa (same grid)
+    is given. weights: NURBS weights of the control points (rational map)."""
+    if weights is not None:
+        J, Wq = rational_jacobians(dirs, ctrl, weights)
+    else:
+        J, Wq = jacobians(dirs, ctrl), None
     det = np.linalg.det(J)
     if not np.all(np.isfinite(det)) or np.any(det <= 0.0):
         raise ValueError("det DF must be positive at every quadrature point")
     Jinv = np.linalg.inv(J)
-    P = np.einsum("...ik,...jk->...ij", Jinv, Jinv) * det[..., None, None]
+    if K is None:
+        P = np.einsum("...ik,...jk->...ij", Jinv, Jinv) * det[..., None, None]
+    else:
+        Kf = np.asarray(K, dtype=np.float64).reshape((6,) + det.shape)
+        Km = np.empty(det.shape + (3, 3))
+        for s, (l, m) in enumerate(COEF_LM):
+            Km[..., l, m] = Km[..., m, l] = Kf[s]
+        P = np.einsum("...ia,...ab,...jb->...ij", Jinv, Km, Jinv) * det[..., None, None]
     out = np.empty((7,) + det.shape)
     for s, (l, m) in enumerate(COEF_LM):
         out[s] = P[..., l, m]
     out[6] = det
+    if nurbs_basis:
+        if Wq is None:
+            raise ValueError("NURBS basis functions need weights")
+        out[6] = det / Wq ** 2
     if kappa is not None:
         out *= np.asarray(kappa, dtype=np.float64).reshape(det.shape)[None]
     return out
@@ -456,13 +529,24 @@ def coef_index(l: int, m: int) -> int:
 class Oracle3D:
     """Oracle for one 3D patch: univariate rules, coefficients, and entries."""
 
-    def __init__(self, p: int, knots: list, ctrl: np.ndarray, kappa: np.ndarray | None = None):
+    def __init__(self, p: int, knots: list, ctrl: np.ndarray, kappa: np.ndarray | None = None,
+                 weights: np.ndarray | None = None, K: np.ndarray | None = None, nurbs_basis: bool = False):
         self.p = p
         self.dirs = [Direction(k, p) for k in knots]
         self.n = tuple(d.n for d in self.dirs)
         self.nqp = tuple(d.nqp for d in self.dirs)
         self.ctrl = np.asarray(ctrl, dtype=np.float64).reshape(-1, 3)
-        self.coef = coefficients(self.dirs, self.ctrl, kappa)
+        self.weights = None if weights is None else np.asarray(weights, dtype=np.float64).reshape(-1)
+        self.nurbs_basis = bool(nurbs_basis)
+        self.coef = coefficients(self.dirs, self.ctrl, kappa, self.weights, K, self.nurbs_basis)
+
+    def basis_scale(self, r: int, which: str):
+        """w_i w_j of row r for NURBS basis functions (mass only), else None."""
+        if not self.nurbs_basis:
+            return None
+        if which != "mass":
+            raise ValueError("the stiffness with NURBS basis functions is not provided")
+        return self.weights[r] * self.weights[self.row_cols(r)]
 
     # -- pattern (Section 3: I_i = prod I_{l,i_l}; linear index i1 + n1(i2 + n2 i3))
     def row_multi(self, r: int) -> tuple:
@@ -501,7 +585,8 @@ class Oracle3D:
                  for k, (d, ik, (a, b)) in enumerate(zip(self.dirs, i, kinds))]
             # nested sum: innermost over q3, then q2, then q1
             out += np.einsum("xc,yb,za,cba->xyz", A[2], A[1], A[0], cc, optimize=False)
-        return out.ravel()
+        scale = self.basis_scale(r, which)
+        return out.ravel() if scale is None else out.ravel() * scale
 
     def rows(self, rows, which: str) -> list:
         return [self.row_values(int(r), which) for r in rows]
@@ -519,10 +604,13 @@ class Oracle3D:
 # Brute-force Galerkin matrices (Eqs. (stiffness-3d), (mass-3d)) for the pins
 
 def galerkin_dense(p: int, knots: list, ctrl: np.ndarray, ng: int | None = None,
-                   kappa_fn=None) -> tuple:
+                   kappa_fn=None, weights: np.ndarray | None = None, K: np.ndarray | None = None,
+                   nurbs_basis: bool = False) -> tuple:
     """Exact-as-Gauss Galerkin stiffness and mass on the parametric cube:
-    s_ij = int grad B_i . (det DF DF^{-1} DF^{-T}) grad B_j, m_ij = int B_i B_j det DF,
-    by ng^3-point Gauss on every element (tiny meshes only)."""
+    s_ij = int grad B_i . (det DF DF^{-1} K DF^{-T}) grad B_j, m_ij = int R_i R_j det DF
+    (R_i = B_i, or w_i B_i / W for NURBS basis functions), by ng^3-point Gauss on every
+    element (tiny meshes only). weights: NURBS weights of the map F = sum w C B / W;
+    K: constant symmetric 3x3 coefficient tensor (default I)."""
     ng = ng if ng is not None else p + 2
     t, wt = np.polynomial.legendre.leggauss(ng)
     gx, gw = [], []
@@ -541,18 +629,28 @@ def galerkin_dense(p: int, knots: list, ctrl: np.ndarray, ng: int | None = None,
         return np.einsum("ax,by,cz->cbazyx", B[0][d1], B[1][d2], B[2][d3])
     Bv = tensor(0, 0, 0)
     G = [tensor(1, 0, 0), tensor(0, 1, 0), tensor(0, 0, 1)]
-    DF = np.stack([np.stack([np.einsum("cbazyx,zyx->cba", G[c], C[..., r]) for c in range(3)], -1)
-                   for r in range(3)], -2)
+    wgt = np.ones((n3, n2, n1)) if weights is None else np.asarray(weights, dtype=np.float64).reshape(n3, n2, n1)
+    Wv = np.einsum("cbazyx,zyx->cba", Bv, wgt)
+    Wd = [np.einsum("cbazyx,zyx->cba", G[c], wgt) for c in range(3)]
+    Nv = [np.einsum("cbazyx,zyx->cba", Bv, wgt * C[..., r]) for r in range(3)]
+    # DF_rc = (d_c N_r - F_r d_c W) / W with F = N / W (quotient rule)
+    DF = np.stack([np.stack([(np.einsum("cbazyx,zyx->cba", G[c], wgt * C[..., r]) - Nv[r] / Wv * Wd[c]) / Wv
+                             for c in range(3)], -1) for r in range(3)], -2)
     det = np.linalg.det(DF)
     Jinv = np.linalg.inv(DF)
-    P = np.einsum("...ik,...jk->...ij", Jinv, Jinv) * det[..., None, None]
+    Km = np.eye(3) if K is None else np.asarray(K, dtype=np.float64)
+    P = np.einsum("...ia,ab,...jb->...ij", Jinv, Km, Jinv) * det[..., None, None]
     w3 = np.einsum("c,b,a->cba", gw[2], gw[1], gw[0])
     if kappa_fn is not None:
         w3 = w3 * kappa_fn(gx)
     N = n1 * n2 * n3
     Bf = Bv.reshape(w3.shape + (N,))
     Gf = [g.reshape(w3.shape + (N,)) for g in G]
-    M = np.einsum("cba,cbai,cbaj->ij", w3 * det, Bf, Bf)
+    if nurbs_basis:
+        Rf = Bf * wgt.reshape(N)[None, None, None, :] / Wv[..., None]
+        M = np.einsum("cba,cbai,cbaj->ij", w3 * det, Rf, Rf)
+    else:
+        M = np.einsum("cba,cbai,cbaj->ij", w3 * det, Bf, Bf)
     S = np.zeros((N, N))
     for l in range(3):
         for m in range(3):

@@ -92,4 +92,7 @@ def rows_c(orc, rows, which: str, threads: int = 1) -> list:
         bounds = np.linspace(0, len(rows), threads * 4 + 1).astype(int)
         with ThreadPoolExecutor(max_workers=threads) as ex:
             list(ex.map(lambda k: run(bounds[k], bounds[k + 1]), range(len(bounds) - 1)))
-    return [out[offs[k]:offs[k + 1]] for k in range(len(rows))]
+    res = [out[offs[k]:offs[k + 1]] for k in range(len(rows))]
+    if getattr(orc, "nurbs_basis", False):
+        res = [v * orc.basis_scale(int(r), which) for r, v in zip(rows, res)]
+    return res

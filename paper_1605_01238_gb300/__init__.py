@@ -15,12 +15,12 @@ import numpy as np
 
 from ._lib import ALLOC_FN, FREE_FN, Options, WqError, check, load
 
-__all__ = ["Plan", "Batch", "bilinear", "WqError", "launch_count", "load", "TorchAllocator", "VALUES_F64",
+__all__ = ["Plan", "Batch", "bilinear", "WqError", "launch_count", "load", "TorchAllocator", "HostBuffer", "VALUES_F64",
            "VALUES_F32", "PREC_FP64", "PREC_FP32"]
 
 VALUES_F64, VALUES_F32 = 0, 1
-PREC_FP64, PREC_FP32, PREC_MIXED, PREC_F32X2 = 0, 1, 2, 3
-_PREC = {"fp64": PREC_FP64, "fp32": PREC_FP32, "mixed": PREC_MIXED, "f32x2": PREC_F32X2}
+PREC_FP64, PREC_FP32, PREC_MIXED, PREC_F32X2, PREC_TF32X3 = 0, 1, 2, 3, 4
+_PREC = {"fp64": PREC_FP64, "fp32": PREC_FP32, "mixed": PREC_MIXED, "f32x2": PREC_F32X2, "tf32x3": PREC_TF32X3}
 _ALGO = {"fused": 0, "staged": 1, "auto": 2}
 
 
@@ -52,6 +52,31 @@ class _DeviceView:
         self._owner = owner
         self.__cuda_array_interface__ = {"shape": shape, "typestr": typestr, "data": (ptr, False),
                                          "version": 3, "strides": None}
+
+
+class HostBuffer:
+    """Page-locked host memory of exactly `count` elements of `dtype` (wq_host_alloc),
+    viewed as a numpy array (`.array`); released by close() or when collected."""
+
+    def __init__(self, count: int, dtype=np.float64):
+        self.dtype = np.dtype(dtype)
+        ptr = ctypes.c_void_p()
+        check(load().wq_host_alloc(int(count) * self.dtype.itemsize, ctypes.byref(ptr)))
+        self._ptr = ptr
+        buf = (ctypes.c_char * (int(count) * self.dtype.itemsize)).from_address(ptr.value)
+        self.array = np.frombuffer(buf, dtype=self.dtype, count=int(count))
+
+    def close(self) -> None:
+        if getattr(self, "_ptr", None) is not None and self._ptr.value:
+            self.array = None
+            load().wq_host_free(self._ptr)
+            self._ptr = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def launch_count() -> int:
@@ -94,13 +119,14 @@ class Plan:
     control points with direction 1 fastest. Options (wq_options): algorithm
     ("auto", "staged", "fused"), precision and dtype (the defaults of the
     assembly calls), tiles ((t1, t2) of the fused kernel), checked (range-checked
-    buffers and finite values, synchronising), tune_cache (a "p t1 t2" text file)
-    and allocator (a TorchAllocator, or any object with alloc_fn / free_fn
-    ctypes callbacks; None = cudaMalloc).
+    buffers and finite values, synchronising), tune_cache (a "p t1 t2" text file),
+    allocator (a TorchAllocator, or any object with alloc_fn / free_fn ctypes
+    callbacks; None = cudaMalloc) and scratch_limit (bytes of staged scratch held
+    at once; 0 = the whole mesh).
     """
 
     def __init__(self, p: int, knots, ctrl, stream=None, *, algorithm=None, precision=None, dtype=None,
-                 tiles=None, checked: bool = False, tune_cache=None, allocator=None):
+                 tiles=None, checked: bool = False, tune_cache=None, allocator=None, scratch_limit: int = 0):
         lib = load()
         self._knots = [np.ascontiguousarray(k, dtype=np.float64) for k in knots]
         if len(self._knots) != 3:
@@ -119,6 +145,7 @@ class Plan:
         if tiles is not None:
             opt.tile[0], opt.tile[1] = int(tiles[0]), int(tiles[1])
         opt.checked = 1 if checked else 0
+        opt.scratch_limit = int(scratch_limit)
         if tune_cache is not None:
             opt.tune_cache = str(tune_cache).encode()
         self._allocator = allocator
@@ -187,6 +214,33 @@ class Plan:
             self._host_ctrl = arr
             ptr, on_dev = arr.ctypes.data, 0
         check(load().wq_plan_set_geometry(self._h, ctypes.c_void_p(ptr), on_dev, _stream(stream)))
+
+    def set_weights(self, weights=None, nurbs_basis: bool = False, stream=None) -> None:
+        """NURBS weights of the control points (wq_plan_set_weights): a rational map
+        F = sum w C B / sum w B; nurbs_basis=True also makes the basis functions NURBS
+        (mass matrix only). weights: (N_DOF,) host array or CUDA float64 tensor, or None."""
+        torch = _torch()
+        ptr, on_dev = None, 0
+        if weights is not None:
+            if isinstance(weights, torch.Tensor) and weights.is_cuda:
+                ptr, on_dev = _dev_ptr(weights, torch.float64, self.n_rows, "weights"), 1
+            else:
+                arr = np.ascontiguousarray(weights, dtype=np.float64).reshape(-1)
+                if arr.size != self.n_rows:
+                    raise ValueError("weights must hold N_DOF values")
+                self._host_w = arr
+                ptr = arr.ctypes.data
+        check(load().wq_plan_set_weights(self._h, ctypes.c_void_p(ptr), on_dev, 1 if nurbs_basis else 0,
+                                         _stream(stream)))
+
+    def set_tensor(self, K=None, stream=None) -> None:
+        """Coefficient tensor field (wq_plan_set_tensor): CUDA float64 (6, N_QP) tensor
+        of K11 K12 K13 K22 K23 K33 at the points (q1 fastest), or None for K = I."""
+        torch = _torch()
+        ptr = None
+        if K is not None:
+            ptr = _dev_ptr(K, torch.float64, 6 * int(np.prod(self.n_qp)), "K")
+        check(load().wq_plan_set_tensor(self._h, ctypes.c_void_p(ptr), _stream(stream)))
 
     def refresh(self, ctrl=None, stream=None) -> None:
         """Re-run every set-up kernel in place (optionally with new control points)."""

@@ -22,7 +22,7 @@ class Options(ctypes.Structure):
     """struct wq_options of include/wq.h."""
     _fields_ = [("size", ctypes.c_size_t), ("value_dtype", c_int), ("precision", c_int), ("algorithm", c_int),
                 ("tile", c_int * 2), ("checked", c_int), ("tune_cache", ctypes.c_char_p),
-                ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_ctx", c_vp)]
+                ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_ctx", c_vp), ("scratch_limit", ctypes.c_size_t)]
 
 # name -> (restype, argtypes)
 SIGNATURES = {
@@ -37,9 +37,13 @@ SIGNATURES = {
     "wq_plan_pattern": (c_int, [c_vp, ctypes.POINTER(c_vp), ctypes.POINTER(c_vp)]),
     "wq_plan_set_geometry": (c_int, [c_vp, c_vp, c_int, c_vp]),
     "wq_plan_refresh": (c_int, [c_vp, c_vp, c_int, c_vp]),
+    "wq_plan_set_weights": (c_int, [c_vp, c_vp, c_int, c_int, c_vp]),
+    "wq_plan_set_tensor": (c_int, [c_vp, c_vp, c_vp]),
     "wq_assemble_stiffness": (c_int, [c_vp, c_vp, c_vp, c_int, c_int, c_vp]),
     "wq_assemble_mass": (c_int, [c_vp, c_vp, c_vp, c_int, c_int, c_vp]),
     "wq_assemble_host": (c_int, [c_vp, c_int, c_vp, c_vp, c_vp, c_vp]),
+    "wq_host_alloc": (c_int, [ctypes.c_size_t, ctypes.POINTER(c_vp)]),
+    "wq_host_free": (c_int, [c_vp]),
     "wq_sync_check": (c_int, [c_vp, c_vp]),
     "wq_last_error": (ctypes.c_char_p, []),
     "wq_status_string": (ctypes.c_char_p, [c_int]),

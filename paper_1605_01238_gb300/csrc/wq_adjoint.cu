@@ -219,6 +219,8 @@ extern "C" wq_status wq_adjoint(wq_plan_t plan, int which, const double* d_kappa
                                 const double* d_u, double* h_J, double* d_grad_kappa, double* d_grad_ctrl,
                                 void* stream) {
   if (!plan || !d_lambda || !d_u || which < 1 || which > 3) return set_error(WQ_ERR_INVALID_ARG, "bad argument");
+  if (plan->wts || plan->Kt)
+    return set_error(WQ_ERR_UNSUPPORTED, "the adjoint handles spline maps with a scalar coefficient only");
   cudaStream_t s = (cudaStream_t)stream;
   wq_plan_s* pl = plan;
   const int p = pl->p, m = p + 1, NQ = pl->nq_max;

@@ -603,6 +603,17 @@ wq_status launch_assemble_f32(wq_plan_s* pl, bool mass, const double* kappa, voi
 
 namespace wq {
 
+// NURBS basis functions: value (i, j) times w_i w_j; one warp per row.
+template <typename T>
+__global__ void k_scale_rows_cols(T* __restrict__ v, const int64_t* __restrict__ row_ptr,
+                                  const int32_t* __restrict__ col, const double* __restrict__ w, int64_t n_rows) {
+  const int64_t r = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / 32;
+  const int lane = threadIdx.x & 31;
+  if (r >= n_rows) return;
+  const double wr = w[r];
+  for (int64_t k = row_ptr[r] + lane; k < row_ptr[r + 1]; k += 32) v[k] = (T)((double)v[k] * (wr * w[col[k]]));
+}
+
 // Checked mode: flags a NaN or infinite value in the error word.
 template <typename T>
 __global__ void k_check_finite(const T* __restrict__ v, int64_t n, int* err) {
@@ -628,23 +639,37 @@ static wq_status assemble(wq_plan_t plan, bool mass, const double* kappa, void* 
   cudaStream_t s = (cudaStream_t)stream;
   if (precision == WQ_PREC_FP64 && value_dtype != WQ_VALUES_F64)
     return set_error(WQ_ERR_INVALID_ARG, "FP64 contractions write FP64 values");
-  if (precision < WQ_PREC_FP64 || precision > WQ_PREC_F32X2) return set_error(WQ_ERR_UNSUPPORTED, "unknown precision");
+  if (precision < WQ_PREC_FP64 || precision > WQ_PREC_TF32X3) return set_error(WQ_ERR_UNSUPPORTED, "unknown precision");
   const size_t vbytes = (value_dtype == WQ_VALUES_F64 ? sizeof(double) : sizeof(float)) * (size_t)plan->nnz;
   if (plan->opt.checked) {
     wq_status st = wq::check_device_range(plan, vals, vbytes, "d_vals");
     if (st == WQ_OK && kappa) st = wq::check_device_range(plan, kappa, sizeof(double) * plan->n_qp_total, "d_kappa");
     if (st != WQ_OK) return st;
   }
+  if (plan->nurbs_basis && !mass)
+    return set_error(WQ_ERR_UNSUPPORTED, "the stiffness matrix with NURBS basis functions is not provided");
   const bool staged = plan->algorithm == WQ_ALGO_STAGED || plan->algorithm == WQ_ALGO_AUTO;
   wq_status st;
-  if (precision == WQ_PREC_MIXED || precision == WQ_PREC_F32X2 ||
+  if (precision == WQ_PREC_MIXED || precision == WQ_PREC_F32X2 || precision == WQ_PREC_TF32X3 ||
       ((precision == WQ_PREC_FP64 || precision == WQ_PREC_FP32) && staged))
     st = wq::launch_staged(plan, mass, kappa, vals, value_dtype, precision, s);
   else if (precision == WQ_PREC_FP64)
     st = wq::launch_assemble_f64(plan, mass, kappa, (double*)vals, s);
   else
     st = wq::launch_assemble_f32(plan, mass, kappa, vals, value_dtype, s);
-  if (st != WQ_OK || !plan->opt.checked) return st;
+  if (st != WQ_OK) return st;
+  if (plan->nurbs_basis) {
+    const unsigned blocks = (unsigned)((plan->n_rows * 32 + 255) / 256);
+    if (value_dtype == WQ_VALUES_F64)
+      wq::k_scale_rows_cols<double><<<blocks, 256, 0, s>>>((double*)vals, plan->row_ptr, plan->col, plan->wts,
+                                                             plan->n_rows);
+    else
+      wq::k_scale_rows_cols<float><<<blocks, 256, 0, s>>>((float*)vals, plan->row_ptr, plan->col, plan->wts,
+                                                            plan->n_rows);
+    wq::count_launch();
+    WQ_CUDA_TRY(cudaGetLastError(), "NURBS basis scaling launch");
+  }
+  if (!plan->opt.checked) return WQ_OK;
   if (value_dtype == WQ_VALUES_F64)
     wq::k_check_finite<double><<<304, 256, 0, s>>>((const double*)vals, plan->nnz, plan->err);
   else
@@ -660,13 +685,13 @@ extern "C" wq_status wq_plan_reserve(wq_plan_t plan, int precision, int value_dt
   if (precision == WQ_PREC_DEFAULT) precision = plan->opt.precision;
   if (value_dtype != WQ_VALUES_F64 && value_dtype != WQ_VALUES_F32)
     return set_error(WQ_ERR_INVALID_ARG, "unknown value dtype");
-  if (precision < WQ_PREC_FP64 || precision > WQ_PREC_F32X2) return set_error(WQ_ERR_UNSUPPORTED, "unknown precision");
+  if (precision < WQ_PREC_FP64 || precision > WQ_PREC_TF32X3) return set_error(WQ_ERR_UNSUPPORTED, "unknown precision");
   if (precision == WQ_PREC_FP64 && value_dtype != WQ_VALUES_F64)
     return set_error(WQ_ERR_INVALID_ARG, "FP64 contractions write FP64 values");
   cudaStream_t s = (cudaStream_t)stream;
   const bool staged = plan->algorithm == WQ_ALGO_STAGED || plan->algorithm == WQ_ALGO_AUTO;
   wq_status st = WQ_OK;
-  if (staged || precision == WQ_PREC_MIXED || precision == WQ_PREC_F32X2)
+  if (staged || precision == WQ_PREC_MIXED || precision == WQ_PREC_F32X2 || precision == WQ_PREC_TF32X3)
     st = wq::launch_staged(plan, false, nullptr, nullptr, value_dtype, precision, s);
   if (st == WQ_OK && adjoint) st = wq::reserve_adjoint(plan, s);
   return st;
@@ -706,16 +731,80 @@ extern "C" wq_status wq_assemble_mass(wq_plan_t plan, const double* d_kappa, voi
   return assemble(plan, true, d_kappa, d_vals, value_dtype, precision, stream);
 }
 
+namespace {
+
+// Copies the values of one slab of direction 3 back to the host on the plan's copy
+// stream, after the assembly stream has reached the end of the slab's kernels.
+struct HostCopy {
+  wq_plan_s* pl;
+  const double* d_vals;
+  double* h_vals;
+  std::vector<int64_t> P3;  // prefix sums of the band widths of direction 3
+};
+
+wq_status copy_slab(void* ctx, int i3a, int i3b, cudaStream_t s) {
+  HostCopy* c = static_cast<HostCopy*>(ctx);
+  const int64_t per = c->pl->nnz1[0] * c->pl->nnz1[1];  // values per band pair of direction 3
+  const int64_t a = c->P3[i3a] * per, b = c->P3[i3b] * per;
+  WQ_CUDA_TRY(cudaEventRecord(c->pl->slab_done, s), "slab event");
+  WQ_CUDA_TRY(cudaStreamWaitEvent(c->pl->copy_stream, c->pl->slab_done, 0), "slab wait");
+  WQ_CUDA_TRY(cudaMemcpyAsync(c->h_vals + a, c->d_vals + a, sizeof(double) * (size_t)(b - a), cudaMemcpyDeviceToHost,
+                              c->pl->copy_stream),
+              "value copy");
+  return WQ_OK;
+}
+
+}  // namespace
+
 extern "C" wq_status wq_assemble_host(wq_plan_t plan, int which, const double* h_ctrl, double* d_vals, double* h_vals,
                                       void* stream) {
   if (!plan || !d_vals || !h_vals || (which != 0 && which != 1)) return set_error(WQ_ERR_INVALID_ARG, "bad argument");
   cudaStream_t s = (cudaStream_t)stream;
   wq_status st = wq_plan_refresh(plan, h_ctrl, 0, stream);
   if (st != WQ_OK) return st;
-  st = assemble(plan, which == 1, nullptr, d_vals, WQ_VALUES_F64, WQ_PREC_FP64, stream);
+  const bool staged = plan->algorithm == WQ_ALGO_STAGED || plan->algorithm == WQ_ALGO_AUTO;
+  if (!staged || plan->opt.checked || plan->nurbs_basis) {
+    st = assemble(plan, which == 1, nullptr, d_vals, WQ_VALUES_F64, WQ_PREC_FP64, stream);
+    if (st != WQ_OK) return st;
+    WQ_CUDA_TRY(cudaMemcpyAsync(h_vals, d_vals, sizeof(double) * plan->nnz, cudaMemcpyDeviceToHost, s), "value copy");
+    WQ_CUDA_TRY(cudaStreamSynchronize(s), "stream synchronize");
+    return WQ_OK;
+  }
+  if (!plan->copy_stream) {
+    WQ_CUDA_TRY(cudaStreamCreateWithFlags(&plan->copy_stream, cudaStreamNonBlocking), "copy stream");
+    WQ_CUDA_TRY(cudaEventCreateWithFlags(&plan->slab_done, cudaEventDisableTiming), "slab event");
+  }
+  HostCopy c{plan, d_vals, h_vals, std::vector<int64_t>(plan->n[2] + 1, 0)};
+  const int n3 = (int)plan->n[2], p = plan->p;
+  for (int i = 0; i < n3; ++i) c.P3[i + 1] = c.P3[i] + (std::min(n3 - 1, i + p) - std::max(0, i - p) + 1);
+  wq::SlabHook hook;
+  hook.rows = std::max(1, (n3 + 7) / 8);  // about eight slabs: the copies overlap all but the last one
+  hook.after = copy_slab;
+  hook.ctx = &c;
+  st = wq::launch_staged(plan, which == 1, nullptr, d_vals, WQ_VALUES_F64, WQ_PREC_FP64, s, &hook);
+  cudaError_t e1 = cudaStreamSynchronize(s), e2 = cudaStreamSynchronize(plan->copy_stream);
   if (st != WQ_OK) return st;
-  WQ_CUDA_TRY(cudaMemcpyAsync(h_vals, d_vals, sizeof(double) * plan->nnz, cudaMemcpyDeviceToHost, s), "value copy");
-  WQ_CUDA_TRY(cudaStreamSynchronize(s), "stream synchronize");
+  WQ_CUDA_TRY(e1, "stream synchronize");
+  WQ_CUDA_TRY(e2, "copy stream synchronize");
+  return WQ_OK;
+}
+
+extern "C" wq_status wq_host_alloc(size_t bytes, void** h_ptr) {
+  if (!h_ptr) return set_error(WQ_ERR_INVALID_ARG, "NULL argument");
+  *h_ptr = nullptr;
+  if (wq::fault("alloc")) return set_error(WQ_ERR_INJECTED, "injected allocation failure: page-locked host memory");
+  cudaError_t e = cudaHostAlloc(h_ptr, bytes ? bytes : 16, cudaHostAllocDefault);
+  if (e == cudaErrorMemoryAllocation) {
+    cudaGetLastError();
+    *h_ptr = nullptr;
+    return set_error(WQ_ERR_OOM, "page-locked host allocation failed");
+  }
+  WQ_CUDA_TRY(e, "page-locked host allocation");
+  return WQ_OK;
+}
+
+extern "C" wq_status wq_host_free(void* h_ptr) {
+  if (h_ptr) WQ_CUDA_TRY(cudaFreeHost(h_ptr), "page-locked host free");
   return WQ_OK;
 }
 
@@ -775,6 +864,7 @@ extern "C" wq_status wq_batch_create(wq_batch_t* out, int count, const wq_plan_t
   for (int k = 0; k < count; ++k) {
     wq_plan_s* pl = plans[k];
     if (!pl) return set_error(WQ_ERR_INVALID_ARG, "NULL plan in batch");
+    if (pl->nurbs_basis) return set_error(WQ_ERR_UNSUPPORTED, "NURBS basis functions are not batched");
     for (int mass = 0; mass < 2; ++mass) {
       void* vals = mass ? (d_mass ? d_mass[k] : nullptr) : (d_stiffness ? d_stiffness[k] : nullptr);
       if (!vals) continue;

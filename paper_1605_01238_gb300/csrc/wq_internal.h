@@ -143,8 +143,16 @@ struct wq_plan_s {
   void* stg_a = nullptr;          // staged: T3
   void* stg_b = nullptr;          // staged: G
   void* stg_c = nullptr;          // staged, mixed precision: FP64 edge copy of G
-  size_t stg_a_bytes = 0, stg_b_bytes = 0, stg_c_bytes = 0;
+  void* stg_d = nullptr;          // staged, tensor-core stage 1: B fragments of the regular rows
+  size_t stg_a_bytes = 0, stg_b_bytes = 0, stg_c_bytes = 0, stg_d_bytes = 0;
   wq_options opt{};               // options given at creation (defaults filled in)
+  double* wts = nullptr;          // NULL (spline map), or [N] NURBS weights of the control points
+  int nurbs_basis = 0;            // 1: NURBS basis functions (mass only)
+  double* Kt = nullptr;           // NULL (identity), or [6][N_QP] coefficient tensor
+  cudaStream_t copy_stream = nullptr;  // end-to-end call: copies back slab by slab
+  cudaEvent_t slab_done = nullptr;
+  cudaStream_t side_stream = nullptr;  // tensor-core stage 1: the edge rows run beside it
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 };
 
 namespace wq {
@@ -176,9 +184,19 @@ wq_status launch_assemble_f64(wq_plan_s* pl, bool mass, const double* kappa, dou
 wq_status launch_assemble_f32(wq_plan_s* pl, bool mass, const double* kappa, void* vals,
                               int value_dtype, cudaStream_t s);
 // Staged assembly (wq_staged.cu: dispatch on the degree; kernels in wq_staged_impl.cuh).
+// Slabs of direction 3 for the staged assembly: `rows` rows i3 per slab (0 = as few
+// slabs as the plan's scratch limit allows) and, if given, a callback run after the
+// kernels of each slab [i3a, i3b) are enqueued (the values of rows with i3 in the
+// slab are then final on `s` once the stream gets there).
+struct SlabHook {
+  int rows = 0;
+  wq_status (*after)(void* ctx, int i3a, int i3b, cudaStream_t s) = nullptr;
+  void* ctx = nullptr;
+};
+
 // vals = NULL: allocate the mode's scratch only (wq_plan_reserve).
 wq_status launch_staged(wq_plan_s* pl, bool mass, const double* kappa, void* vals, int value_dtype, int precision,
-                        cudaStream_t s);
+                        cudaStream_t s, const SlabHook* hook = nullptr);
 // Adjoint fields (wq_adjoint.cu).
 wq_status reserve_adjoint(wq_plan_s* pl, cudaStream_t s);
 

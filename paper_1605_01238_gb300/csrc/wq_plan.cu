@@ -529,14 +529,60 @@ constexpr int kCoefTQ1 = 32, kCoefTQ2 = 8;
 struct CoefArgs {
   int p;
   int n1, n2, n3, nq1, nq2, nq3;
-  const double* ctrl;   // C_i - g_i (see k_delta)
+  const double* ctrl;   // C_i - g_i (see k_delta); the control points C_i for a rational map
   const double *bp1, *bp2, *bp3;
   const int *f1, *f2, *f3;
   double* coef;
   double* jac;  // NULL, or [9][N_QP]: DF_{rc} at (3r + c)
   int64_t nqp_total;
   int* err;
+  const double* K;        // NULL (identity), or [6][N_QP]: K11 K12 K13 K22 K23 K33 at the points
+  const double* weights;  // rational map only: w_i [N_DOF]
+  int nurbs_basis;        // rational map only: c = det DF / W^2 (NURBS basis functions)
 };
+
+// From DF at point qg: c_lm = det DF (DF^{-1} K DF^{-T})_lm = (adj K adj^T)_lm / det DF
+// (Eq. (coef_stiff) with the coefficient tensor K, the identity when a.K is NULL),
+// and c = det DF * mass_scale (Eq. (mass2)).
+__device__ void write_coefficients(const CoefArgs& a, const double (&F)[3][3], int64_t qg, double mass_scale) {
+  if (a.jac)
+    for (int r = 0; r < 3; ++r)
+      for (int c = 0; c < 3; ++c) a.jac[(3 * r + c) * a.nqp_total + qg] = F[r][c];
+  // adj = det * DF^{-1}: adj[l][k] = cofactor[k][l]
+  double adj[3][3];
+  adj[0][0] = F[1][1] * F[2][2] - F[1][2] * F[2][1];
+  adj[0][1] = F[0][2] * F[2][1] - F[0][1] * F[2][2];
+  adj[0][2] = F[0][1] * F[1][2] - F[0][2] * F[1][1];
+  adj[1][0] = F[1][2] * F[2][0] - F[1][0] * F[2][2];
+  adj[1][1] = F[0][0] * F[2][2] - F[0][2] * F[2][0];
+  adj[1][2] = F[0][2] * F[1][0] - F[0][0] * F[1][2];
+  adj[2][0] = F[1][0] * F[2][1] - F[1][1] * F[2][0];
+  adj[2][1] = F[0][1] * F[2][0] - F[0][0] * F[2][1];
+  adj[2][2] = F[0][0] * F[1][1] - F[0][1] * F[1][0];
+  double det = F[0][0] * adj[0][0] + F[0][1] * adj[1][0] + F[0][2] * adj[2][0];
+  if (!(det > 0.0) || !isfinite(det)) atomicOr(a.err, kErrBadGeometry);
+  double inv = 1.0 / det;
+  const int L[6] = {0, 0, 0, 1, 1, 2}, Mi[6] = {0, 1, 2, 1, 2, 2};
+  if (a.K) {
+    double Km[3][3];
+    for (int s = 0; s < 6; ++s) Km[L[s]][Mi[s]] = Km[Mi[s]][L[s]] = a.K[(int64_t)s * a.nqp_total + qg];
+    double AK[3][3];  // adj K
+    for (int l = 0; l < 3; ++l)
+      for (int b = 0; b < 3; ++b) AK[l][b] = adj[l][0] * Km[0][b] + adj[l][1] * Km[1][b] + adj[l][2] * Km[2][b];
+    for (int s = 0; s < 6; ++s) {
+      int l = L[s], mm = Mi[s];
+      double v = AK[l][0] * adj[mm][0] + AK[l][1] * adj[mm][1] + AK[l][2] * adj[mm][2];
+      a.coef[(int64_t)s * a.nqp_total + qg] = v * inv;
+    }
+  } else {
+    for (int s = 0; s < 6; ++s) {
+      int l = L[s], mm = Mi[s];
+      double v = adj[l][0] * adj[mm][0] + adj[l][1] * adj[mm][1] + adj[l][2] * adj[mm][2];
+      a.coef[(int64_t)s * a.nqp_total + qg] = v * inv;
+    }
+  }
+  a.coef[6 * a.nqp_total + qg] = det * mass_scale;
+}
 
 __global__ void k_coef(CoefArgs a) {
   extern __shared__ double sm[];
@@ -596,31 +642,90 @@ __global__ void k_coef(CoefArgs a) {
         F[rr][c] = acc + (rr == c ? 1.0 : 0.0);  // dF_r / dzeta_c
       }
     }
-    const int64_t qg = ((int64_t)q3 * a.nq2 + q2) * a.nq1 + q1;
-    if (a.jac)
-      for (int r = 0; r < 3; ++r)
-        for (int c = 0; c < 3; ++c) a.jac[(3 * r + c) * a.nqp_total + qg] = F[r][c];
-    // adj = det * DF^{-1}: adj[l][k] = cofactor[k][l]
-    double adj[3][3];
-    adj[0][0] = F[1][1] * F[2][2] - F[1][2] * F[2][1];
-    adj[0][1] = F[0][2] * F[2][1] - F[0][1] * F[2][2];
-    adj[0][2] = F[0][1] * F[1][2] - F[0][2] * F[1][1];
-    adj[1][0] = F[1][2] * F[2][0] - F[1][0] * F[2][2];
-    adj[1][1] = F[0][0] * F[2][2] - F[0][2] * F[2][0];
-    adj[1][2] = F[0][2] * F[1][0] - F[0][0] * F[1][2];
-    adj[2][0] = F[1][0] * F[2][1] - F[1][1] * F[2][0];
-    adj[2][1] = F[0][1] * F[2][0] - F[0][0] * F[2][1];
-    adj[2][2] = F[0][0] * F[1][1] - F[0][1] * F[1][0];
-    double det = F[0][0] * adj[0][0] + F[0][1] * adj[1][0] + F[0][2] * adj[2][0];
-    if (!(det > 0.0) || !isfinite(det)) atomicOr(a.err, kErrBadGeometry);
-    double inv = 1.0 / det;
-    const int L[6] = {0, 0, 0, 1, 1, 2}, Mi[6] = {0, 1, 2, 1, 2, 2};
-    for (int s = 0; s < 6; ++s) {
-      int l = L[s], mm = Mi[s];
-      double v = adj[l][0] * adj[mm][0] + adj[l][1] * adj[mm][1] + adj[l][2] * adj[mm][2];
-      a.coef[(int64_t)s * a.nqp_total + qg] = v * inv;
-    }
-    a.coef[6 * a.nqp_total + qg] = det;
+    write_coefficients(a, F, ((int64_t)q3 * a.nq2 + q2) * a.nq1 + q1, 1.0);
+  }
+}
+
+// Coefficients of a rational (NURBS) map F = sum_i w_i C_i B_i / W, W = sum_i w_i B_i.
+// Point by point over the (p+1)^3 functions active there (one block per (q3, tile
+// of TQ2 q2, tile of TQ1 q1), the tile's control points and weights in shared
+// memory): F first, then DF = sum_i w_i (C_i - F) x grad B_i / W (the quotient rule
+// with sum_i w_i grad B_i = grad W), so the O(1/h) gradients multiply the small
+// differences C_i - F and do not cancel in the sum. With NURBS basis functions
+// (w_i B_i / W) the mass coefficient is det DF / W^2 (the denominator folded into c).
+__global__ void k_coef_rational(CoefArgs a) {
+  extern __shared__ double sm[];
+  const int p = a.p, m = p + 1;
+  const int nt1 = (a.nq1 + kCoefTQ1 - 1) / kCoefTQ1;
+  int bid = blockIdx.x;
+  const int tq1 = bid % nt1;
+  bid /= nt1;
+  const int nt2 = (a.nq2 + kCoefTQ2 - 1) / kCoefTQ2;
+  const int tq2 = bid % nt2;
+  const int q3 = bid / nt2;
+  const int qa1 = tq1 * kCoefTQ1, qb1 = min(a.nq1, qa1 + kCoefTQ1);
+  const int qa2 = tq2 * kCoefTQ2, qb2 = min(a.nq2, qa2 + kCoefTQ2);
+  const int ia1 = a.f1[qa1], ib1 = a.f1[qb1 - 1] + p + 1;
+  const int ia2 = a.f2[qa2], ib2 = a.f2[qb2 - 1] + p + 1;
+  const int W1 = ib1 - ia1, W2 = ib2 - ia2;
+  const int f3 = a.f3[q3];
+  double* Cs = sm;  // [m][W2][W1][4]: C_x C_y C_z w
+  for (int e = threadIdx.x; e < m * W2 * W1; e += blockDim.x) {
+    const int i1 = e % W1, i2 = (e / W1) % W2, t3 = e / (W1 * W2);
+    const int64_t idx = ((int64_t)(f3 + t3) * a.n2 + (ia2 + i2)) * a.n1 + (ia1 + i1);
+    double* c = Cs + (size_t)e * 4;
+    c[0] = a.ctrl[idx * 3];
+    c[1] = a.ctrl[idx * 3 + 1];
+    c[2] = a.ctrl[idx * 3 + 2];
+    c[3] = a.weights[idx];
+  }
+  __syncthreads();
+  const int nq1t = qb1 - qa1, nq2t = qb2 - qa2;
+  for (int e = threadIdx.x; e < nq2t * nq1t; e += blockDim.x) {
+    const int q1 = qa1 + e % nq1t, q2 = qa2 + e / nq1t;
+    const int o1 = a.f1[q1] - ia1, o2 = a.f2[q2] - ia2;
+    const double* b1 = a.bp1 + (int64_t)q1 * m;
+    const double* d1 = a.bp1 + ((int64_t)a.nq1 + q1) * m;
+    const double* b2 = a.bp2 + (int64_t)q2 * m;
+    const double* d2 = a.bp2 + ((int64_t)a.nq2 + q2) * m;
+    const double* b3 = a.bp3 + (int64_t)q3 * m;
+    const double* d3 = a.bp3 + ((int64_t)a.nq3 + q3) * m;
+    double W = 0.0, N[3] = {0.0, 0.0, 0.0};
+    for (int t3 = 0; t3 < m; ++t3)
+      for (int t2 = 0; t2 < m; ++t2) {
+        const double* row = Cs + ((size_t)(t3 * W2 + o2 + t2) * W1 + o1) * 4;
+        const double b23 = b3[t3] * b2[t2];
+        for (int t1 = 0; t1 < m; ++t1) {
+          const double* c = row + t1 * 4;
+          const double wb = c[3] * (b23 * b1[t1]);
+          W += wb;
+          N[0] = fma(wb, c[0], N[0]);
+          N[1] = fma(wb, c[1], N[1]);
+          N[2] = fma(wb, c[2], N[2]);
+        }
+      }
+    const double iw = 1.0 / W;
+    const double Fx[3] = {N[0] * iw, N[1] * iw, N[2] * iw};
+    double J[3][3] = {{0.0, 0.0, 0.0}, {0.0, 0.0, 0.0}, {0.0, 0.0, 0.0}};
+    for (int t3 = 0; t3 < m; ++t3)
+      for (int t2 = 0; t2 < m; ++t2) {
+        const double* row = Cs + ((size_t)(t3 * W2 + o2 + t2) * W1 + o1) * 4;
+        for (int t1 = 0; t1 < m; ++t1) {
+          const double* c = row + t1 * 4;
+          const double g[3] = {c[3] * d1[t1] * b2[t2] * b3[t3], c[3] * b1[t1] * d2[t2] * b3[t3],
+                               c[3] * b1[t1] * b2[t2] * d3[t3]};
+          for (int r = 0; r < 3; ++r) {
+            const double dr = c[r] - Fx[r];
+            J[r][0] = fma(g[0], dr, J[r][0]);
+            J[r][1] = fma(g[1], dr, J[r][1]);
+            J[r][2] = fma(g[2], dr, J[r][2]);
+          }
+        }
+      }
+    for (int r = 0; r < 3; ++r)
+      for (int c = 0; c < 3; ++c) J[r][c] *= iw;
+    if (!(W > 0.0) || !isfinite(W)) atomicOr(a.err, kErrBadGeometry);
+    write_coefficients(a, J, ((int64_t)q3 * a.nq2 + q2) * a.nq1 + q1, a.nurbs_basis ? iw * iw : 1.0);
   }
 }
 
@@ -629,8 +734,45 @@ static size_t coef_smem(int p) {
   return sizeof(double) * (size_t)(2 * W2 * W1 * 3 + 3 * kCoefTQ2 * W1 * 3);
 }
 
+static size_t coef_rational_smem(int p) {
+  int W1 = kCoefTQ1 / 2 + p + 2, W2 = kCoefTQ2 / 2 + p + 2;
+  return sizeof(double) * (size_t)(p + 1) * W2 * W1 * 4;
+}
+
 wq_status run_coefficients(wq_plan_s* pl, cudaStream_t s, double* jac) {
   if (fault("geometry")) return set_error(WQ_ERR_INJECTED, "injected failure at the coefficient step");
+  if (pl->wts) {
+    CoefArgs a{};
+    a.p = pl->p;
+    a.n1 = (int)pl->n[0];
+    a.n2 = (int)pl->n[1];
+    a.n3 = (int)pl->n[2];
+    a.nq1 = (int)pl->nqp[0];
+    a.nq2 = (int)pl->nqp[1];
+    a.nq3 = (int)pl->nqp[2];
+    a.ctrl = pl->ctrl;
+    a.bp1 = pl->dir[0].bp;
+    a.bp2 = pl->dir[1].bp;
+    a.bp3 = pl->dir[2].bp;
+    a.f1 = pl->dir[0].first;
+    a.f2 = pl->dir[1].first;
+    a.f3 = pl->dir[2].first;
+    a.coef = pl->coef;
+    a.jac = jac;
+    a.nqp_total = pl->n_qp_total;
+    a.err = pl->err;
+    a.K = pl->Kt;
+    a.weights = pl->wts;
+    a.nurbs_basis = pl->nurbs_basis;
+    int64_t blocks = (int64_t)((a.nq1 + kCoefTQ1 - 1) / kCoefTQ1) * ((a.nq2 + kCoefTQ2 - 1) / kCoefTQ2) * a.nq3;
+    size_t smem = coef_rational_smem(pl->p);
+    WQ_CUDA_TRY(cudaFuncSetAttribute(k_coef_rational, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
+                "rational coefficient kernel attributes");
+    k_coef_rational<<<(unsigned)blocks, 256, smem, s>>>(a);
+    count_launch();
+    WQ_CUDA_TRY(cudaGetLastError(), "rational coefficient kernel launch");
+    return WQ_OK;
+  }
   DeltaArgs da;
   da.n1 = (int)pl->n[0];
   da.n2 = (int)pl->n[1];
@@ -642,7 +784,7 @@ wq_status run_coefficients(wq_plan_s* pl, cudaStream_t s, double* jac) {
   da.delta = pl->ctrl_delta;
   k_delta<<<(unsigned)((pl->n_rows + 255) / 256), 256, 0, s>>>(da);
   count_launch();
-  CoefArgs a;
+  CoefArgs a{};
   a.p = pl->p;
   a.n1 = (int)pl->n[0];
   a.n2 = (int)pl->n[1];
@@ -661,6 +803,9 @@ wq_status run_coefficients(wq_plan_s* pl, cudaStream_t s, double* jac) {
   a.jac = jac;
   a.nqp_total = pl->n_qp_total;
   a.err = pl->err;
+  a.K = pl->Kt;
+  a.weights = nullptr;
+  a.nurbs_basis = 0;
   int64_t blocks = (int64_t)((a.nq1 + kCoefTQ1 - 1) / kCoefTQ1) * ((a.nq2 + kCoefTQ2 - 1) / kCoefTQ2) * a.nq3;
   size_t smem = coef_smem(pl->p);
   WQ_CUDA_TRY(cudaFuncSetAttribute(k_coef, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
@@ -771,8 +916,13 @@ static void free_plan(wq_plan_s* pl) {
     for (void* q : ptrs) wq::plan_free(pl, q, nullptr);
   }
   void* ptrs[] = {pl->ctrl, pl->ctrl_delta, pl->coef, pl->row_ptr, pl->col, pl->gauss, pl->err, pl->jac,
-                  pl->adj_scratch, pl->coefT, pl->stg_a, pl->stg_b, pl->stg_c};
+                  pl->adj_scratch, pl->coefT, pl->stg_a, pl->stg_b, pl->stg_c, pl->stg_d, pl->wts, pl->Kt};
   for (void* q : ptrs) wq::plan_free(pl, q, nullptr);
+  if (pl->slab_done) cudaEventDestroy(pl->slab_done);
+  if (pl->copy_stream) cudaStreamDestroy(pl->copy_stream);
+  if (pl->ev_fork) cudaEventDestroy(pl->ev_fork);
+  if (pl->ev_join) cudaEventDestroy(pl->ev_join);
+  if (pl->side_stream) cudaStreamDestroy(pl->side_stream);
   delete pl;
 }
 
@@ -914,7 +1064,7 @@ static wq_status validate_options(const wq_options* o) {
     return set_error(WQ_ERR_INVALID_ARG, "wq_options.size does not match this library (call wq_options_init)");
   if (o->value_dtype != WQ_VALUES_F64 && o->value_dtype != WQ_VALUES_F32)
     return set_error(WQ_ERR_INVALID_ARG, "wq_options.value_dtype is not a value type");
-  if (o->precision < WQ_PREC_FP64 || o->precision > WQ_PREC_F32X2)
+  if (o->precision < WQ_PREC_FP64 || o->precision > WQ_PREC_TF32X3)
     return set_error(WQ_ERR_INVALID_ARG, "wq_options.precision is not a precision mode");
   if (o->precision == WQ_PREC_FP64 && o->value_dtype != WQ_VALUES_F64)
     return set_error(WQ_ERR_INVALID_ARG, "FP64 contractions write FP64 values");
@@ -1105,6 +1255,58 @@ extern "C" wq_status wq_plan_refresh(wq_plan_t plan, const double* ctrl, int ctr
   wq_status st = copy_ctrl(plan, ctrl, ctrl_on_device, s);
   if (st != WQ_OK) return st;
   return wq::run_setup(plan, s, true);
+}
+
+extern "C" wq_status wq_plan_set_weights(wq_plan_t plan, const double* w, int on_device, int nurbs_basis,
+                                         void* stream) {
+  if (!plan) return set_error(WQ_ERR_INVALID_ARG, "NULL plan");
+  if (nurbs_basis != 0 && nurbs_basis != 1) return set_error(WQ_ERR_INVALID_ARG, "nurbs_basis must be 0 or 1");
+  if (!w && nurbs_basis) return set_error(WQ_ERR_INVALID_ARG, "NURBS basis functions need weights");
+  cudaStream_t s = (cudaStream_t)stream;
+  if (!w) {
+    wq::plan_free(plan, plan->wts, s);
+    plan->wts = nullptr;
+    plan->nurbs_basis = 0;
+    return wq::run_coefficients(plan, s);
+  }
+  const size_t bytes = sizeof(double) * (size_t)plan->n_rows;
+  if (!on_device) {
+    for (int64_t k = 0; k < plan->n_rows; ++k)
+      if (!(w[k] > 0.0) || !std::isfinite(w[k])) return set_error(WQ_ERR_INVALID_ARG, "weights must be positive");
+    if (wq::fault("h2d")) return set_error(WQ_ERR_INJECTED, "injected failure of the weight copy");
+  } else if (plan->opt.checked) {
+    wq_status st = wq::check_device_range(plan, w, bytes, "weights");
+    if (st != WQ_OK) return st;
+  }
+  if (!plan->wts) {
+    wq_status st = wq::plan_alloc(plan, (void**)&plan->wts, bytes, s, "NURBS weights");
+    if (st != WQ_OK) return st;
+  }
+  WQ_CUDA_TRY(cudaMemcpyAsync(plan->wts, w, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s),
+              "weight copy");
+  plan->nurbs_basis = nurbs_basis;
+  return wq::run_coefficients(plan, s);
+}
+
+extern "C" wq_status wq_plan_set_tensor(wq_plan_t plan, const double* d_K, void* stream) {
+  if (!plan) return set_error(WQ_ERR_INVALID_ARG, "NULL plan");
+  cudaStream_t s = (cudaStream_t)stream;
+  if (!d_K) {
+    wq::plan_free(plan, plan->Kt, s);
+    plan->Kt = nullptr;
+    return wq::run_coefficients(plan, s);
+  }
+  const size_t bytes = sizeof(double) * 6 * (size_t)plan->n_qp_total;
+  if (plan->opt.checked) {
+    wq_status st = wq::check_device_range(plan, d_K, bytes, "d_K");
+    if (st != WQ_OK) return st;
+  }
+  if (!plan->Kt) {
+    wq_status st = wq::plan_alloc(plan, (void**)&plan->Kt, bytes, s, "coefficient tensor");
+    if (st != WQ_OK) return st;
+  }
+  WQ_CUDA_TRY(cudaMemcpyAsync(plan->Kt, d_K, bytes, cudaMemcpyDeviceToDevice, s), "tensor copy");
+  return wq::run_coefficients(plan, s);
 }
 
 extern "C" wq_status wq_sync_check(wq_plan_t plan, void* stream) {

@@ -22,8 +22,13 @@
 // Arithmetic (template parameters Real for K3/K2, R1 for K1):
 //   FP64        double everywhere;
 //   F32X2       f2 (double-float, ~48 bits on the FP32 pipe) everywhere;
-//   MIXED       f2 in K3/K2, float in K1; K1's first and last P+1 rows of direction 1
-//               run in double from an FP64 copy of G that K2 writes for their points;
+//   MIXED       f2 in K3; K2 in f2 for the first and last P+1 rows of direction 2 and
+//               for the points q1 that the first and last P+1 rows of direction 1 read,
+//               float for the rest; float in K1, whose first and last P+1 rows of
+//               direction 1 run in double from an FP64 copy of G that K2 writes for
+//               their points. Near the boundary the WQ weights are large and alternate
+//               in sign, so rounding is amplified only in the stages that contract
+//               over such rows;
 //   FP32        float everywhere.
 #pragma once
 
@@ -157,6 +162,10 @@ template <>
 __device__ __forceinline__ float toOut<float, f2>(f2 x) { return __fadd_rn(x.hi, x.lo); }
 template <>
 __device__ __forceinline__ f2 toOut<f2, f2>(f2 x) { return x; }
+template <>
+__device__ __forceinline__ f2 toOut<f2, float>(float x) { return f2{x, 0.0f}; }
+template <>
+__device__ __forceinline__ f2 toOut<f2, double>(double x) { return f2_from(x); }
 
 // an intermediate stored as S, read into arithmetic type T (double-float T3 read by
 // the FP32 part of stage 2 is rounded to the nearest float)
@@ -201,10 +210,14 @@ struct StagedArgs {
   // Mixed precision only: an FP64 copy of G at the q1 points that the first and
   // last P+1 rows of direction 1 read (q1 < nbl and q1 >= hstart), and the FP64
   // direction-1 tables, so that stage 1 runs those rows in FP64.
-  double* Gb;             // NULL or double [nnz1_3][NG][nbq][nnz1_2]
-  const double* w1d;      // double [4][n1][NQ]
-  const double* bt1d;     // double [2][n1][NQ]
+  void* Gb;               // NULL or [nnz1_3][NG][nbq][nnz1_2] in the edge-row type GE
+  const void* w1e;        // [4][n1][NQ]: direction-1 rules in the edge-row type
+  const void* bt1e;       // [2][n1][NQ]
   int nbl, hstart, nbq;
+  // Slab of direction 3: rows i3 in [i3_off, i3_off + n3 of the launch), band pairs
+  // p3 in [p3_off, ...); T3, G and Gb hold the slab only (index p3 - p3_off).
+  int64_t p3_off;
+  int i3_off;
 };
 
 // position of point q1 in the FP64 edge copy of G (in range for every q1 that a
@@ -268,7 +281,7 @@ __global__ void __launch_bounds__(128) k_stage3(StagedArgs A) {
   constexpr int BW = 2 * P + 1;
   const Dir& D3 = A.d[2];
   const int nq1 = A.d[0].nqp, nq2 = A.d[1].nqp;
-  const int i3 = blockIdx.x;
+  const int i3 = A.i3_off + blockIdx.x;
   const int64_t e = blockIdx.y * (int64_t)blockDim.x + threadIdx.x;  // point index q1 * nq2 + q2
   const int q1 = (int)(e / nq2), q2 = (int)(e % nq2);
   const int NQ = A.NQ;
@@ -301,7 +314,7 @@ __global__ void __launch_bounds__(128) k_stage3(StagedArgs A) {
   if (q1 >= nq1) return;
   const int64_t plane = (int64_t)nq1 * nq2;
   const int64_t pt = (int64_t)q1 * nq2 + q2;
-  const int64_t p3base = D3.prefix[i3];
+  const int64_t p3base = D3.prefix[i3] - A.p3_off;  // slab-relative
   Real* T3 = reinterpret_cast<Real*>(A.T3);
   const int nslots = MASS ? 1 : 6;
   for (int s = 0; s < nslots; ++s) {
@@ -330,7 +343,7 @@ __global__ void __launch_bounds__(128) k_stage3(StagedArgs A) {
 // threads sharing q2 points. Boundary rows [0, r_lo) and [r_hi, n2): threads run
 // over (the row, then q1), so every lane has work and the rows of one side read
 // neighbouring q2 and write neighbouring band pairs.
-template <int P, bool MASS, typename Real, bool REG, typename GOut>
+template <int P, bool MASS, typename Real, bool REG, typename GOut, typename GE = Real>
 __global__ void __launch_bounds__(128) k_stage2(StagedArgs A, int r_lo, int r_hi) {
   constexpr int BW = 2 * P + 1;
   constexpr int NT = MASS ? 1 : 9;
@@ -419,11 +432,11 @@ __global__ void __launch_bounds__(128) k_stage2(StagedArgs A, int r_lo, int r_hi
         if (REG || (j2 >= jlo && j2 <= jhi)) dst[j2 - jlo] = toOut<GOut>(acc[tt]);
       }
       if (sizeof(GOut) < sizeof(Real) && A.Gb && (q1 < A.nbl || q1 >= A.hstart)) {
-        double* dd = A.Gb + ((p3 * NG + g) * A.nbq + edge_row(q1, A.nbl, A.hstart, A.nbq)) * nnz2 + pbase;
+        GE* dd = reinterpret_cast<GE*>(A.Gb) + ((p3 * NG + g) * A.nbq + edge_row(q1, A.nbl, A.hstart, A.nbq)) * nnz2 + pbase;
 #pragma unroll
         for (int tt = 0; tt < BW; ++tt) {
           const int j2 = i2 - P + tt;
-          if (REG || (j2 >= jlo && j2 <= jhi)) dd[j2 - jlo] = toD(acc[tt]);
+          if (REG || (j2 >= jlo && j2 <= jhi)) dd[j2 - jlo] = toOut<GE>(acc[tt]);
         }
       }
     }
@@ -477,7 +490,7 @@ __device__ __forceinline__ void stage1_edge(const T* G, int64_t gstride, int64_t
 // aligned to the regular pattern: Bs[b][j2 - i0 + P][u] is B^(b)_j2 at point 2 j2 - P + u.
 // TIn is the stored type of T3 (the mixed mode runs this kernel in FP32 on double-float
 // T3 for the points q1 that no first or last P+1 row of direction 1 reads).
-template <int P, bool MASS, typename Real, typename GOut, typename TIn = Real>
+template <int P, bool MASS, typename Real, typename GOut, typename TIn = Real, typename GE = Real>
 __global__ void __launch_bounds__(128) k_stage2_reg(StagedArgs A, int r_lo, int r_hi, int q_lo, int q_hi) {
   constexpr int BW = 2 * P + 1;
   constexpr int NT = MASS ? 1 : 9;
@@ -571,9 +584,9 @@ __global__ void __launch_bounds__(128) k_stage2_reg(StagedArgs A, int r_lo, int 
 #pragma unroll
           for (int tt = 0; tt < BW; ++tt) dst[tt] = toOut<GOut>(acc[v][tt]);
           if (sizeof(GOut) < sizeof(Real) && A.Gb && (q1 < A.nbl || q1 >= A.hstart)) {
-            double* dd = A.Gb + ((p3 * NG + g) * A.nbq + edge_row(q1, A.nbl, A.hstart, A.nbq)) * nnz2 + pbase;
+            GE* dd = reinterpret_cast<GE*>(A.Gb) + ((p3 * NG + g) * A.nbq + edge_row(q1, A.nbl, A.hstart, A.nbq)) * nnz2 + pbase;
 #pragma unroll
-            for (int tt = 0; tt < BW; ++tt) dd[tt] = toD(acc[v][tt]);
+            for (int tt = 0; tt < BW; ++tt) dd[tt] = toOut<GE>(acc[v][tt]);
           }
         }
       }
@@ -603,7 +616,7 @@ __host__ __device__ constexpr int e_toff(int P, int R, bool H, int jj) {
 }
 
 // Stage 2 for edge row R of direction 2 (i2 = R or n2-1-R) at point q1 of pair p3.
-template <int P, bool MASS, typename Real, typename GOut, int R, bool H>
+template <int P, bool MASS, typename Real, typename GOut, int R, bool H, typename GE>
 __device__ __forceinline__ void stage2_edge_row(const StagedArgs& A, int q1, int64_t p3) {
   constexpr int NT = MASS ? 1 : 9;
   constexpr int NG = MASS ? 1 : 4;
@@ -655,9 +668,9 @@ __device__ __forceinline__ void stage2_edge_row(const StagedArgs& A, int q1, int
 #pragma unroll
       for (int jj = 0; jj < NJ; ++jj) dst[jj] = toOut<GOut>(acc[jj]);
       if (sizeof(GOut) < sizeof(Real) && A.Gb && (q1 < A.nbl || q1 >= A.hstart)) {
-        double* dd = A.Gb + ((p3 * NG + g) * A.nbq + edge_row(q1, A.nbl, A.hstart, A.nbq)) * nnz2 + pbase;
+        GE* dd = reinterpret_cast<GE*>(A.Gb) + ((p3 * NG + g) * A.nbq + edge_row(q1, A.nbl, A.hstart, A.nbq)) * nnz2 + pbase;
 #pragma unroll
-        for (int jj = 0; jj < NJ; ++jj) dd[jj] = toD(acc[jj]);
+        for (int jj = 0; jj < NJ; ++jj) dd[jj] = toOut<GE>(acc[jj]);
       }
     }
   }
@@ -667,37 +680,40 @@ __device__ __forceinline__ void stage2_edge_row(const StagedArgs& A, int q1, int
 // compile-time point pattern; threads over (p3, q1), so a warp shares one pattern
 // and every lane has work. One instantiation per edge row keeps each row's
 // registers to itself.
-template <int P, bool MASS, typename Real, typename GOut, int R, bool H>
+template <int P, bool MASS, typename Real, typename GOut, int R, bool H, typename GE>
 __global__ void __launch_bounds__(128) k_stage2_edge(StagedArgs A, int64_t np3) {
   const int nq1 = A.d[0].nqp;
   const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;  // p3 * nq1 + q1
   if (e >= np3 * nq1) return;
-  stage2_edge_row<P, MASS, Real, GOut, R, H>(A, (int)(e % nq1), e / nq1);
+  stage2_edge_row<P, MASS, Real, GOut, R, H, GE>(A, (int)(e % nq1), e / nq1);
 }
 
-template <int P, bool MASS, typename Real, typename GOut, int B = 0>
+template <int P, bool MASS, typename Real, typename GOut, typename GE, int B = 0>
 static void launch_stage2_edge(const StagedArgs& A, int nq1, int64_t np3, cudaStream_t s) {
-  k_stage2_edge<P, MASS, Real, GOut, (B <= P ? B : B - P - 1), (B > P)>
+  k_stage2_edge<P, MASS, Real, GOut, (B <= P ? B : B - P - 1), (B > P), GE>
       <<<(unsigned)((np3 * nq1 + 127) / 128), 128, 0, s>>>(A, np3);
-  if constexpr (B + 1 < 2 * P + 2) launch_stage2_edge<P, MASS, Real, GOut, B + 1>(A, nq1, np3, s);
+  if constexpr (B + 1 < 2 * P + 2) launch_stage2_edge<P, MASS, Real, GOut, GE, B + 1>(A, nq1, np3, s);
 }
 
 // K1: one thread per (p2, i1, p3): the 2P+1 values of row (i1, i2, i3) in the
 // column block (j2, j3). A block covers 32 consecutive p2 and 4 consecutive i1, so
 // the G rows of overlapping supports are read from L1.
-// EDGE64: the first and last P+1 rows of direction 1 run in FP64 from the edge
-// copy of G (mixed precision), where the large, sign-alternating WQ weights near
-// the boundary amplify FP32 rounding.
-template <int P, bool MASS, typename Real, typename OutT, bool EDGE64>
-__global__ void __launch_bounds__(128) k_stage1(StagedArgs A) {
+// EDGE64: the first and last P+1 rows of direction 1 run in type RE (FP64, or
+// double-float beside the tensor-core kernel) from the edge copy of G, where the
+// large, sign-alternating WQ weights near the boundary amplify FP32 rounding.
+// Rows [gap_lo, gap_lo + gap_len) of direction 1 are skipped (the tensor-core
+// kernel assembles them); gap_len = 0 assembles every row.
+template <int P, bool MASS, typename Real, typename OutT, bool EDGE64, typename RE = double>
+__global__ void __launch_bounds__(128) k_stage1(StagedArgs A, int gap_lo, int gap_len) {
   constexpr int BW = 2 * P + 1;
   constexpr int NG = MASS ? 1 : 4;
   const Dir& D1 = A.d[0];
   const Dir& D2 = A.d[1];
   const Dir& D3 = A.d[2];
   const int64_t p2 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  const int i1 = blockIdx.y * blockDim.y + threadIdx.y;
-  const int64_t p3 = blockIdx.z;
+  const int i1k = blockIdx.y * blockDim.y + threadIdx.y;
+  const int i1 = i1k < gap_lo ? i1k : i1k + gap_len;
+  const int64_t p3l = blockIdx.z, p3 = A.p3_off + p3l;  // slab-relative and absolute band pair
   const int64_t nnz2 = A.nnz1[1];
   const int n1 = D1.n, n2 = D2.n, n3 = D3.n, nq1 = D1.nqp, NQ = A.NQ;
   if (p2 >= nnz2 || i1 >= n1) return;
@@ -705,7 +721,7 @@ __global__ void __launch_bounds__(128) k_stage1(StagedArgs A) {
   const int i3 = D3.pair_row[p3], j3 = blo(i3, P) + (int)(p3 - D3.prefix[i3]);
   const int qi1 = D1.q0[i1];
   const bool reg = i1 >= P + 1 && i1 <= n1 - P - 2;
-  const Real* G = reinterpret_cast<const Real*>(A.G) + ((p3 * NG) * nq1) * nnz2 + p2;
+  const Real* G = reinterpret_cast<const Real*>(A.G) + ((p3l * NG) * nq1) * nnz2 + p2;
   const int64_t gstride = (int64_t)nq1 * nnz2;  // next group
   const int64_t N1 = D1.prefix[n1], N2 = D2.prefix[n2];
   const int bw1 = bw(i1, P, n1), bw2 = bw(i2, P, n2), bw3 = bw(i3, P, n3);
@@ -746,14 +762,251 @@ __global__ void __launch_bounds__(128) k_stage1(StagedArgs A) {
 #pragma unroll
     for (int tt = 0; tt < BW; ++tt) out[base + tt] = toOut<OutT>(s[tt]);  // j1 - jlo1 = tt for regular rows
   } else if (EDGE64 && A.Gb) {
-    const double* Gd = A.Gb + ((p3 * NG) * A.nbq) * nnz2 + p2;
-    stage1_edge<P, MASS, double, OutT, true>(Gd, (int64_t)A.nbq * nnz2, nnz2, A.w1d + (size_t)i1 * NQ, wk, A.bt1d,
+    const RE* Gd = reinterpret_cast<const RE*>(A.Gb) + ((p3l * NG) * A.nbq) * nnz2 + p2;
+    stage1_edge<P, MASS, RE, OutT, true>(Gd, (int64_t)A.nbq * nnz2, nnz2, tab<RE>(A.w1e) + (size_t)i1 * NQ, wk,
+                                         tab<RE>(A.bt1e),
                                              bder, D1, i1, n1, NQ, A.nbl, A.hstart, A.nbq, out, base - jlo1);
   } else {
     stage1_edge<P, MASS, Real, OutT, false>(G, gstride, nnz2, w, wk, bt1, bder, D1, i1, n1, NQ, 0, 0, 0, out,
                                             base - jlo1);
   }
 }
+
+// ---------------------------------------------------------------------------
+// Stage 1 on the tensor cores (WQ_PREC_TF32X3), regular rows of direction 1.
+//
+// For a regular row i1 (Q_i1 = [q0, q0 + 2P]) the last mode product is a small
+// dense contraction, the same for every band pair (p2, p3):
+//   s(i1; p2, p3)[tt] = sum_k G[p3][g][q0 + t][p2] W_i1[k][tt],   k = NG t + g,
+//   W_i1[k][tt] = w1^{g}(i1, q0 + t) B1^{g & 1}(i1 - P + tt, q0 + t)
+// (zero outside the support overlap). With M = 16 band pairs p2 per warp, K = k and
+// N = tt it runs as mma.sync m16n8k8 on TF32 operands, each operand split into a
+// TF32 head and a TF32 tail (a = a_h + a_t) and the product taken as
+// a_t b_h + a_h b_t + a_h b_h with FP32 accumulation: about FP32 accuracy, against
+// TF32's 2^-11. For stiffness (NG = 4) one k-step of 8 holds 2 points x 4 groups,
+// so row i1 + 1 (window shifted by 2 points) reuses the A fragments of row i1
+// shifted by one k-step: G is read once per CTA. The outputs go through shared
+// memory and leave as contiguous runs of the CSR rows (coalesced stores).
+namespace tc {
+
+__device__ __forceinline__ unsigned tf32_rna(float x) {
+  unsigned r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return r;
+}
+
+__device__ __forceinline__ void mma_tf32(float (&d)[4], const unsigned (&a)[4], unsigned b0, unsigned b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+template <int P, bool MASS>
+struct Shape {
+  static constexpr int BW = 2 * P + 1;
+  static constexpr int NG = MASS ? 1 : 4;
+  static constexpr int KT = NG * BW;       // K extent
+  static constexpr int KS = (KT + 7) / 8;  // k-steps of 8
+  static constexpr int NT = (BW + 7) / 8;  // n-tiles of 8
+  static constexpr int WARPS = 8;
+  static constexpr int MT = 16 * WARPS;    // band pairs p2 per CTA
+  static constexpr int CHUNK = 32;         // rows i1 per CTA
+};
+
+// W_i1 in the B-fragment layout of mma.m16n8k8 (.col): for k-step s, n-tile nt and
+// lane l, {b0_head, b1_head, b0_tail, b1_tail} with b0 = W[8s + l%4][8nt + l/4] and
+// b1 = W[8s + 4 + l%4][8nt + l/4]. One thread per (row, s, nt, lane).
+template <int P, bool MASS>
+__global__ void k_bfrag(const double* __restrict__ w, const double* __restrict__ bt, const int* __restrict__ q0,
+                        const int* __restrict__ nq, int n1, int NQ, int i1_lo, int nrows, float4* __restrict__ out) {
+  using S = Shape<P, MASS>;
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= (int64_t)nrows * S::KS * S::NT * 32) return;
+  const int lane = (int)(e % 32);
+  const int nt = (int)((e / 32) % S::NT);
+  const int st = (int)((e / (32 * S::NT)) % S::KS);
+  const int i1 = i1_lo + (int)(e / (32 * S::NT * S::KS));
+  const int tt = 8 * nt + lane / 4;
+  const int qi = q0[i1];
+  float hv[2], tv[2];
+  for (int h = 0; h < 2; ++h) {
+    const int k = 8 * st + 4 * h + lane % 4;
+    double v = 0.0;
+    if (k < S::KT && tt < S::BW) {
+      const int t = MASS ? k : k / 4, g = MASS ? 0 : k % 4;
+      const int j1 = i1 - P + tt, q = qi + t;
+      const int loc = q - q0[j1];
+      if (j1 >= 0 && j1 < n1 && loc >= 0 && loc < nq[j1])
+        v = w[((size_t)g * n1 + i1) * NQ + t] * bt[((size_t)(g & 1) * n1 + j1) * NQ + loc];
+    }
+    const float f = (float)v;
+    const float head = __uint_as_float(tf32_rna(f));
+    hv[h] = head;
+    tv[h] = __uint_as_float(tf32_rna(f - head));
+  }
+  out[e] = make_float4(hv[0], hv[1], tv[0], tv[1]);
+}
+
+template <int P, bool MASS>
+__device__ __forceinline__ float a_elem(const float* __restrict__ G, int64_t gstride, int64_t nnz2, int nq1, int qi,
+                                        int k, int64_t p2, bool ok) {
+  const int t = MASS ? k : k >> 2, g = MASS ? 0 : k & 3;
+  const int q = qi + t;
+  return (ok && q < nq1) ? __ldg(G + g * gstride + (int64_t)q * nnz2 + p2) : 0.0f;
+}
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gmem));
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+__device__ __forceinline__ void split4(const float (&v)[4], unsigned (&ah)[4], unsigned (&at)[4]) {
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    ah[r] = tf32_rna(v[r]);
+    at[r] = tf32_rna(v[r] - __uint_as_float(ah[r]));
+  }
+}
+
+template <int P, bool MASS>
+__device__ __forceinline__ void fetch_a(const float* G, int64_t gstride, int64_t nnz2, int nq1, int qi, int st,
+                                        int64_t p2a, bool oka, int64_t p2b, bool okb, int lane, float (&v)[4]) {
+  const int k0 = 8 * st + lane % 4;
+  v[0] = a_elem<P, MASS>(G, gstride, nnz2, nq1, qi, k0, p2a, oka);
+  v[1] = a_elem<P, MASS>(G, gstride, nnz2, nq1, qi, k0, p2b, okb);
+  v[2] = a_elem<P, MASS>(G, gstride, nnz2, nq1, qi, k0 + 4, p2a, oka);
+  v[3] = a_elem<P, MASS>(G, gstride, nnz2, nq1, qi, k0 + 4, p2b, okb);
+}
+
+// The W fragments of row i1 (shared by the CTA's warps) stream into a double
+// buffer in shared memory with cp.async one row ahead; the A k-step that row i1 + 1
+// adds is fetched into registers before the products of row i1.
+template <int P, bool MASS, typename OutT>
+__global__ void __launch_bounds__(256) k_stage1_mma(StagedArgs A, const float4* __restrict__ bfrag, int i1_lo,
+                                                    int i1_hi) {
+  using S = Shape<P, MASS>;
+  constexpr int BW = S::BW, KS = S::KS, NT = S::NT, MT = S::MT, NG = S::NG;
+  constexpr int NF = KS * NT * 32;  // float4 fragments per row i1
+  __shared__ float stage[2][MT * BW];
+  __shared__ float4 wsm[2][NF];
+  __shared__ int64_t xb[MT];
+  __shared__ int yb[MT];
+  const Dir& D1 = A.d[0];
+  const Dir& D2 = A.d[1];
+  const Dir& D3 = A.d[2];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t nnz2 = A.nnz1[1];
+  const int64_t p2_0 = (int64_t)blockIdx.x * MT;
+  const int64_t p3l = blockIdx.y, p3 = A.p3_off + p3l;  // slab-relative and absolute band pair
+  const int ia = i1_lo + blockIdx.z * S::CHUNK, ib = min(i1_hi, ia + S::CHUNK);
+  const int n1 = D1.n, n2 = D2.n, n3 = D3.n, nq1 = D1.nqp;
+  // W fragments of the first row
+  for (int f = threadIdx.x; f < NF; f += blockDim.x) cp_async16(&wsm[0][f], bfrag + (size_t)(ia - i1_lo) * NF + f);
+  // output base of each band pair of the tile: value (i1, p2, p3, tt) sits at
+  // xb + yb * prefix1(i1) + tt for a regular row i1 (Kronecker order, Section 3)
+  {
+    const int i3 = D3.pair_row[p3], j3 = blo(i3, P) + (int)(p3 - D3.prefix[i3]);
+    const int bw3 = bw(i3, P, n3);
+    const int64_t N1 = D1.prefix[n1], N2 = D2.prefix[n2];
+    for (int r = threadIdx.x; r < MT; r += blockDim.x) {
+      const int64_t p2 = p2_0 + r;
+      if (p2 < nnz2) {
+        const int i2 = D2.pair_row[p2], j2 = blo(i2, P) + (int)(p2 - D2.prefix[i2]);
+        const int bw2 = bw(i2, P, n2);
+        xb[r] = D3.prefix[i3] * N2 * N1 + (int64_t)bw3 * D2.prefix[i2] * N1 +
+                ((int64_t)(j3 - blo(i3, P)) * bw2 + (j2 - blo(i2, P))) * BW;
+        yb[r] = bw3 * bw2;
+      }
+    }
+  }
+  const float* G = reinterpret_cast<const float*>(A.G) + (p3l * NG) * (int64_t)nq1 * nnz2;
+  const int64_t gstride = (int64_t)nq1 * nnz2;
+  const int64_t p2a = p2_0 + 16 * warp + (lane >> 2), p2b = p2a + 8;
+  const bool oka = p2a < nnz2, okb = p2b < nnz2;
+  unsigned ah[KS][4], at[KS][4];
+  {
+    const int qi = D1.q0[ia];
+#pragma unroll
+    for (int st = 0; st < KS; ++st) {
+      float v[4];
+      fetch_a<P, MASS>(G, gstride, nnz2, nq1, qi, st, p2a, oka, p2b, okb, lane, v);
+      split4(v, ah[st], at[st]);
+    }
+  }
+  cp_async_wait_all();
+  __syncthreads();
+  OutT* out = reinterpret_cast<OutT*>(A.vals);
+  const int nflush = MT * BW;
+  for (int i1 = ia; i1 < ib; ++i1) {
+    const int cur = (i1 - ia) & 1;
+    const bool more = i1 + 1 < ib;
+    // prefetch: W of row i1 + 1 into the other buffer, the k-step that row i1 + 1 adds
+    if (more)
+      for (int f = threadIdx.x; f < NF; f += blockDim.x)
+        cp_async16(&wsm[cur ^ 1][f], bfrag + (size_t)(i1 + 1 - i1_lo) * NF + f);
+    float nv[4];
+    if (!MASS && more) fetch_a<P, MASS>(G, gstride, nnz2, nq1, D1.q0[i1 + 1], KS - 1, p2a, oka, p2b, okb, lane, nv);
+    float acc[NT][4];
+#pragma unroll
+    for (int nt = 0; nt < NT; ++nt) acc[nt][0] = acc[nt][1] = acc[nt][2] = acc[nt][3] = 0.0f;
+    const float4* wf = wsm[cur] + lane;
+#pragma unroll
+    for (int st = 0; st < KS; ++st)
+#pragma unroll
+      for (int nt = 0; nt < NT; ++nt) {
+        const float4 b = wf[(st * NT + nt) * 32];
+        mma_tf32(acc[nt], at[st], __float_as_uint(b.x), __float_as_uint(b.y));   // tail x head
+        mma_tf32(acc[nt], ah[st], __float_as_uint(b.z), __float_as_uint(b.w));   // head x tail
+        mma_tf32(acc[nt], ah[st], __float_as_uint(b.x), __float_as_uint(b.y));   // head x head
+      }
+    // accumulators: rows lane/4 (+8), columns 8 nt + 2 (lane % 4) (+1)
+    float* sb = stage[cur];
+    const int r0 = 16 * warp + (lane >> 2);
+#pragma unroll
+    for (int nt = 0; nt < NT; ++nt)
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
+        const int tt = 8 * nt + 2 * (lane & 3) + c;
+        if (tt < BW) {
+          sb[r0 * BW + tt] = acc[nt][c];
+          sb[(r0 + 8) * BW + tt] = acc[nt][2 + c];
+        }
+      }
+    if (more) {
+      if (MASS) {
+        const int qn = D1.q0[i1 + 1];
+#pragma unroll
+        for (int st = 0; st < KS; ++st) {
+          float v[4];
+          fetch_a<P, MASS>(G, gstride, nnz2, nq1, qn, st, p2a, oka, p2b, okb, lane, v);
+          split4(v, ah[st], at[st]);
+        }
+      } else {
+        // the window moves by two points = one k-step
+#pragma unroll
+        for (int st = 0; st + 1 < KS; ++st)
+#pragma unroll
+          for (int r = 0; r < 4; ++r) {
+            ah[st][r] = ah[st + 1][r];
+            at[st][r] = at[st + 1][r];
+          }
+        split4(nv, ah[KS - 1], at[KS - 1]);
+      }
+    }
+    cp_async_wait_all();
+    __syncthreads();
+    const int64_t pre = D1.prefix[i1];
+    for (int e = threadIdx.x; e < nflush; e += blockDim.x) {
+      const int r = e / BW;
+      if (p2_0 + r < nnz2) out[xb[r] + (int64_t)yb[r] * pre + (e - r * BW)] = toOut<OutT>(sb[e]);
+    }
+  }
+}
+
+}  // namespace tc
 
 __global__ void k_pair_rows(const int64_t* __restrict__ prefix, int n, int* __restrict__ pair_row) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -786,7 +1039,7 @@ static wq_status staged_scratch(wq_plan_s* pl, size_t t3, size_t g, size_t gb, b
     plan_free(pl, pl->stg_c, s);
     pl->stg_c = nullptr;
     pl->stg_c_bytes = 0;
-    wq_status st = plan_alloc(pl, &pl->stg_c, gb, s, "staged assembly scratch (FP64 edge copy of G)");
+    wq_status st = plan_alloc(pl, &pl->stg_c, gb, s, "staged assembly scratch (edge copy of G)");
     if (st != WQ_OK) return st;
     pl->stg_c_bytes = gb;
   }
@@ -827,15 +1080,33 @@ static void edge_points(const wq_plan_s* pl, int* nbl, int* hstart, int* nbq) {
 }
 
 // Real: arithmetic of stages 3 and 2 (and T3); R1: arithmetic of stage 1 (and G).
-template <int P, bool MASS, typename Real, typename R1, typename OutT>
-static wq_status staged_t(wq_plan_s* pl, const double* kappa, void* vals, cudaStream_t s) {
+// TC: the regular rows of stage 1 on the tensor cores (3xTF32, tc::k_stage1_mma).
+template <int P, bool MASS, typename Real, typename R1, typename OutT, bool TC = false>
+static wq_status staged_t(wq_plan_s* pl, const double* kappa, void* vals, cudaStream_t s, const SlabHook* hook) {
   const int NT = MASS ? 1 : 9, NG = MASS ? 1 : 4;
   constexpr bool EDGE64 = sizeof(R1) < sizeof(Real);
+  static_assert(!TC || std::is_same<R1, float>::value, "the tensor-core stage 1 reads FP32 G");
+  // arithmetic of the first and last P+1 rows of direction 1 in the mixed modes: FP64
+  // where they share a launch with the FP32 rows (the FP64 pipe is otherwise idle),
+  // double-float where they run in a launch of their own beside the tensor cores
+  using GE = typename std::conditional<TC, Real, double>::type;
   int nbl = 0, hstart = 0, nbq = 0;
   if (EDGE64) edge_points(pl, &nbl, &hstart, &nbq);
-  wq_status st = staged_scratch(pl, (size_t)pl->nnz1[2] * NT * pl->nqp[0] * pl->nqp[1] * sizeof(Real),
-                                (size_t)pl->nnz1[2] * NG * pl->nqp[0] * pl->nnz1[1] * sizeof(R1),
-                                (size_t)pl->nnz1[2] * NG * nbq * pl->nnz1[1] * sizeof(double),
+  // slabs of direction 3: T3, G and the FP64 edge copy of G hold one slab at a time
+  const int n3 = (int)pl->n[2];
+  std::vector<int64_t> P3(n3 + 1, 0);  // prefix sums of the band widths of direction 3
+  for (int i = 0; i < n3; ++i) P3[i + 1] = P3[i] + (std::min(n3 - 1, i + P) - std::max(0, i - P) + 1);
+  const size_t per_p3 = (size_t)NT * pl->nqp[0] * pl->nqp[1] * sizeof(Real) +
+                        (size_t)NG * pl->nqp[0] * pl->nnz1[1] * sizeof(R1) + (size_t)NG * nbq * pl->nnz1[1] * sizeof(GE);
+  int rows = hook && hook->rows > 0 ? hook->rows : n3;
+  if (!(hook && hook->rows > 0) && pl->opt.scratch_limit > 0)
+    rows = (int)std::max<size_t>(1, pl->opt.scratch_limit / (per_p3 * (2 * P + 1)));
+  rows = std::max(1, std::min(rows, n3));
+  int64_t np3_max = 0;
+  for (int a = 0; a < n3; a += rows) np3_max = std::max(np3_max, P3[std::min(n3, a + rows)] - P3[a]);
+  wq_status st = staged_scratch(pl, (size_t)np3_max * NT * pl->nqp[0] * pl->nqp[1] * sizeof(Real),
+                                (size_t)np3_max * NG * pl->nqp[0] * pl->nnz1[1] * sizeof(R1),
+                                (size_t)np3_max * NG * nbq * pl->nnz1[1] * sizeof(GE),
                                 sizeof(Real) == sizeof(float) || sizeof(R1) == sizeof(float), s);
   if (st != WQ_OK) return st;
   constexpr bool F2 = std::is_same<Real, f2>::value, F2_1 = std::is_same<R1, f2>::value;
@@ -884,45 +1155,115 @@ static wq_status staged_t(wq_plan_s* pl, const double* kappa, void* vals, cudaSt
   A.T3 = A1.T3 = pl->stg_a;
   A.G = A1.G = pl->stg_b;
   A.vals = A1.vals = vals;
-  A.Gb = A1.Gb = EDGE64 ? reinterpret_cast<double*>(pl->stg_c) : nullptr;
-  A.w1d = A1.w1d = pl->dir[0].w;
-  A.bt1d = A1.bt1d = pl->dir[0].bt;
+  A.Gb = A1.Gb = EDGE64 ? pl->stg_c : nullptr;
+  // direction-1 tables in the edge-row type
+  A.w1e = A1.w1e = std::is_same<GE, double>::value ? (const void*)pl->dir[0].w : A.d[0].w;
+  A.bt1e = A1.bt1e = std::is_same<GE, double>::value ? (const void*)pl->dir[0].bt : A.d[0].bt;
   A.nbl = A1.nbl = nbl;
   A.hstart = A1.hstart = hstart;
   A.nbq = A1.nbq = nbq;
+  // tensor-core stage 1: B fragments of the regular rows of direction 1
+  const int tc_lo = P + 1, tc_rows = TC ? std::max(0, (int)pl->n[0] - 2 * P - 2) : 0;
+  if (TC && tc_rows > 0) {
+    using SH = tc::Shape<P, MASS>;
+    const size_t fb = (size_t)tc_rows * SH::KS * SH::NT * 32 * sizeof(float4);
+    if (pl->stg_d_bytes < fb) {
+      plan_free(pl, pl->stg_d, s);
+      pl->stg_d = nullptr;
+      pl->stg_d_bytes = 0;
+      wq_status st2 = plan_alloc(pl, &pl->stg_d, fb, s, "tensor-core stage-1 fragments");
+      if (st2 != WQ_OK) return st2;
+      pl->stg_d_bytes = fb;
+    }
+  }
   if (!vals) return WQ_OK;  // wq_plan_reserve: scratch only
   // transposed coefficients (the slots this matrix uses) and kappa, in Real
   {
     dim3 blk(32, 8), grd((nq1 + 31) / 32, (nq2 + 31) / 32, 7 * nq3 + (kappa ? nq3 : 0));
     k_transpose_coef<Real><<<grd, blk, 0, s>>>(pl->coef, kappa, cT, cT + 7 * NQP, nq1, nq2, nq3, 7);
   }
-  const int n1 = (int)pl->n[0], n2 = (int)pl->n[1], n3 = (int)pl->n[2];
-  k_stage3<P, MASS, Real><<<dim3(n3, (unsigned)(((int64_t)nq1 * nq2 + 127) / 128)), 128, 0, s>>>(A);
+  const int n1 = (int)pl->n[0], n2 = (int)pl->n[1];
   int r_lo = P + 1, r_hi = n2 - P - 1;  // regular rows [r_lo, r_hi)
   if (r_hi <= r_lo) r_lo = r_hi = n2;   // no regular rows: every row takes the boundary path
-  const int64_t np3 = pl->nnz1[2];
+  if (TC && tc_rows > 0) {
+    using SH = tc::Shape<P, MASS>;
+    const int64_t nf = (int64_t)tc_rows * SH::KS * SH::NT * 32;
+    tc::k_bfrag<P, MASS><<<(unsigned)((nf + 255) / 256), 256, 0, s>>>(
+        pl->dir[0].w, pl->dir[0].bt, pl->dir[0].q0, pl->dir[0].nq, n1, pl->nq_max, tc_lo, tc_rows,
+        reinterpret_cast<float4*>(pl->stg_d));
+    count_launch();
+  }
+  for (int i3a = 0; i3a < n3; i3a += rows) {
+  const int i3b = std::min(n3, i3a + rows);
+  A.p3_off = A1.p3_off = P3[i3a];
+  A.i3_off = A1.i3_off = i3a;
+  const int64_t np3 = P3[i3b] - P3[i3a];
+  k_stage3<P, MASS, Real><<<dim3(i3b - i3a, (unsigned)(((int64_t)nq1 * nq2 + 127) / 128)), 128, 0, s>>>(A);
   // Regular rows: k_stage2_reg (tables in shared memory, 32 rows per block) unless
   // the FP64 pipe, not L1, bounds the flat mapping (FP64, P <= 4: measured at 97%
   // of the DFMA rate) and 32-row blocks would leave more than 4% of lanes idle.
   const int nreg = r_hi - r_lo;
   const bool flat = std::is_same<Real, double>::value && P <= 4 && 32 * ((nreg + 31) / 32) * 100 > 104 * nreg;
   if (nreg > 0 && flat)
-    k_stage2<P, MASS, Real, true, R1>
+    k_stage2<P, MASS, Real, true, R1, GE>
         <<<dim3((unsigned)(((int64_t)nreg * nq1 + 127) / 128), (unsigned)np3), 128, 0, s>>>(A, r_lo, r_hi);
-  else if (nreg > 0)
-    k_stage2_reg<P, MASS, Real, R1>
+  else if (nreg > 0 && EDGE64) {
+    // mixed precision: double-float only for the points q1 that the first and last P+1
+    // rows of direction 1 read (their large WQ weights amplify rounding in stage 1);
+    // FP32 on the points between, whose G only regular rows of direction 1 read
+    const dim3 g2((unsigned)((nreg + 31) / 32), (unsigned)np3), b2(32, 4);
+    const int a1 = std::min(nbl, nq1), b0 = std::max(hstart, a1);
+    k_stage2_reg<P, MASS, Real, R1, Real, GE><<<g2, b2, 0, s>>>(A, r_lo, r_hi, 0, a1);
+    if (b0 < nq1) k_stage2_reg<P, MASS, Real, R1, Real, GE><<<g2, b2, 0, s>>>(A, r_lo, r_hi, b0, nq1);
+    if (b0 > a1) k_stage2_reg<P, MASS, R1, R1, Real, GE><<<g2, b2, 0, s>>>(A1, r_lo, r_hi, a1, b0);
+    count_launch((b0 < nq1 ? 1 : 0) + (b0 > a1 ? 1 : 0));
+  } else if (nreg > 0)
+    k_stage2_reg<P, MASS, Real, R1, Real, GE>
         <<<dim3((unsigned)((nreg + 31) / 32), (unsigned)np3), dim3(32, 4), 0, s>>>(A, r_lo, r_hi, 0, nq1);
   const int nb = r_lo + (n2 - r_hi);
   const bool edge2 = pl->dir[1].n_el >= 2 * P + 2;  // edge rows with compile-time patterns
   if (edge2)
-    launch_stage2_edge<P, MASS, Real, R1>(A, nq1, np3, s);
+    launch_stage2_edge<P, MASS, Real, R1, GE>(A, nq1, np3, s);
   else
-    k_stage2<P, MASS, Real, false, R1>
+    k_stage2<P, MASS, Real, false, R1, GE>
         <<<dim3((unsigned)(((int64_t)nb * nq1 + 127) / 128), (unsigned)np3), 128, 0, s>>>(A, r_lo, r_hi);
-  k_stage1<P, MASS, R1, OutT, EDGE64>
-      <<<dim3((unsigned)((pl->nnz1[1] + 31) / 32), (n1 + 3) / 4, (unsigned)np3), dim3(32, 4), 0, s>>>(A1);
-  count_launch(3 + (r_hi > r_lo ? 1 : 0) + (edge2 ? 2 * P + 2 : 1));
+  int gap_lo = 0, gap_len = 0;
+  cudaStream_t s1 = s;  // stream of the FFMA stage-1 kernel
+  if (TC && tc_rows > 0) {
+    // the edge rows (double-float, FFMA) run beside the tensor-core kernel on the
+    // plan's side stream, forked from and joined back into `s`
+    if (!pl->side_stream) {
+      WQ_CUDA_TRY(cudaStreamCreateWithFlags(&pl->side_stream, cudaStreamNonBlocking), "side stream");
+      WQ_CUDA_TRY(cudaEventCreateWithFlags(&pl->ev_fork, cudaEventDisableTiming), "fork event");
+      WQ_CUDA_TRY(cudaEventCreateWithFlags(&pl->ev_join, cudaEventDisableTiming), "join event");
+    }
+    WQ_CUDA_TRY(cudaEventRecord(pl->ev_fork, s), "fork event");
+    WQ_CUDA_TRY(cudaStreamWaitEvent(pl->side_stream, pl->ev_fork, 0), "fork wait");
+    s1 = pl->side_stream;
+    using SH = tc::Shape<P, MASS>;
+    tc::k_stage1_mma<P, MASS, OutT>
+        <<<dim3((unsigned)((pl->nnz1[1] + SH::MT - 1) / SH::MT), (unsigned)np3,
+                (unsigned)((tc_rows + SH::CHUNK - 1) / SH::CHUNK)),
+           32 * SH::WARPS, 0, s>>>(A1, reinterpret_cast<const float4*>(pl->stg_d), tc_lo, tc_lo + tc_rows);
+    count_launch();
+    gap_lo = tc_lo;
+    gap_len = tc_rows;
+  }
+  k_stage1<P, MASS, R1, OutT, EDGE64, GE>
+      <<<dim3((unsigned)((pl->nnz1[1] + 31) / 32), (n1 - gap_len + 3) / 4, (unsigned)np3), dim3(32, 4), 0, s1>>>(
+          A1, gap_lo, gap_len);
+  if (s1 != s) {
+    WQ_CUDA_TRY(cudaEventRecord(pl->ev_join, s1), "join event");
+    WQ_CUDA_TRY(cudaStreamWaitEvent(s, pl->ev_join, 0), "join wait");
+  }
+  count_launch(2 + (r_hi > r_lo ? 1 : 0) + (edge2 ? 2 * P + 2 : 1));
   WQ_CUDA_TRY(cudaGetLastError(), "staged assembly launch");
+  if (hook && hook->after) {
+    wq_status hs = hook->after(hook->ctx, i3a, i3b, s);
+    if (hs != WQ_OK) return hs;
+  }
+  }  // slabs
+  count_launch();  // the coefficient transpose
   return WQ_OK;
 }
 
@@ -930,30 +1271,37 @@ static wq_status staged_t(wq_plan_s* pl, const double* kappa, void* vals, cudaSt
 // unit of its own (wq_staged_p<P>.cu), so the degrees compile in parallel.
 template <int P>
 wq_status launch_staged_deg(wq_plan_s* pl, bool mass, const double* kappa, void* vals, int value_dtype,
-                            int precision, cudaStream_t s) {
+                            int precision, cudaStream_t s, const SlabHook* hook) {
   const bool v32 = value_dtype == WQ_VALUES_F32;
   if (precision == WQ_PREC_FP64)
-    return mass ? staged_t<P, true, double, double, double>(pl, kappa, vals, s)
-                : staged_t<P, false, double, double, double>(pl, kappa, vals, s);
+    return mass ? staged_t<P, true, double, double, double>(pl, kappa, vals, s, hook)
+                : staged_t<P, false, double, double, double>(pl, kappa, vals, s, hook);
   if (precision == WQ_PREC_F32X2) {
     if (v32)
-      return mass ? staged_t<P, true, f2, f2, float>(pl, kappa, vals, s)
-                  : staged_t<P, false, f2, f2, float>(pl, kappa, vals, s);
-    return mass ? staged_t<P, true, f2, f2, double>(pl, kappa, vals, s)
-                : staged_t<P, false, f2, f2, double>(pl, kappa, vals, s);
+      return mass ? staged_t<P, true, f2, f2, float>(pl, kappa, vals, s, hook)
+                  : staged_t<P, false, f2, f2, float>(pl, kappa, vals, s, hook);
+    return mass ? staged_t<P, true, f2, f2, double>(pl, kappa, vals, s, hook)
+                : staged_t<P, false, f2, f2, double>(pl, kappa, vals, s, hook);
+  }
+  if (precision == WQ_PREC_TF32X3) {
+    if (v32)
+      return mass ? staged_t<P, true, f2, float, float, true>(pl, kappa, vals, s, hook)
+                  : staged_t<P, false, f2, float, float, true>(pl, kappa, vals, s, hook);
+    return mass ? staged_t<P, true, f2, float, double, true>(pl, kappa, vals, s, hook)
+                : staged_t<P, false, f2, float, double, true>(pl, kappa, vals, s, hook);
   }
   if (precision == WQ_PREC_MIXED) {
     if (v32)
-      return mass ? staged_t<P, true, f2, float, float>(pl, kappa, vals, s)
-                  : staged_t<P, false, f2, float, float>(pl, kappa, vals, s);
-    return mass ? staged_t<P, true, f2, float, double>(pl, kappa, vals, s)
-                : staged_t<P, false, f2, float, double>(pl, kappa, vals, s);
+      return mass ? staged_t<P, true, f2, float, float>(pl, kappa, vals, s, hook)
+                  : staged_t<P, false, f2, float, float>(pl, kappa, vals, s, hook);
+    return mass ? staged_t<P, true, f2, float, double>(pl, kappa, vals, s, hook)
+                : staged_t<P, false, f2, float, double>(pl, kappa, vals, s, hook);
   }
   if (v32)
-    return mass ? staged_t<P, true, float, float, float>(pl, kappa, vals, s)
-                : staged_t<P, false, float, float, float>(pl, kappa, vals, s);
-  return mass ? staged_t<P, true, float, float, double>(pl, kappa, vals, s)
-              : staged_t<P, false, float, float, double>(pl, kappa, vals, s);
+    return mass ? staged_t<P, true, float, float, float>(pl, kappa, vals, s, hook)
+                : staged_t<P, false, float, float, float>(pl, kappa, vals, s, hook);
+  return mass ? staged_t<P, true, float, float, double>(pl, kappa, vals, s, hook)
+              : staged_t<P, false, float, float, double>(pl, kappa, vals, s, hook);
 }
 
 }  // namespace wq

@@ -5,8 +5,8 @@
 namespace wq {
 
 wq_status launch_staged_p2(wq_plan_s* pl, bool mass, const double* kappa, void* vals, int value_dtype,
-                            int precision, cudaStream_t s) {
-  return launch_staged_deg<2>(pl, mass, kappa, vals, value_dtype, precision, s);
+                            int precision, cudaStream_t s, const SlabHook* hook) {
+  return launch_staged_deg<2>(pl, mass, kappa, vals, value_dtype, precision, s, hook);
 }
 
 }  // namespace wq

@@ -47,9 +47,10 @@ def test_binding_enums_match_the_header():
     text = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
     enum = {k: int(v) for k, v in re.findall(r"\b(WQ_(?:PREC|VALUES|ALGO)_[A-Z0-9]+)\s*=\s*(\d+)", text)}
     assert {k for k in enum if k.startswith("WQ_PREC_")} == {"WQ_PREC_FP64", "WQ_PREC_FP32", "WQ_PREC_MIXED",
-                                                            "WQ_PREC_F32X2"}
+                                                            "WQ_PREC_F32X2", "WQ_PREC_TF32X3"}
     assert wq._PREC == {"fp64": enum["WQ_PREC_FP64"], "fp32": enum["WQ_PREC_FP32"],
-                        "mixed": enum["WQ_PREC_MIXED"], "f32x2": enum["WQ_PREC_F32X2"]}
+                        "mixed": enum["WQ_PREC_MIXED"], "f32x2": enum["WQ_PREC_F32X2"],
+                        "tf32x3": enum["WQ_PREC_TF32X3"]}
 
 
 def _create(lib, p, knots, ctrl, d=3):

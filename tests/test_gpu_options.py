@@ -147,3 +147,48 @@ def test_tune_cache_sets_the_tiles_of_the_plans_degree(wq, patch, tmp_path):
     plan = wq.Plan(patch.p, patch.knots, patch.ctrl, algorithm="fused", tune_cache=path, tiles=(16, 4))
     assert plan.tiles() == (16, 4)                                    # explicit tiles win
     plan.close()
+
+
+def test_slabs_of_direction_3_give_identical_values(wq):
+    """A scratch limit that forces one or two rows i3 per slab changes nothing in the
+    values (every mode product computes the same sums, slab by slab), and the scratch
+    the plan holds shrinks accordingly."""
+    from wq_synth import perturbed_cube
+    patch = perturbed_cube(4, (9, 7, 11), seed=73)
+    ref = wq.Plan(patch.p, patch.knots, patch.ctrl)
+    want = {m: ref.stiffness(precision=m, dtype=torch.float32 if m in ("mixed", "tf32x3", "fp32") else None)
+            for m in ("fp64", "mixed", "tf32x3", "f32x2", "fp32")}
+    want["mass"] = ref.mass()
+    ref.close()
+    for limit in (1, 3 << 20):
+        alloc = wq.TorchAllocator()
+        plan = wq.Plan(patch.p, patch.knots, patch.ctrl, scratch_limit=limit, allocator=alloc)
+        for m, v in want.items():
+            if m == "mass":
+                got = plan.mass()
+            else:
+                got = plan.stiffness(precision=m, dtype=v.dtype)
+            torch.cuda.synchronize()
+            assert torch.equal(got, v), (limit, m)
+        plan.close()
+
+
+def test_end_to_end_call_pipelines_slabs_into_page_locked_memory(wq):
+    """wq_assemble_host (slab by slab, copies on a second stream) returns the device
+    path's values bit for bit, into page-locked (wq_host_alloc) and pageable memory."""
+    from wq_synth import perturbed_cube
+    patch = perturbed_cube(3, (8, 6, 19), seed=74)
+    plan = wq.Plan(patch.p, patch.knots, patch.ctrl)
+    S = plan.stiffness().cpu().numpy()
+    M = plan.mass().cpu().numpy()
+    d = torch.empty(plan.nnz, dtype=torch.float64, device="cuda")
+    hb = wq.HostBuffer(plan.nnz)
+    for which, want in (("stiffness", S), ("mass", M)):
+        hb.array[:] = np.nan
+        plan.assemble_host(which, patch.ctrl.reshape(-1), d, hb.array)
+        np.testing.assert_array_equal(hb.array, want)
+        pageable = np.full(plan.nnz, np.nan)
+        plan.assemble_host(which, None, d, pageable)
+        np.testing.assert_array_equal(pageable, want)
+    hb.close()
+    plan.close()

@@ -41,10 +41,10 @@ def setup():
     plan.close()
 
 
-BARS = {"mixed": 1e-6, "fp32": 1e-5, "f32x2": 1e-12}
+BARS = {"mixed": 1e-6, "tf32x3": 1e-6, "fp32": 1e-5, "f32x2": 1e-12}
 
 
-@pytest.mark.parametrize("precision", ["mixed", "fp32", "f32x2"])
+@pytest.mark.parametrize("precision", ["mixed", "tf32x3", "fp32", "f32x2"])
 @pytest.mark.parametrize("dtype", ["float32", "float64"])
 def test_reduced_precision_p5_128(setup, precision, dtype):
     plan, rows, ref, rp = setup

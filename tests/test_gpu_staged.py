@@ -78,21 +78,53 @@ def test_staged_fp32(wq):
     print(f"staged fp32: worst row-relative error {worst:.3e}")
 
 
-@pytest.mark.parametrize("p", [2, 3, 4, 5, 6, 8])
+@pytest.mark.parametrize("p", [2, 3, 4, 5, 6, 7, 8])
 @pytest.mark.parametrize("which", ["stiffness", "mass"])
-def test_staged_mixed_precision(wq, p, which):
-    """Double-float for the q3 and q2 mode products, FP32 for the q1 one (FP64 for the first
-    and last p+1 rows of direction 1): 1e-6 row-relative."""
+@pytest.mark.parametrize("precision", ["mixed", "tf32x3"])
+def test_staged_mixed_precision(wq, p, which, precision):
+    """Mixed precision: double-float for the q3 mode product; for the q2 one double-float on
+    the first and last p+1 rows of direction 2 and on the points q1 that the first and last
+    p+1 rows of direction 1 read, FP32 elsewhere; FP32 for the q1 one (FFMA, or 3xTF32 on
+    the tensor cores) with its first and last p+1 rows of direction 1 in FP64: 1e-6
+    row-relative."""
     patch = perturbed_cube(p, (2 * p + 5, p + 4, p + 3), seed=40 + p)
     plan = wq.Plan(patch.p, patch.knots, patch.ctrl)
     kappa = random_field(int(np.prod(plan.n_qp)), seed=90 + p, kind="positive")
     fn = plan.stiffness if which == "stiffness" else plan.mass
-    S = fn(kappa=torch.as_tensor(kappa, device="cuda"), precision="mixed", dtype=torch.float32)
+    S = fn(kappa=torch.as_tensor(kappa, device="cuda"), precision=precision, dtype=torch.float32)
     torch.cuda.synchronize()
     orc = Oracle3D(patch.p, patch.knots, patch.ctrl, kappa=kappa)
     rows = sample_rows(plan.n, plan.p, 80, seed=600 + p)
     worst = check_rows(orc, plan, S, which, rows, tol=1e-6)
-    print(f"mixed p={p} {which}: worst row-relative error {worst:.3e}")
+    print(f"{precision} p={p} {which}: worst row-relative error {worst:.3e}")
+    plan.close()
+
+
+@pytest.mark.parametrize("p", [3, 5, 8])
+@pytest.mark.parametrize("which", ["stiffness", "mass"])
+def test_tensor_core_stage1_tiles_chunks_and_tails(wq, p, which):
+    """The 3xTF32 tensor-core stage 1 over several 32-row chunks of direction 1 and
+    several 128-pair tiles of direction 2 with a ragged last tile: every regular row of
+    direction 1 it writes matches the oracle at 1e-6, and the FFMA mixed path to FP32
+    rounding; FP64 values too."""
+    patch = perturbed_cube(p, (p + 70, 2 * p + 9, 3), seed=130 + p)
+    plan = wq.Plan(patch.p, patch.knots, patch.ctrl)
+    n1, n2, n3 = plan.n
+    fn = plan.stiffness if which == "stiffness" else plan.mass
+    T = fn(precision="tf32x3", dtype=torch.float32)
+    T64 = fn(precision="tf32x3", dtype=torch.float64)
+    F = fn(precision="mixed", dtype=torch.float32)
+    torch.cuda.synchronize()
+    rp = plan.pattern()[0].cpu().numpy()
+    i1s = [p + 1, p + 2, 33, 40 + p, n1 - p - 2]
+    rows = np.array([i1 + n1 * (i2 + n2 * i3) for i3 in (0, n3 - 1) for i2 in (0, n2 // 2, n2 - 1) for i1 in i1s])
+    orc = Oracle3D(patch.p, patch.knots, patch.ctrl)
+    check_rows(orc, plan, T, which, rows, tol=1e-6)
+    t, t64, f = T.double().cpu().numpy(), T64.cpu().numpy(), F.double().cpu().numpy()
+    for r in rows:
+        a, b = t[rp[r]:rp[r + 1]], f[rp[r]:rp[r + 1]]
+        np.testing.assert_array_equal(a, t64[rp[r]:rp[r + 1]])   # FP32 accumulators, either value type
+        assert np.abs(a - b).max() <= 2e-6 * np.abs(b).max(), r
     plan.close()
 
 

@@ -101,6 +101,7 @@ class Patch:
     ctrl: np.ndarray                 # (N_DOF, 3) float64
     name: str = ""
     meta: dict = field(default_factory=dict)
+    weights: np.ndarray | None = None  # (N_DOF,) NURBS weights, or None for a B-spline map
 
     @property
     def n(self) -> tuple:
@@ -165,6 +166,98 @@ def graded_breaks(n_el: int, seed: int, spread: float = 0.5) -> np.ndarray:
     w = 1.0 + spread * (2.0 * gen.uniforms(n_el) - 1.0)
     x = np.concatenate([[0.0], np.cumsum(w)])
     return x / x[-1]
+
+
+# ---------------------------------------------------------------------------
+# Rational (NURBS) geometries. Control points and weights are built in
+# homogeneous coordinates (w x, w y, w z, w), where degree elevation and knot
+# insertion are the B-spline ones; they change the representation, not the map.
+
+def _elevate_bezier(Pw: np.ndarray) -> np.ndarray:
+    """One degree elevation of a Bezier curve (rows = homogeneous control points):
+    Q_0 = P_0, Q_i = (i/(k+1)) P_{i-1} + (1 - i/(k+1)) P_i, Q_{k+1} = P_k."""
+    k = len(Pw) - 1
+    Q = np.empty((k + 2, Pw.shape[1]))
+    Q[0], Q[k + 1] = Pw[0], Pw[k]
+    for i in range(1, k + 1):
+        a = i / (k + 1)
+        Q[i] = a * Pw[i - 1] + (1.0 - a) * Pw[i]
+    return Q
+
+
+def _insert_knot(U: np.ndarray, Pw: np.ndarray, p: int, u: float) -> tuple:
+    """Insert knot u once into knot vector U of degree p (Boehm): the points of the
+    p spans around u become convex combinations of their neighbours."""
+    k = int(np.searchsorted(U, u, side="right") - 1)        # U[k] <= u < U[k+1]
+    n = len(Pw)
+    Q = np.empty((n + 1, Pw.shape[1]))
+    for i in range(n + 1):
+        if i <= k - p:
+            Q[i] = Pw[i]
+        elif i >= k + 1:
+            Q[i] = Pw[i - 1]
+        else:
+            a = (u - U[i]) / (U[i + p] - U[i])
+            Q[i] = (1.0 - a) * Pw[i - 1] + a * Pw[i]
+    return np.insert(U, k + 1, u), Q
+
+
+def quarter_arc(p: int, n_el: int) -> tuple:
+    """The quarter of the unit circle from (1, 0) to (0, 1) as a degree-p NURBS curve
+    with n_el uniform spans and simple interior knots: the rational quadratic arc
+    (control points (1,0), (1,1), (0,1), weights 1, 1/sqrt(2), 1), degree-elevated
+    and refined. Returns (open knot vector, (n, 2) control points, (n,) weights)."""
+    w1 = math.sqrt(0.5)
+    Pw = np.array([[1.0, 0.0, 1.0], [w1, w1, w1], [0.0, 1.0, 1.0]])
+    for _ in range(p - 2):
+        Pw = _elevate_bezier(Pw)
+    U = np.concatenate([np.zeros(p + 1), np.ones(p + 1)])
+    for e in range(1, n_el):
+        U, Pw = _insert_knot(U, Pw, p, e / n_el)
+    return U, Pw[:, :2] / Pw[:, 2:3], Pw[:, 2].copy()
+
+
+def quarter_annulus(p: int, n_el, r_in: float = 1.0, r_out: float = 2.0, height: float = 1.0) -> Patch:
+    """Thick quarter annulus {r_in <= sqrt(x^2 + y^2) <= r_out, x, y >= 0, 0 <= z <= height}
+    as a degree-p NURBS solid: direction 1 radial and direction 3 vertical (linear,
+    Greville control points, weight 1), direction 2 the circular arc of quarter_arc.
+    Every point of the map lies on the circle of radius r_in + (r_out - r_in) zeta_1."""
+    if isinstance(n_el, int):
+        n_el = (n_el, n_el, n_el)
+    U, arc, wa = quarter_arc(p, n_el[1])
+    k1 = open_knot_vector(uniform_breaks(n_el[0]), p)
+    k3 = open_knot_vector(uniform_breaks(n_el[2]), p)
+    r = r_in + (r_out - r_in) * greville(k1, p)
+    z = height * greville(k3, p)
+    n1, n2, n3 = len(r), len(wa), len(z)
+    i3, i2, i1 = np.meshgrid(np.arange(n3), np.arange(n2), np.arange(n1), indexing="ij")
+    ctrl = np.stack([r[i1] * arc[i2, 0], r[i1] * arc[i2, 1], z[i3]], axis=-1).reshape(-1, 3)
+    weights = wa[i2].reshape(-1).astype(np.float64)
+    return Patch(p=p, knots=[k1, U, k3], ctrl=np.ascontiguousarray(ctrl), weights=np.ascontiguousarray(weights),
+                 name=f"annulus_p{p}_nel{'x'.join(map(str, n_el))}",
+                 meta={"r_in": r_in, "r_out": r_out, "height": height,
+                       "volume": 0.25 * math.pi * (r_out ** 2 - r_in ** 2) * height})
+
+
+def perturbed_nurbs_cube(p: int, n_el, seed: int, amp: float = 0.05, wspread: float = 0.3) -> Patch:
+    """perturbed_cube with seeded NURBS weights U[1 - wspread, 1 + wspread] on every
+    control point (a general rational map, weights not of tensor-product form)."""
+    patch = perturbed_cube(p, n_el, seed=seed, amp=amp)
+    gen = SplitMix64(seed + 7919)
+    patch.weights = 1.0 + wspread * (2.0 * gen.uniforms(patch.n_dof) - 1.0)
+    patch.name = patch.name.replace("cube", "nurbs_cube")
+    return patch
+
+
+def random_spd_field(count: int, seed: int, spread: float = 0.5) -> np.ndarray:
+    """(6, count) symmetric positive-definite 3x3 tensors K = L L^T + (1 - spread) I with
+    L lower triangular, entries U[-spread, spread] (components K11 K12 K13 K22 K23 K33)."""
+    gen = SplitMix64(seed)
+    u = spread * (2.0 * gen.uniforms(6 * count).reshape(6, count) - 1.0)
+    L = np.zeros((count, 3, 3))
+    L[:, 0, 0], L[:, 1, 0], L[:, 2, 0], L[:, 1, 1], L[:, 2, 1], L[:, 2, 2] = u
+    K = np.einsum("nik,njk->nij", L, L) + (1.0 - spread) * np.eye(3)[None]
+    return np.stack([K[:, 0, 0], K[:, 0, 1], K[:, 0, 2], K[:, 1, 1], K[:, 1, 2], K[:, 2, 2]])
 
 
 # ---------------------------------------------------------------------------
