@@ -300,20 +300,31 @@ def timed(torch, stream, fn, reps: int = 3) -> float:
 
 def run_batch_variant(wq, torch, stream, count: int = 64):
     """64 seeded cubes (n_el in [8, 48]^3, p in {2, 3, 4, 5}), stiffness + mass, one
-    persistent graph-captured launch, tiles from the autotuner."""
+    graph launch: the staged kernels of every patch on parallel graph branches (the
+    default form), and the persistent fused kernel with tiles from the autotuner."""
     from paper_1605_01238_gb300 import tune
     from wq_synth import workload_batch
-    tiles = {int(k): tuple(v) for k, v in tune.tune(degrees=(2, 3, 4, 5), cache=None).items()}
     patches = workload_batch(count)
     plans = [wq.Plan(pt.p, pt.knots, pt.ctrl) for pt in patches]
-    tune.apply_tiles(plans, tiles)
     S = [torch.empty(pl.nnz, dtype=torch.float64, device="cuda") for pl in plans]
     M = [torch.empty(pl.nnz, dtype=torch.float64, device="cuda") for pl in plans]
+    out = {}
     batch = wq.Batch(plans, stiffness=S, mass=M)
     ms = timed(torch, stream, batch.launch)
-    out = {"patches": count, "nnz_written": batch.nnz_total, "work_items": batch.n_items, "grid": batch.grid,
-           "ms_per_launch": ms, "nnz_per_s": batch.nnz_total / (ms * 1e-3), "tiles": {str(k): v for k, v in tiles.items()},
-           "note": "stiffness + mass of every patch, FP64, one graph launch"}
+    out = {"patches": count, "nnz_written": batch.nnz_total, "jobs": batch.n_items, "graph_branches": batch.grid,
+           "ms_per_launch": ms, "nnz_per_s": batch.nnz_total / (ms * 1e-3),
+           "note": "stiffness + mass of every patch, FP64, staged kernels of each patch on parallel branches "
+                   "of one CUDA graph"}
+    batch.close()
+    tiles = {int(k): tuple(v) for k, v in tune.tune(degrees=(2, 3, 4, 5), cache=None).items()}
+    tune.apply_tiles(plans, tiles)
+    for pl in plans:
+        pl.set_algorithm("fused")
+    batch = wq.Batch(plans, stiffness=S, mass=M)
+    msf = timed(torch, stream, batch.launch)
+    out["fused"] = {"ms_per_launch": msf, "nnz_per_s": batch.nnz_total / (msf * 1e-3), "work_items": batch.n_items,
+                    "grid": batch.grid, "tiles": {str(k): v for k, v in tiles.items()},
+                    "note": "one persistent kernel over (patch, matrix, tile) items"}
     batch.close()
     for pl in plans:
         pl.close()

@@ -293,6 +293,14 @@ wq_status wq_assemble_host(wq_plan_t plan, int which, const double* h_ctrl, doub
 wq_status wq_host_alloc(size_t bytes, void** h_ptr);
 wq_status wq_host_free(void* h_ptr);
 
+/* Load vector by weighted quadrature: b_i = Q_i(f det DF) with the (0,0) rule of
+ * every direction (Eq. (quadrule): the WQ approximation of int f R_i dx).
+ *   d_f  device double[N_QP]: the source f at the points (q1 fastest)
+ *   d_b  device double[N_DOF]: output, i1 fastest
+ * Asynchronous on `stream`; the first call allocates plan-owned scratch of
+ * N_QP + nqp3 nqp2 n1 + nqp3 n2 n1 doubles. Not provided for NURBS basis functions. */
+wq_status wq_assemble_load(wq_plan_t plan, const double* d_f, double* d_b, void* stream);
+
 /* ---- adjoint ------------------------------------------------------------------
  * J = lambda^T S u (which = 1), lambda^T M u (which = 2) or both (which = 3), for
  * the plan's current geometry and the coefficient field kappa, and its gradients
@@ -316,12 +324,18 @@ wq_status wq_adjoint(wq_plan_t plan, int which, const double* d_kappa, const dou
                      const double* d_u, double* h_J, double* d_grad_kappa, double* d_grad_ctrl, void* stream);
 
 /* ---- batched assembly --------------------------------------------------------
- * Many patches of different size and degree assembled by one persistent kernel
- * launch, captured once in a CUDA graph (a memset of the work counter and the
- * kernel). The paper treats a single patch; rows of different patches are as
- * independent as rows of one patch (Section 1 notes that every row can be
- * computed on its own), so all (patch, matrix, tile) work items share one queue,
- * ordered longest first.
+ * Many patches of different size and degree assembled by one launch of a CUDA graph
+ * captured at creation. The paper treats a single patch; rows of different patches
+ * are as independent as rows of one patch (Section 1 notes that every row can be
+ * computed on its own). Two forms:
+ *  - staged (every plan's algorithm WQ_ALGO_AUTO or WQ_ALGO_STAGED, the default): the
+ *    graph holds each patch's staged kernels (stiffness then mass) on up to eight
+ *    parallel branches, patches assigned largest first to the least loaded branch;
+ *    wq_batch_create reserves each plan's FP64 staged scratch (wq_plan_reserve) and
+ *    synchronises `stream` before the capture;
+ *  - fused (any plan set to WQ_ALGO_FUSED): one persistent kernel whose blocks take
+ *    (patch, matrix, tile) work items from one queue, longest first (a memset of the
+ *    work counter and the kernel).
  *   plans        count plans (they must outlive the batch; wq_plan_refresh and
  *                wq_plan_set_geometry update them in place and stay valid)
  *   d_stiffness  NULL or count device pointers (FP64, nnz of each plan; a NULL
@@ -336,7 +350,8 @@ wq_status wq_batch_create(wq_batch_t* batch, int count, const wq_plan_t* plans, 
 wq_status wq_batch_launch(wq_batch_t batch, void* stream);
 /* The same call under the name of the library's interface description. */
 wq_status wq_batch_assemble(wq_batch_t batch, void* stream);
-/* Work items, total nonzeros written per launch and the persistent grid size. */
+/* Work items ((patch, matrix) jobs when staged, tiles when fused), total nonzeros
+ * written per launch, and the graph branches (staged) or persistent grid (fused). */
 wq_status wq_batch_info(wq_batch_t batch, int64_t* n_items, int64_t* nnz_total, int* grid);
 wq_status wq_batch_destroy(wq_batch_t batch);
 

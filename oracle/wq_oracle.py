@@ -588,6 +588,16 @@ class Oracle3D:
         scale = self.basis_scale(r, which)
         return out.ravel() if scale is None else out.ravel() * scale
 
+    def load(self, f: np.ndarray) -> np.ndarray:
+        """WQ load vector b_i = sum_{q in Q_i} prod_k w^{(0,0)}_{k,i_k,q_k} f(x_q) c(x_q)
+        (Eq. (quadrule) with the test function's (0,0) rules, c = det DF): array (N_DOF,)
+        with i1 fastest. f: values at the point grid (q1 fastest)."""
+        if self.nurbs_basis:
+            raise ValueError("the load vector with NURBS basis functions is not provided")
+        g = np.asarray(f, dtype=np.float64).reshape(self.coef[6].shape) * self.coef[6]   # (q3, q2, q1)
+        W = [d.W[0, 0] for d in self.dirs]                                             # (n, nqp) each
+        return np.einsum("xc,yb,za,cba->xyz", W[2], W[1], W[0], g, optimize=True).ravel()
+
     def rows(self, rows, which: str) -> list:
         return [self.row_values(int(r), which) for r in rows]
 

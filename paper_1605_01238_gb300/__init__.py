@@ -307,6 +307,17 @@ class Plan:
         """CSR values of the WQ mass matrix (Eq. (Mass_approx))."""
         return self._assemble(load().wq_assemble_mass, kappa, out, dtype, precision, stream)
 
+    def load(self, f, out=None, stream=None):
+        """WQ load vector b_i = Q_i(f det DF) (wq_assemble_load); f: CUDA float64 source
+        at the points (q1 fastest), N_QP values."""
+        torch = _torch()
+        fp = _dev_ptr(f, torch.float64, int(np.prod(self.n_qp)), "f")
+        if out is None:
+            out = torch.empty(self.n_rows, dtype=torch.float64, device="cuda")
+        bp = _dev_ptr(out, torch.float64, self.n_rows, "out")
+        check(load().wq_assemble_load(self._h, ctypes.c_void_p(fp), ctypes.c_void_p(bp), _stream(stream)))
+        return out
+
     def assemble_host(self, which: str, h_ctrl, d_vals, h_vals, stream=None) -> None:
         """End-to-end call with host buffers (wq_assemble_host): h_ctrl host float64
         control points or None, d_vals a CUDA float64 staging tensor of nnz

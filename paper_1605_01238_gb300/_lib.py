@@ -42,6 +42,7 @@ SIGNATURES = {
     "wq_assemble_stiffness": (c_int, [c_vp, c_vp, c_vp, c_int, c_int, c_vp]),
     "wq_assemble_mass": (c_int, [c_vp, c_vp, c_vp, c_int, c_int, c_vp]),
     "wq_assemble_host": (c_int, [c_vp, c_int, c_vp, c_vp, c_vp, c_vp]),
+    "wq_assemble_load": (c_int, [c_vp, c_vp, c_vp, c_vp]),
     "wq_host_alloc": (c_int, [ctypes.c_size_t, ctypes.POINTER(c_vp)]),
     "wq_host_free": (c_int, [c_vp]),
     "wq_sync_check": (c_int, [c_vp, c_vp]),

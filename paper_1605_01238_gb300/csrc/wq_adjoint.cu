@@ -178,7 +178,54 @@ __global__ void k_adjoint_point(PointArgs a) {
 
 static unsigned blocks_for(int64_t n, int tb) { return (unsigned)((n + tb - 1) / tb); }
 
+// g(q) = f(q) c(q): the load integrand on the reference cube (c = det DF, Eq. (mass2)).
+__global__ void k_load_field(const double* __restrict__ f, const double* __restrict__ c, double* __restrict__ g,
+                             int64_t n) {
+  const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (q < n) g[q] = f[q] * c[q];
+}
+
 }  // namespace wq
+
+// Load vector by weighted quadrature: b_i = Q_i(f det DF), the (0,0) rules of the
+// three directions applied to the point field (Eq. (quadrule) with the test
+// function's weights, the WQ approximation of int f R_i dx). Three mode products
+// from the points to the functions, as in the adjoint's last pass.
+extern "C" wq_status wq_assemble_load(wq_plan_t plan, const double* d_f, double* d_b, void* stream) {
+  if (!plan || !d_f || !d_b) return wq::set_error(WQ_ERR_INVALID_ARG, "NULL argument");
+  if (plan->nurbs_basis)
+    return wq::set_error(WQ_ERR_UNSUPPORTED, "the load vector with NURBS basis functions is not provided");
+  cudaStream_t s = (cudaStream_t)stream;
+  wq_plan_s* pl = plan;
+  const int n1 = (int)pl->n[0], n2 = (int)pl->n[1];
+  const int q1 = (int)pl->nqp[0], q2 = (int)pl->nqp[1], q3 = (int)pl->nqp[2];
+  const int64_t NQP = pl->n_qp_total;
+  if (pl->opt.checked) {
+    wq_status sc = wq::check_device_range(pl, d_f, sizeof(double) * (size_t)NQP, "d_f");
+    if (sc == WQ_OK) sc = wq::check_device_range(pl, d_b, sizeof(double) * (size_t)pl->n_rows, "d_b");
+    if (sc != WQ_OK) return sc;
+  }
+  const size_t need = (size_t)NQP + (size_t)q3 * q2 * n1 + (size_t)q3 * n2 * n1;
+  if (!pl->load_scratch) {
+    wq_status st = wq::plan_alloc(pl, (void**)&pl->load_scratch, need * sizeof(double), s, "load vector scratch");
+    if (st != WQ_OK) return st;
+  }
+  double* g = pl->load_scratch;
+  double* T1 = g + NQP;
+  double* T2 = T1 + (size_t)q3 * q2 * n1;
+  const int tb = 256, NQ = pl->nq_max;
+  wq::k_load_field<<<wq::blocks_for(NQP, tb), tb, 0, s>>>(d_f, pl->coef + 6 * NQP, g, NQP);
+  // rules of kind (0, 0) are the first block of each direction's table
+  wq::k_to_functions<<<wq::blocks_for((int64_t)n1 * q2 * q3, tb), tb, 0, s>>>(
+      g, T1, q1, q2, q3, 0, n1, pl->dir[0].w, pl->dir[0].q0, pl->dir[0].nq, NQ, 1, 0, 0);
+  wq::k_to_functions<<<wq::blocks_for((int64_t)n1 * n2 * q3, tb), tb, 0, s>>>(
+      T1, T2, n1, q2, q3, 1, n2, pl->dir[1].w, pl->dir[1].q0, pl->dir[1].nq, NQ, 1, 0, 0);
+  wq::k_to_functions<<<wq::blocks_for(pl->n_rows, tb), tb, 0, s>>>(
+      T2, d_b, n1, n2, q3, 2, (int)pl->n[2], pl->dir[2].w, pl->dir[2].q0, pl->dir[2].nq, NQ, 1, 0, 0);
+  wq::count_launch(4);
+  WQ_CUDA_TRY(cudaGetLastError(), "load vector launch");
+  return WQ_OK;
+}
 
 using wq::set_error;
 

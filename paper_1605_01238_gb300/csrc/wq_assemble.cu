@@ -837,6 +837,7 @@ struct wq_batch_s {
   int grid = 0;
   size_t smem = 0;
   int64_t nnz_total = 0;
+  int64_t kernels = 1;   // kernels one replay launches
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
 };
@@ -851,11 +852,102 @@ static void free_batch(wq_batch_s* b) {
   delete b;
 }
 
+// Staged batch: every patch's staged assembly (the three mode-product kernels of
+// Eq. (sumfactorization), stiffness then mass) captured into one CUDA graph on
+// up to eight parallel branches, patches assigned largest first to the least
+// loaded branch, so that small patches run side by side and the graph fills the
+// GPU. Each plan's FP64 staged scratch is reserved before the capture (nothing is
+// allocated inside it).
+static wq_status batch_staged(wq_batch_s* b, int count, const wq_plan_t* plans, void* const* d_stiffness,
+                              void* const* d_mass, cudaStream_t stream) {
+  std::vector<int> jobs;
+  std::vector<double> cost;
+  for (int k = 0; k < count; ++k) {
+    const bool s_k = d_stiffness && d_stiffness[k], m_k = d_mass && d_mass[k];
+    if (!s_k && !m_k) continue;
+    wq_status st = wq_plan_reserve(plans[k], WQ_PREC_FP64, WQ_VALUES_F64, 0, stream);
+    if (st != WQ_OK) return st;
+    jobs.push_back(k);
+    cost.push_back((double)plans[k]->nnz * ((s_k ? 3.0 : 0.0) + (m_k ? 1.0 : 0.0)));
+    b->nnz_total += plans[k]->nnz * ((s_k ? 1 : 0) + (m_k ? 1 : 0));
+  }
+  if (jobs.empty()) return set_error(WQ_ERR_INVALID_ARG, "the batch has no output arrays");
+  WQ_CUDA_TRY(cudaStreamSynchronize(stream), "batch reservation");
+  const int nb = std::max(1, std::min<int>(8, (int)jobs.size()));
+  std::vector<int> order(jobs.size());
+  for (size_t i = 0; i < order.size(); ++i) order[i] = (int)i;
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return cost[x] > cost[y]; });
+  std::vector<std::vector<int>> branch(nb);
+  std::vector<double> load(nb, 0.0);
+  for (int o : order) {
+    const int t = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+    branch[t].push_back(jobs[o]);
+    load[t] += cost[o];
+  }
+  std::vector<cudaStream_t> bs(nb, nullptr);
+  std::vector<cudaEvent_t> ev(nb + 1, nullptr);
+  cudaStream_t cs = nullptr;
+  cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+  for (int t = 0; t < nb && e == cudaSuccess; ++t) e = cudaStreamCreateWithFlags(&bs[t], cudaStreamNonBlocking);
+  for (int t = 0; t <= nb && e == cudaSuccess; ++t) e = cudaEventCreateWithFlags(&ev[t], cudaEventDisableTiming);
+  wq_status st = WQ_OK;
+  const int64_t launches0 = wq_launch_count();
+  bool capturing = false;
+  if (e == cudaSuccess) {
+    e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    capturing = e == cudaSuccess;
+  }
+  if (capturing) {
+    e = cudaEventRecord(ev[nb], cs);
+    for (int t = 0; t < nb && e == cudaSuccess; ++t) e = cudaStreamWaitEvent(bs[t], ev[nb], 0);
+    for (int t = 0; t < nb && e == cudaSuccess && st == WQ_OK; ++t) {
+      for (int k : branch[t]) {
+        if (st == WQ_OK && d_stiffness && d_stiffness[k])
+          st = wq::launch_staged(plans[k], false, nullptr, d_stiffness[k], WQ_VALUES_F64, WQ_PREC_FP64, bs[t]);
+        if (st == WQ_OK && d_mass && d_mass[k])
+          st = wq::launch_staged(plans[k], true, nullptr, d_mass[k], WQ_VALUES_F64, WQ_PREC_FP64, bs[t]);
+      }
+      if (e == cudaSuccess) e = cudaEventRecord(ev[t], bs[t]);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, ev[t], 0);
+    }
+    cudaError_t e2 = cudaStreamEndCapture(cs, &b->graph);
+    if (e == cudaSuccess) e = e2;
+  }
+  if (e == cudaSuccess && st == WQ_OK) e = cudaGraphInstantiate(&b->exec, b->graph, 0);
+  b->kernels = wq_launch_count() - launches0;
+  for (int t = 0; t < nb; ++t)
+    if (bs[t]) cudaStreamDestroy(bs[t]);
+  for (int t = 0; t <= nb; ++t)
+    if (ev[t]) cudaEventDestroy(ev[t]);
+  if (cs) cudaStreamDestroy(cs);
+  if (st != WQ_OK) return st;
+  if (e != cudaSuccess) return wq::cuda_error(e, "staged batch graph capture");
+  b->n_items = (int)jobs.size();
+  b->grid = nb;
+  return WQ_OK;
+}
+
 extern "C" wq_status wq_batch_create(wq_batch_t* out, int count, const wq_plan_t* plans, void* const* d_stiffness,
                                      void* const* d_mass, void* stream) {
-  (void)stream;
   if (!out || count <= 0 || !plans) return set_error(WQ_ERR_INVALID_ARG, "bad batch arguments");
   *out = nullptr;
+  bool all_staged = true;
+  for (int k = 0; k < count; ++k) {
+    if (!plans[k]) return set_error(WQ_ERR_INVALID_ARG, "NULL plan in batch");
+    if (plans[k]->nurbs_basis) return set_error(WQ_ERR_UNSUPPORTED, "NURBS basis functions are not batched");
+    all_staged = all_staged && plans[k]->algorithm != WQ_ALGO_FUSED;
+  }
+  if (all_staged) {
+    wq_batch_s* b = new wq_batch_s();
+    cudaGetDevice(&b->device);
+    wq_status st = batch_staged(b, count, plans, d_stiffness, d_mass, (cudaStream_t)stream);
+    if (st != WQ_OK) {
+      free_batch(b);
+      return st;
+    }
+    *out = b;
+    return WQ_OK;
+  }
   std::vector<wq::BatchJob> jobs;
   std::vector<wq::BatchItem> items;
   std::vector<double> cost;
@@ -950,7 +1042,7 @@ extern "C" wq_status wq_batch_create(wq_batch_t* out, int count, const wq_plan_t
 extern "C" wq_status wq_batch_launch(wq_batch_t batch, void* stream) {
   if (!batch) return set_error(WQ_ERR_INVALID_ARG, "NULL batch");
   WQ_CUDA_TRY(cudaGraphLaunch(batch->exec, (cudaStream_t)stream), "batch graph launch");
-  wq::count_launch();
+  wq::count_launch((int)batch->kernels);
   return WQ_OK;
 }
 

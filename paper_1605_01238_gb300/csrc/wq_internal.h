@@ -149,6 +149,7 @@ struct wq_plan_s {
   double* wts = nullptr;          // NULL (spline map), or [N] NURBS weights of the control points
   int nurbs_basis = 0;            // 1: NURBS basis functions (mass only)
   double* Kt = nullptr;           // NULL (identity), or [6][N_QP] coefficient tensor
+  double* load_scratch = nullptr; // wq_assemble_load: point field and two mode-product buffers
   cudaStream_t copy_stream = nullptr;  // end-to-end call: copies back slab by slab
   cudaEvent_t slab_done = nullptr;
   cudaStream_t side_stream = nullptr;  // tensor-core stage 1: the edge rows run beside it

@@ -916,7 +916,7 @@ static void free_plan(wq_plan_s* pl) {
     for (void* q : ptrs) wq::plan_free(pl, q, nullptr);
   }
   void* ptrs[] = {pl->ctrl, pl->ctrl_delta, pl->coef, pl->row_ptr, pl->col, pl->gauss, pl->err, pl->jac,
-                  pl->adj_scratch, pl->coefT, pl->stg_a, pl->stg_b, pl->stg_c, pl->stg_d, pl->wts, pl->Kt};
+                  pl->adj_scratch, pl->coefT, pl->stg_a, pl->stg_b, pl->stg_c, pl->stg_d, pl->wts, pl->Kt, pl->load_scratch};
   for (void* q : ptrs) wq::plan_free(pl, q, nullptr);
   if (pl->slab_done) cudaEventDestroy(pl->slab_done);
   if (pl->copy_stream) cudaStreamDestroy(pl->copy_stream);

@@ -926,15 +926,11 @@ __global__ void __launch_bounds__(256) k_stage1_mma(StagedArgs A, const float4* 
   const int64_t gstride = (int64_t)nq1 * nnz2;
   const int64_t p2a = p2_0 + 16 * warp + (lane >> 2), p2b = p2a + 8;
   const bool oka = p2a < nnz2, okb = p2b < nnz2;
-  unsigned ah[KS][4], at[KS][4];
+  float av[KS][4];  // A fragments as FP32; split into TF32 head and tail at each use
   {
     const int qi = D1.q0[ia];
 #pragma unroll
-    for (int st = 0; st < KS; ++st) {
-      float v[4];
-      fetch_a<P, MASS>(G, gstride, nnz2, nq1, qi, st, p2a, oka, p2b, okb, lane, v);
-      split4(v, ah[st], at[st]);
-    }
+    for (int st = 0; st < KS; ++st) fetch_a<P, MASS>(G, gstride, nnz2, nq1, qi, st, p2a, oka, p2b, okb, lane, av[st]);
   }
   cp_async_wait_all();
   __syncthreads();
@@ -949,19 +945,26 @@ __global__ void __launch_bounds__(256) k_stage1_mma(StagedArgs A, const float4* 
         cp_async16(&wsm[cur ^ 1][f], bfrag + (size_t)(i1 + 1 - i1_lo) * NF + f);
     float nv[4];
     if (!MASS && more) fetch_a<P, MASS>(G, gstride, nnz2, nq1, D1.q0[i1 + 1], KS - 1, p2a, oka, p2b, okb, lane, nv);
-    float acc[NT][4];
+    // two accumulator sets: head x head, and the two correction products, so that
+    // 2 NT independent MMA chains are in flight
+    float acc[NT][4], cor[NT][4];
 #pragma unroll
-    for (int nt = 0; nt < NT; ++nt) acc[nt][0] = acc[nt][1] = acc[nt][2] = acc[nt][3] = 0.0f;
+    for (int nt = 0; nt < NT; ++nt)
+#pragma unroll
+      for (int r = 0; r < 4; ++r) acc[nt][r] = cor[nt][r] = 0.0f;
     const float4* wf = wsm[cur] + lane;
 #pragma unroll
-    for (int st = 0; st < KS; ++st)
+    for (int st = 0; st < KS; ++st) {
+      unsigned ah[4], at[4];
+      split4(av[st], ah, at);
 #pragma unroll
       for (int nt = 0; nt < NT; ++nt) {
         const float4 b = wf[(st * NT + nt) * 32];
-        mma_tf32(acc[nt], at[st], __float_as_uint(b.x), __float_as_uint(b.y));   // tail x head
-        mma_tf32(acc[nt], ah[st], __float_as_uint(b.z), __float_as_uint(b.w));   // head x tail
-        mma_tf32(acc[nt], ah[st], __float_as_uint(b.x), __float_as_uint(b.y));   // head x head
+        mma_tf32(cor[nt], at, __float_as_uint(b.x), __float_as_uint(b.y));   // tail x head
+        mma_tf32(acc[nt], ah, __float_as_uint(b.x), __float_as_uint(b.y));   // head x head
+        mma_tf32(cor[nt], ah, __float_as_uint(b.z), __float_as_uint(b.w));   // head x tail
       }
+    }
     // accumulators: rows lane/4 (+8), columns 8 nt + 2 (lane % 4) (+1)
     float* sb = stage[cur];
     const int r0 = 16 * warp + (lane >> 2);
@@ -971,29 +974,23 @@ __global__ void __launch_bounds__(256) k_stage1_mma(StagedArgs A, const float4* 
       for (int c = 0; c < 2; ++c) {
         const int tt = 8 * nt + 2 * (lane & 3) + c;
         if (tt < BW) {
-          sb[r0 * BW + tt] = acc[nt][c];
-          sb[(r0 + 8) * BW + tt] = acc[nt][2 + c];
+          sb[r0 * BW + tt] = acc[nt][c] + cor[nt][c];
+          sb[(r0 + 8) * BW + tt] = acc[nt][2 + c] + cor[nt][2 + c];
         }
       }
     if (more) {
       if (MASS) {
         const int qn = D1.q0[i1 + 1];
 #pragma unroll
-        for (int st = 0; st < KS; ++st) {
-          float v[4];
-          fetch_a<P, MASS>(G, gstride, nnz2, nq1, qn, st, p2a, oka, p2b, okb, lane, v);
-          split4(v, ah[st], at[st]);
-        }
+        for (int st = 0; st < KS; ++st) fetch_a<P, MASS>(G, gstride, nnz2, nq1, qn, st, p2a, oka, p2b, okb, lane, av[st]);
       } else {
         // the window moves by two points = one k-step
 #pragma unroll
         for (int st = 0; st + 1 < KS; ++st)
 #pragma unroll
-          for (int r = 0; r < 4; ++r) {
-            ah[st][r] = ah[st + 1][r];
-            at[st][r] = at[st + 1][r];
-          }
-        split4(nv, ah[KS - 1], at[KS - 1]);
+          for (int r = 0; r < 4; ++r) av[st][r] = av[st + 1][r];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) av[KS - 1][r] = nv[r];
       }
     }
     cp_async_wait_all();

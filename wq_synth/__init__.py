@@ -202,6 +202,18 @@ def _insert_knot(U: np.ndarray, Pw: np.ndarray, p: int, u: float) -> tuple:
     return np.insert(U, k + 1, u), Q
 
 
+def refined_curve(values, p: int, n_el: int) -> tuple:
+    """A degree-p spline curve fixed on one span (Bezier control values `values`, p+1
+    of them, shape (p+1,) or (p+1, k)) and refined by knot insertion to n_el uniform
+    spans with simple knots: the same curve on every mesh. Returns (knots, control values)."""
+    P = np.asarray(values, dtype=np.float64)
+    P = P.reshape(p + 1, -1)
+    U = np.concatenate([np.zeros(p + 1), np.ones(p + 1)])
+    for e in range(1, n_el):
+        U, P = _insert_knot(U, P, p, e / n_el)
+    return U, P if np.asarray(values).ndim > 1 else P[:, 0]
+
+
 def quarter_arc(p: int, n_el: int) -> tuple:
     """The quarter of the unit circle from (1, 0) to (0, 1) as a degree-p NURBS curve
     with n_el uniform spans and simple interior knots: the rational quadratic arc
