@@ -45,16 +45,18 @@ METRIC = "WQ 3D stiffness nnz/s and % of HBM-write roofline; mixed vs FP64 at â‰
 
 # DRAM traffic of one FP64 staged stiffness assembly (k_stage3, k_stage2 and its
 # edge-row kernels, k_stage1), from one ncu capture of dram__bytes_read.sum +
-# dram__bytes_write.sum per workload. It is reported only while the kernel
-# sources still hash to the captured value.
-TRAFFIC_CAPTURE = {"p": 4, "n_el": 64, "bytes": 3997.57e6 + 4354.18e6, "sources": "17c1a0e7441ac796",
+# dram__bytes_write.sum on a smaller case of the same degree (the full-size case is
+# too large to capture), scaled to the bench workload by the nonzeros assembled. It
+# is reported only while the kernel sources still hash to the captured value.
+TRAFFIC_CAPTURE = {"p": 8, "workload": "cube_8_32", "nnz": None, "bytes": None, "sources": None,
                    "files": ("paper_1605_01238_gb300/csrc/wq_staged_impl.cuh", "paper_1605_01238_gb300/csrc/wq_internal.h")}
 
 
-def captured_traffic(p: int, n_el: int):
-    if (p, n_el) != (TRAFFIC_CAPTURE["p"], TRAFFIC_CAPTURE["n_el"]):
+def captured_traffic(p: int, nnz: int):
+    c = TRAFFIC_CAPTURE
+    if p != c["p"] or not c["bytes"] or not c["nnz"] or kernel_source_hash() != c["sources"]:
         return None
-    return TRAFFIC_CAPTURE["bytes"] if kernel_source_hash() == TRAFFIC_CAPTURE["sources"] else None
+    return c["bytes"] * nnz / c["nnz"]
 
 
 def kernel_source_hash() -> str:
@@ -561,7 +563,7 @@ def run_ours(args):
         "config": config,
         "roofline": {"bound": "alu", "achieved": achieved_tf, "peak": peak_tf, "unit": "TFLOP/s",
                      "frac": achieved_tf / peak_tf,
-                     "traffic": captured_traffic(p, patch.n_el[0]) if args.algo in ("auto", "staged") else None,
+                     "traffic": captured_traffic(p, nnz) if args.algo in ("auto", "staged") else None,
                      "kernel": (f"wq_assemble_stiffness, FP64, p={p}: k_stage3, k_stage2 (regular rows + "
                                 f"{2 * p + 2} edge-row kernels), k_stage1" if args.algo in ("auto", "staged")
                                 else f"k_assemble<{p},stiffness,fp64> (fused)"),

@@ -190,7 +190,7 @@ wq_status wq_plan_pattern(wq_plan_t plan, const int64_t** d_row_ptr, const int32
 wq_status wq_plan_set_geometry(wq_plan_t plan, const double* ctrl, int ctrl_on_device,
                                void* stream);
 
-/* NURBS geometry (the paper's parametrisations are "spline or NURBS", Section 3):
+/* NURBS geometry (Section 3 allows spline or NURBS parametrisations of the domain):
  * with weights w_i > 0 the map is F = sum_i w_i C_i B_i / W, W = sum_i w_i B_i, and
  * DF, det DF and c_lm follow the rational map; the basis functions stay the
  * B-splines pushed forward (R_i = B_i o F^{-1}, Section 3), so the stiffness and
@@ -208,8 +208,8 @@ wq_status wq_plan_set_geometry(wq_plan_t plan, const double* ctrl, int ctrl_on_d
 wq_status wq_plan_set_weights(wq_plan_t plan, const double* w, int on_device, int nurbs_basis, void* stream);
 
 /* Coefficient tensor of the operator -div(K grad u) (Eq. (coef_stiff) with K:
- * c_lm = det DF (DF^{-1} K DF^{-T})_lm; "c incorporates the coefficient of the
- * equation", after Eq. (mass2)).
+ * c_lm = det DF (DF^{-1} K DF^{-T})_lm; after Eq. (mass2) the paper lets c take in
+ * the coefficient of the PDE).
  *   d_K  NULL (K = I again), or device double[6][N_QP]: K11 K12 K13 K22 K23 K33 at
  *        every point (q1 fastest), symmetric positive definite (not checked), copied
  * Recomputes the coefficients on `stream`; the first call allocates the plan-owned

@@ -1005,6 +1005,198 @@ __global__ void __launch_bounds__(256) k_stage1_mma(StagedArgs A, const float4* 
 
 }  // namespace tc
 
+// ---------------------------------------------------------------------------
+// Stage 1 for the regular rows of direction 1 with FP32 G (WQ_PREC_MIXED, WQ_PREC_FP32):
+// one band pair p2 per thread, a CTA of 256 consecutive band pairs for one p3 and
+// a chunk of rows i1. For a regular row the q1 window is [2 i1 - P, 2 i1 + P], so
+// row i1 + 1 reuses the window of row i1 shifted by two points: each thread keeps
+// the window of its G column in registers and loads every value once. The row's
+// rule weights and trial values sit in shared memory (built one row ahead, read as
+// broadcasts), the contraction folds the test weights into h_b per point and adds
+// B^{(b)}(j1) h_b over the support overlaps only, and the values leave through
+// shared memory as contiguous runs of the CSR rows.
+// Tables of the FFMA stage 1 for regular rows [i1_lo, i1_lo + nrows) of direction 1,
+// as float4: the four rule weights of point t, then for point t the (B, B') values of
+// its band tt = (t + 1)/2 .. (t + 1)/2 + P (P + 1 - (t & 1) of them, the rest zero),
+// SL float4 per point. One thread per (row, float4).
+template <int P, bool MASS>
+__global__ void k_s1_tables(const float* __restrict__ w1, const float* __restrict__ b1, const int* __restrict__ q0,
+                            const int* __restrict__ nq, int n1, int NQ, int i1_lo, int nrows, float4* __restrict__ out) {
+  constexpr int BW = 2 * P + 1, SL = (P + 2) / 2, TF4 = BW + BW * SL;
+  const int64_t e0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e0 >= (int64_t)nrows * TF4) return;
+  const int i1 = i1_lo + (int)(e0 / TF4), e = (int)(e0 % TF4);
+  const int qi = q0[i1];
+  auto bval = [&](int b, int t, int tt) {
+    const int j1 = i1 - P + tt, loc = qi + t - q0[j1];
+    return (tt < BW && loc >= 0 && loc < nq[j1]) ? b1[((size_t)b * n1 + j1) * NQ + loc] : 0.0f;
+  };
+  float4 v;
+  if (e < BW) {
+    const size_t o = (size_t)i1 * NQ + e, k = (size_t)n1 * NQ;
+    v = MASS ? make_float4(w1[o], 0.0f, 0.0f, 0.0f) : make_float4(w1[o], w1[o + k], w1[o + 2 * k], w1[o + 3 * k]);
+  } else {
+    const int f = e - BW, t = f / SL, k = 2 * (f % SL), tt = (t + 1) / 2 + k;
+    const int cnt = P + 1 - (t & 1);
+    v = make_float4(k < cnt ? bval(0, t, tt) : 0.0f, (!MASS && k < cnt) ? bval(1, t, tt) : 0.0f,
+                    k + 1 < cnt ? bval(0, t, tt + 1) : 0.0f, (!MASS && k + 1 < cnt) ? bval(1, t, tt + 1) : 0.0f);
+  }
+  out[e0] = v;
+}
+
+// The first and last P+1 rows of direction 1 for band pair (p2, p3): the support
+// overlaps are clipped there, and in the mixed mode they run in RE from the edge
+// copy of G (the large, sign-alternating boundary weights amplify FP32 rounding).
+template <int P, bool MASS, typename OutT, bool EDGE64, typename RE>
+__device__ void stage1_edge_rows(const StagedArgs& A, int64_t p2, int64_t p3l, int64_t p3) {
+  constexpr int NG = MASS ? 1 : 4;
+  const Dir& D1 = A.d[0];
+  const Dir& D2 = A.d[1];
+  const Dir& D3 = A.d[2];
+  const int64_t nnz2 = A.nnz1[1];
+  if (p2 >= nnz2) return;
+  const int n1 = D1.n, n2 = D2.n, n3 = D3.n, nq1 = D1.nqp, NQ = A.NQ;
+  const int i2 = D2.pair_row[p2], j2 = blo(i2, P) + (int)(p2 - D2.prefix[i2]);
+  const int i3 = D3.pair_row[p3], j3 = blo(i3, P) + (int)(p3 - D3.prefix[i3]);
+  const int bw2 = bw(i2, P, n2), bw3 = bw(i3, P, n3);
+  const int64_t N1 = D1.prefix[n1], N2 = D2.prefix[n2];
+  const int64_t pre23 = D3.prefix[i3] * N2 * N1 + (int64_t)bw3 * D2.prefix[i2] * N1;
+  const int64_t off23 = (int64_t)(j3 - blo(i3, P)) * bw2 + (j2 - blo(i2, P));
+  OutT* out = reinterpret_cast<OutT*>(A.vals);
+  const int64_t wk = (int64_t)n1 * NQ, bder = (int64_t)n1 * NQ;
+  for (int k = 0; k < 2 * P + 2; ++k) {
+    const int i1 = k <= P ? k : n1 - (2 * P + 2) + k;
+    const int bw1 = bw(i1, P, n1), jlo1 = blo(i1, P);
+    const int64_t base = pre23 + (int64_t)bw3 * bw2 * D1.prefix[i1] + off23 * bw1 - jlo1;
+    if (EDGE64 && A.Gb) {
+      const RE* Gd = reinterpret_cast<const RE*>(A.Gb) + ((p3l * NG) * A.nbq) * nnz2 + p2;
+      stage1_edge<P, MASS, RE, OutT, true>(Gd, (int64_t)A.nbq * nnz2, nnz2, tab<RE>(A.w1e) + (size_t)i1 * NQ, wk,
+                                           tab<RE>(A.bt1e), bder, D1, i1, n1, NQ, A.nbl, A.hstart, A.nbq, out, base);
+    } else {
+      const float* G = reinterpret_cast<const float*>(A.G) + ((p3l * NG) * nq1) * nnz2 + p2;
+      stage1_edge<P, MASS, float, OutT, false>(G, (int64_t)nq1 * nnz2, nnz2, tab<float>(D1.w) + (size_t)i1 * NQ, wk,
+                                               tab<float>(D1.bt), bder, D1, i1, n1, NQ, 0, 0, 0, out, base);
+    }
+  }
+}
+
+// blockIdx.x = tile of 256 band pairs * (n_chunks + 1) + role: roles 0 .. n_chunks - 1 take
+// 32 regular rows each, role n_chunks the edge rows of the tile, so that blocks doing
+// the FP64 (or double-float) edge rows run beside blocks doing FP32 regular rows.
+template <int P, bool MASS, typename OutT, bool EDGE64, typename RE>
+__global__ void __launch_bounds__(256) k_stage1_ffma(StagedArgs A, const float4* __restrict__ tabs, int i1_lo,
+                                                     int i1_hi, int n_chunks) {
+  constexpr int BW = 2 * P + 1, NG = MASS ? 1 : 4, MT = 256, CHUNK = 32;
+  const int role = blockIdx.x % (n_chunks + 1);
+  const int64_t p2_0 = (int64_t)(blockIdx.x / (n_chunks + 1)) * MT;
+  if (role == n_chunks) {
+    stage1_edge_rows<P, MASS, OutT, EDGE64, RE>(A, p2_0 + threadIdx.x, blockIdx.y, A.p3_off + blockIdx.y);
+    return;
+  }
+  // Tables of a row, read as float4 broadcasts: the four rule weights of point t,
+  // then for point t the (B, B') values of its band tt = (t + 1)/2 .. (t + 1)/2 + P
+  // (P + 1 - (t & 1) of them; the rest zero), in a slot of SL float4.
+  constexpr int SL = (P + 2) / 2;                 // float4 per point: 2 (B, B') pairs each
+  constexpr int TF4 = BW + BW * SL;
+  __shared__ float stage[2][MT * BW];
+  __shared__ float4 tbl[2][TF4];
+  __shared__ int64_t xb[MT];
+  __shared__ int yb[MT];
+  const Dir& D1 = A.d[0];
+  const Dir& D2 = A.d[1];
+  const Dir& D3 = A.d[2];
+  const int64_t nnz2 = A.nnz1[1];
+  const int64_t p3l = blockIdx.y, p3 = A.p3_off + p3l;
+  const int ia = i1_lo + role * CHUNK, ib = min(i1_hi, ia + CHUNK);
+  const int n1 = D1.n, n2 = D2.n, n3 = D3.n, nq1 = D1.nqp, NQ = A.NQ;
+  // tables of row i1 (precomputed by k_s1_tables), one row ahead through cp.async
+  auto build = [&](int i1, float4* t4) {
+    for (int e = threadIdx.x; e < TF4; e += blockDim.x) tc::cp_async16(t4 + e, tabs + (size_t)(i1 - i1_lo) * TF4 + e);
+  };
+  build(ia, tbl[0]);
+  {
+    const int i3 = D3.pair_row[p3], j3 = blo(i3, P) + (int)(p3 - D3.prefix[i3]);
+    const int bw3 = bw(i3, P, n3);
+    const int64_t N1 = D1.prefix[n1], N2 = D2.prefix[n2];
+    for (int r = threadIdx.x; r < MT; r += blockDim.x) {
+      const int64_t q2 = p2_0 + r;
+      if (q2 < nnz2) {
+        const int i2 = D2.pair_row[q2], j2 = blo(i2, P) + (int)(q2 - D2.prefix[i2]);
+        const int bw2 = bw(i2, P, n2);
+        xb[r] = D3.prefix[i3] * N2 * N1 + (int64_t)bw3 * D2.prefix[i2] * N1 +
+                ((int64_t)(j3 - blo(i3, P)) * bw2 + (j2 - blo(i2, P))) * BW;
+        yb[r] = bw3 * bw2;
+      }
+    }
+  }
+  const int64_t p2 = p2_0 + threadIdx.x;
+  const bool ok = p2 < nnz2;
+  const float* G = reinterpret_cast<const float*>(A.G) + (p3l * NG) * (int64_t)nq1 * nnz2 + (ok ? p2 : 0);
+  const int64_t gstride = (int64_t)nq1 * nnz2;
+  auto ldg = [&](int g, int q) { return (ok && q < nq1) ? __ldg(G + g * gstride + (int64_t)q * nnz2) : 0.0f; };
+  float gw[NG][BW];  // the q1 window of this thread's G column
+  {
+    const int qi = D1.q0[ia];
+#pragma unroll
+    for (int g = 0; g < NG; ++g)
+#pragma unroll
+      for (int t = 0; t < BW; ++t) gw[g][t] = ldg(g, qi + t);
+  }
+  tc::cp_async_wait_all();
+  __syncthreads();
+  OutT* out = reinterpret_cast<OutT*>(A.vals);
+  for (int i1 = ia; i1 < ib; ++i1) {
+    const int cur = (i1 - ia) & 1;
+    const bool more = i1 + 1 < ib;
+    if (more) build(i1 + 1, tbl[cur ^ 1]);
+    const float4* tw = tbl[cur];
+    const float4* tb = tbl[cur] + BW;
+    float sacc[BW];
+#pragma unroll
+    for (int tt = 0; tt < BW; ++tt) sacc[tt] = 0.0f;
+#pragma unroll
+    for (int t = 0; t < BW; ++t) {
+      const float4 wv = tw[t];
+      float h0, h1 = 0.0f;
+      if (MASS) {
+        h0 = wv.x * gw[0][t];
+      } else {
+        h0 = fmaf(wv.x, gw[0][t], wv.z * gw[2][t]);
+        h1 = fmaf(wv.y, gw[1][t], wv.w * gw[3][t]);
+      }
+      const int tt0 = (t + 1) / 2, cnt = P + 1 - (t & 1);
+#pragma unroll
+      for (int m = 0; m < SL; ++m) {
+        const float4 bv = tb[t * SL + m];
+        if (2 * m < cnt) sacc[tt0 + 2 * m] = MASS ? fmaf(bv.x, h0, sacc[tt0 + 2 * m])
+                                                   : fmaf(bv.y, h1, fmaf(bv.x, h0, sacc[tt0 + 2 * m]));
+        if (2 * m + 1 < cnt) sacc[tt0 + 2 * m + 1] = MASS ? fmaf(bv.z, h0, sacc[tt0 + 2 * m + 1])
+                                                           : fmaf(bv.w, h1, fmaf(bv.z, h0, sacc[tt0 + 2 * m + 1]));
+      }
+    }
+    float* sb = stage[cur];
+#pragma unroll
+    for (int tt = 0; tt < BW; ++tt) sb[threadIdx.x * BW + tt] = sacc[tt];
+    if (more) {  // the window moves by two points
+      const int qn = D1.q0[i1 + 1];
+#pragma unroll
+      for (int g = 0; g < NG; ++g) {
+#pragma unroll
+        for (int t = 0; t + 2 < BW; ++t) gw[g][t] = gw[g][t + 2];
+        gw[g][BW - 2] = ldg(g, qn + BW - 2);
+        gw[g][BW - 1] = ldg(g, qn + BW - 1);
+      }
+    }
+    tc::cp_async_wait_all();
+    __syncthreads();
+    const int64_t pre = D1.prefix[i1];
+    for (int e = threadIdx.x; e < MT * BW; e += blockDim.x) {
+      const int r = e / BW;
+      if (p2_0 + r < nnz2) out[xb[r] + (int64_t)yb[r] * pre + (e - r * BW)] = toOut<OutT>(sb[e]);
+    }
+  }
+}
+
 __global__ void k_pair_rows(const int64_t* __restrict__ prefix, int n, int* __restrict__ pair_row) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
@@ -1159,8 +1351,26 @@ static wq_status staged_t(wq_plan_s* pl, const double* kappa, void* vals, cudaSt
   A.nbl = A1.nbl = nbl;
   A.hstart = A1.hstart = hstart;
   A.nbq = A1.nbq = nbq;
-  // tensor-core stage 1: B fragments of the regular rows of direction 1
+  // tensor-core stage 1: B fragments of the regular rows of direction 1; FFMA stage 1
+  // (FP32 G): the float4 tables of the regular rows
+  // FP32 mode: stage 1 by k_stage1_ffma. In the mixed mode the FP64 edge rows bound
+  // stage 1 (the FP64 pipe); k_stage1, whose warps interleave them with FP32 rows,
+  // does as well there.
+  constexpr bool FF = !TC && !EDGE64 && std::is_same<R1, float>::value;
   const int tc_lo = P + 1, tc_rows = TC ? std::max(0, (int)pl->n[0] - 2 * P - 2) : 0;
+  const int ff_rows = FF ? std::max(0, (int)pl->n[0] - 2 * P - 2) : 0;
+  constexpr int FF_TF4 = (2 * P + 1) * (1 + (P + 2) / 2);
+  if (FF && ff_rows > 0) {
+    const size_t fb = (size_t)ff_rows * FF_TF4 * sizeof(float4);
+    if (pl->stg_d_bytes < fb) {
+      plan_free(pl, pl->stg_d, s);
+      pl->stg_d = nullptr;
+      pl->stg_d_bytes = 0;
+      wq_status st2 = plan_alloc(pl, &pl->stg_d, fb, s, "stage-1 row tables");
+      if (st2 != WQ_OK) return st2;
+      pl->stg_d_bytes = fb;
+    }
+  }
   if (TC && tc_rows > 0) {
     using SH = tc::Shape<P, MASS>;
     const size_t fb = (size_t)tc_rows * SH::KS * SH::NT * 32 * sizeof(float4);
@@ -1182,6 +1392,13 @@ static wq_status staged_t(wq_plan_s* pl, const double* kappa, void* vals, cudaSt
   const int n1 = (int)pl->n[0], n2 = (int)pl->n[1];
   int r_lo = P + 1, r_hi = n2 - P - 1;  // regular rows [r_lo, r_hi)
   if (r_hi <= r_lo) r_lo = r_hi = n2;   // no regular rows: every row takes the boundary path
+  if (FF && ff_rows > 0) {
+    const int64_t nf = (int64_t)ff_rows * FF_TF4;
+    k_s1_tables<P, MASS><<<(unsigned)((nf + 255) / 256), 256, 0, s>>>(
+        reinterpret_cast<const float*>(A1.d[0].w), reinterpret_cast<const float*>(A1.d[0].bt), pl->dir[0].q0,
+        pl->dir[0].nq, n1, pl->nq_max, P + 1, ff_rows, reinterpret_cast<float4*>(pl->stg_d));
+    count_launch();
+  }
   if (TC && tc_rows > 0) {
     using SH = tc::Shape<P, MASS>;
     const int64_t nf = (int64_t)tc_rows * SH::KS * SH::NT * 32;
@@ -1225,8 +1442,14 @@ static wq_status staged_t(wq_plan_s* pl, const double* kappa, void* vals, cudaSt
     k_stage2<P, MASS, Real, false, R1, GE>
         <<<dim3((unsigned)(((int64_t)nb * nq1 + 127) / 128), (unsigned)np3), 128, 0, s>>>(A, r_lo, r_hi);
   int gap_lo = 0, gap_len = 0;
-  cudaStream_t s1 = s;  // stream of the FFMA stage-1 kernel
-  if (TC && tc_rows > 0) {
+  cudaStream_t s1 = s;  // stream of the k_stage1 launch (all rows, or the edge rows)
+  if (FF && ff_rows > 0) {
+    const int nch = (ff_rows + 31) / 32;
+    k_stage1_ffma<P, MASS, OutT, EDGE64, GE>
+        <<<dim3((unsigned)(((pl->nnz1[1] + 255) / 256) * (nch + 1)), (unsigned)np3), 256, 0, s>>>(
+            A1, reinterpret_cast<const float4*>(pl->stg_d), P + 1, P + 1 + ff_rows, nch);
+    count_launch();
+  } else if (TC && tc_rows > 0) {
     // the edge rows (double-float, FFMA) run beside the tensor-core kernel on the
     // plan's side stream, forked from and joined back into `s`
     if (!pl->side_stream) {
@@ -1242,18 +1465,19 @@ static wq_status staged_t(wq_plan_s* pl, const double* kappa, void* vals, cudaSt
         <<<dim3((unsigned)((pl->nnz1[1] + SH::MT - 1) / SH::MT), (unsigned)np3,
                 (unsigned)((tc_rows + SH::CHUNK - 1) / SH::CHUNK)),
            32 * SH::WARPS, 0, s>>>(A1, reinterpret_cast<const float4*>(pl->stg_d), tc_lo, tc_lo + tc_rows);
-    count_launch();
     gap_lo = tc_lo;
     gap_len = tc_rows;
+    count_launch();
   }
-  k_stage1<P, MASS, R1, OutT, EDGE64, GE>
-      <<<dim3((unsigned)((pl->nnz1[1] + 31) / 32), (n1 - gap_len + 3) / 4, (unsigned)np3), dim3(32, 4), 0, s1>>>(
-          A1, gap_lo, gap_len);
+  if (!(FF && ff_rows > 0))
+    k_stage1<P, MASS, R1, OutT, EDGE64, GE>
+        <<<dim3((unsigned)((pl->nnz1[1] + 31) / 32), (n1 - gap_len + 3) / 4, (unsigned)np3), dim3(32, 4), 0, s1>>>(
+            A1, gap_lo, gap_len);
   if (s1 != s) {
     WQ_CUDA_TRY(cudaEventRecord(pl->ev_join, s1), "join event");
     WQ_CUDA_TRY(cudaStreamWaitEvent(s, pl->ev_join, 0), "join wait");
   }
-  count_launch(2 + (r_hi > r_lo ? 1 : 0) + (edge2 ? 2 * P + 2 : 1));
+  count_launch(1 + (FF && ff_rows > 0 ? 0 : 1) + (r_hi > r_lo ? 1 : 0) + (edge2 ? 2 * P + 2 : 1));
   WQ_CUDA_TRY(cudaGetLastError(), "staged assembly launch");
   if (hook && hook->after) {
     wq_status hs = hook->after(hook->ctx, i3a, i3b, s);

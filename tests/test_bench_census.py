@@ -64,3 +64,15 @@ def test_source_key_ignores_comments_and_sees_code(tmp_path, monkeypatch):
     src.write_text("__global__ void k(float* a) { a[0] = 2.0f; }\n")
     assert bench.kernel_source_hash() != key
 
+
+
+def test_traffic_capture_scales_by_nonzeros_and_follows_the_sources(monkeypatch):
+    """The captured bytes of the small case are scaled to the bench workload by the nonzeros
+    assembled, for the captured degree only, and dropped once the kernel code changes."""
+    monkeypatch.setitem(bench.TRAFFIC_CAPTURE, "bytes", 1.0e9)
+    monkeypatch.setitem(bench.TRAFFIC_CAPTURE, "nnz", 1.0e8)
+    monkeypatch.setitem(bench.TRAFFIC_CAPTURE, "sources", bench.kernel_source_hash())
+    assert bench.captured_traffic(bench.TRAFFIC_CAPTURE["p"], 4e8) == 4.0e9
+    assert bench.captured_traffic(bench.TRAFFIC_CAPTURE["p"] - 1, 4e8) is None
+    monkeypatch.setitem(bench.TRAFFIC_CAPTURE, "sources", "0" * 16)
+    assert bench.captured_traffic(bench.TRAFFIC_CAPTURE["p"], 4e8) is None

@@ -171,7 +171,7 @@ def test_p4_64_sampled_rows(wq):
     check_rows(orc, plan, M, "mass", rows[:64])
 
 
-@pytest.mark.parametrize("p,count", [(2, 96), (3, 96), (5, 64), (6, 40), (8, 16)])
+@pytest.mark.parametrize("p,count", [(2, 96), (3, 96), (5, 64), (6, 40), (7, 24), (8, 16)])
 def test_degree_sweep_sampled_rows(wq, p, count):
     patch = workload_sweep(p)
     plan, orc = make(wq, patch)

@@ -137,7 +137,7 @@ def _edge_rows(n, p):
     return np.array([(i3 * n[1] + i2) * n[0] + i1 for i3 in picks(n[2]) for i2 in e2 for i1 in picks(n[0])])
 
 
-@pytest.mark.parametrize("p", [2, 3, 4, 5, 6, 8])
+@pytest.mark.parametrize("p", [2, 3, 4, 5, 6, 7, 8])
 @pytest.mark.parametrize("extra", [0, 1])
 def test_staged_edge_rows_compile_time_patterns(wq, p, extra):
     """Direction 2 with n_el = 2p+2 (+1): the first and last p+1 rows take the
@@ -158,7 +158,7 @@ def test_staged_edge_rows_compile_time_patterns(wq, p, extra):
     plan.close()
 
 
-@pytest.mark.parametrize("p", [2, 3, 4, 5, 6, 8])
+@pytest.mark.parametrize("p", [2, 3, 4, 5, 6, 7, 8])
 @pytest.mark.parametrize("which", ["stiffness", "mass"])
 def test_staged_double_float(wq, p, which):
     """WQ_PREC_F32X2 (double-float on the FP32 pipe) holds the FP64 parity bar."""

@@ -1,6 +1,6 @@
 """Pins of the oracle's NURBS geometry, coefficient tensor and NURBS-basis mass
-(the sentence after Eq. (mass2): c absorbs the coefficient of the equation and, for
-NURBS functions, the polynomial denominator; Eq. (coef_stiff) with a tensor K).
+(after Eq. (mass2) the paper lets c take in the PDE coefficient and, for NURBS
+functions, the denominator polynomial; Eq. (coef_stiff) with a tensor K).
 
 - unit (and constant) weights give back the spline map, and constant weights give
   NURBS basis functions equal to the B-splines;
