@@ -256,8 +256,8 @@ wq_status wq_assemble_mass(wq_plan_t plan, const double* d_kappa, void* d_vals,
  *   WQ_ALGO_AUTO   (default) staged
  * All give the same values up to rounding order. WQ_PREC_MIXED and WQ_PREC_F32X2
  * exist only as staged kernels and run staged under every setting; the mixed
- * path adds plan-owned scratch for an FP64 copy of G at the 3p+1 points of each
- * end of direction 1. */
+ * path adds plan-owned scratch for a double-float copy of G at the 3p+1 points of
+ * each end of direction 1. */
 enum { WQ_ALGO_FUSED = 0, WQ_ALGO_STAGED = 1, WQ_ALGO_AUTO = 2 };
 wq_status wq_plan_set_algorithm(wq_plan_t plan, int algorithm);
 

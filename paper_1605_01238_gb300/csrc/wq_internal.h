@@ -142,7 +142,7 @@ struct wq_plan_s {
   double* coefT = nullptr;        // staged: [8][N_QP] transposed coefficients (+ kappa)
   void* stg_a = nullptr;          // staged: T3
   void* stg_b = nullptr;          // staged: G
-  void* stg_c = nullptr;          // staged, mixed precision: FP64 edge copy of G
+  void* stg_c = nullptr;          // staged, mixed precision: double-float edge copy of G
   void* stg_d = nullptr;          // staged, tensor-core stage 1: B fragments of the regular rows
   size_t stg_a_bytes = 0, stg_b_bytes = 0, stg_c_bytes = 0, stg_d_bytes = 0;
   wq_options opt{};               // options given at creation (defaults filled in)

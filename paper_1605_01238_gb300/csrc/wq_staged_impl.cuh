@@ -25,7 +25,7 @@
 //   MIXED       f2 in K3; K2 in f2 for the first and last P+1 rows of direction 2 and
 //               for the points q1 that the first and last P+1 rows of direction 1 read,
 //               float for the rest; float in K1, whose first and last P+1 rows of
-//               direction 1 run in double from an FP64 copy of G that K2 writes for
+//               direction 1 run in f2 from a double-float copy of G that K2 writes for
 //               their points. Near the boundary the WQ weights are large and alternate
 //               in sign, so rounding is amplified only in the stages that contract
 //               over such rows;
@@ -46,6 +46,7 @@ __constant__ int sTermL[9] = {0, 0, 0, 1, 1, 1, 2, 2, 2};
 __constant__ int sTermM[9] = {0, 1, 2, 0, 1, 2, 0, 1, 2};
 // coefficient slot of each term: c_11 c_12 c_13 c_22 c_23 c_33 (c_lm = c_ml)
 __constant__ int sSlot[9] = {0, 1, 2, 1, 3, 4, 2, 4, 5};
+__constant__ int sSlotTerms[6][2] = {{0, -1}, {1, 3}, {2, 6}, {4, -1}, {5, 7}, {8, -1}};  // terms of each slot
 
 // Stage-2 classes of equal (group, b2), terms ordered as sTerm*:
 // class 0: (0,0) g3 b0; 1: (0,1) g2 b1; 2: (0,2) g2 b0; 3: (1,0),(2,0) g1 b0;
@@ -207,9 +208,10 @@ struct StagedArgs {
   void* T3;               // Real [nnz1_3][NT][nqp1][nqp2]
   void* G;                // Real [nnz1_3][NG][nqp1][nnz1_2]
   void* vals;
-  // Mixed precision only: an FP64 copy of G at the q1 points that the first and
-  // last P+1 rows of direction 1 read (q1 < nbl and q1 >= hstart), and the FP64
-  // direction-1 tables, so that stage 1 runs those rows in FP64.
+  // Mixed precision only: a copy of G in the edge-row type GE (double-float) at the
+  // q1 points that the first and last P+1 rows of direction 1 read (q1 < nbl and
+  // q1 >= hstart), and the direction-1 tables in that type, so that stage 1 runs
+  // those rows in it.
   void* Gb;               // NULL or [nnz1_3][NG][nbq][nnz1_2] in the edge-row type GE
   const void* w1e;        // [4][n1][NQ]: direction-1 rules in the edge-row type
   const void* bt1e;       // [2][n1][NQ]
@@ -220,7 +222,7 @@ struct StagedArgs {
   int i3_off;
 };
 
-// position of point q1 in the FP64 edge copy of G (in range for every q1 that a
+// position of point q1 in the edge copy of G (in range for every q1 that a
 // first or last P+1 row of direction 1 reads; clamped for any other q1)
 __device__ __forceinline__ int edge_row(int q1, int nbl, int hstart, int nbq) {
   return q1 < nbl ? q1 : min(nbq - 1, max(nbl, q1 - hstart + nbl));
@@ -317,6 +319,36 @@ __global__ void __launch_bounds__(128) k_stage3(StagedArgs A) {
   const int64_t p3base = D3.prefix[i3] - A.p3_off;  // slab-relative
   Real* T3 = reinterpret_cast<Real*>(A.T3);
   const int nslots = MASS ? 1 : 6;
+  if (i3 >= P + 1 && i3 <= D3.n - P - 2) {
+    // regular row: Q_i3 holds 2P+1 points and the overlap with Q_j3 (jj = j3 - i3 + P)
+    // is t in [2 jj - 2P, 2 jj], known at compile time, so c stays in registers
+#pragma unroll 1
+    for (int s = 0; s < nslots; ++s) {
+      const int slot = MASS ? 6 : s;
+      const Real* cs = tab<Real>(A.cT) + ((int64_t)slot * D3.nqp + qi3) * plane + pt;
+      const Real* ks = A.kappaT ? tab<Real>(A.kappaT) + (int64_t)qi3 * plane + pt : nullptr;
+      Real c[BW];
+#pragma unroll
+      for (int t = 0; t < BW; ++t) c[t] = ks ? mulR(ro(cs + t * plane), ro(ks + t * plane)) : ro(cs + t * plane);
+      for (int k = 0; k < (MASS ? 1 : 2); ++k) {
+        const int term = MASS ? 0 : sSlotTerms[s][k];
+        if (term < 0) break;
+        const int l = MASS ? 0 : sTermL[term], m = MASS ? 0 : sTermM[term];
+        const int k3 = MASS ? 0 : 2 * (l == 2) + (m == 2);
+        Real* dst = T3 + ((p3base * NT + term) * nq1 + q1) * (int64_t)nq2 + q2;
+#pragma unroll
+        for (int jj = 0; jj < BW; ++jj) {
+          const Real* a = a3[k3][jj];
+          Real acc = zeroR<Real>();
+#pragma unroll
+          for (int t = (2 * jj - 2 * P > 0 ? 2 * jj - 2 * P : 0); t <= (2 * jj < 2 * P ? 2 * jj : 2 * P); ++t)
+            acc = fmaR<Real>(a[t], c[t], acc);
+          dst[(int64_t)jj * NT * plane] = acc;
+        }
+      }
+    }
+    return;
+  }
   for (int s = 0; s < nslots; ++s) {
     const int slot = MASS ? 6 : s;
     Real c[MAXQ];
@@ -445,7 +477,7 @@ __global__ void __launch_bounds__(128) k_stage2(StagedArgs A, int r_lo, int r_hi
 
 // Stage 1 for a first or last P+1 row of direction 1: Q_i1 is not the regular
 // 2P+1 window and the band is clipped. G points at (p3, group 0, row 0, p2);
-// MAPQ maps q1 into the FP64 edge copy. out + base + j1 is the value of column j1.
+// MAPQ maps q1 into the edge copy. out + base + j1 is the value of column j1.
 template <int P, bool MASS, typename T, typename OutT, bool MAPQ>
 __device__ __forceinline__ void stage1_edge(const T* G, int64_t gstride, int64_t nnz2, const T* w, int64_t wk,
                                             const T* bt1, int64_t bder, const Dir& D1, int i1, int n1, int NQ,
@@ -504,6 +536,7 @@ __global__ void __launch_bounds__(128) k_stage2_reg(StagedArgs A, int r_lo, int 
   constexpr int CU = ROLL ? 1 : NC;
   __shared__ Real Ws[NK][RW][BW];
   __shared__ Real Bs[NB][NJS][BW];
+  __shared__ GOut stg[4][RW * BW];   // per warp: its 32 rows x BW values of one G row
   const Dir& D2 = A.d[1];
   const int nq1 = A.d[0].nqp, nq2 = D2.nqp, NQ = A.NQ, n2 = D2.n;
   const int i0 = r_lo + blockIdx.x * RW;
@@ -525,12 +558,16 @@ __global__ void __launch_bounds__(128) k_stage2_reg(StagedArgs A, int r_lo, int 
     Bs[b][jr][u] = v;
   }
   __syncthreads();
-  const int i2 = i0 + lane;
-  if (i2 >= r_hi) return;
+  // lanes past r_hi compute on row r_hi - 1 and store nothing
+  const bool act = i0 + lane < r_hi;
+  const int i2 = act ? i0 + lane : r_hi - 1;
+  const int nval = min(RW, r_hi - i0) * BW;  // values of the warp's rows in one G row
   const int64_t nnz2 = A.nnz1[1];
   const int64_t pbase = D2.prefix[i2];
+  const int64_t pbase0 = D2.prefix[i0];     // regular rows: pbase = pbase0 + lane * BW
   const int64_t tstride = (int64_t)nq1 * nq2;
   const TIn* T3p = reinterpret_cast<const TIn*>(A.T3) + (p3 * NT) * tstride + (2 * i2 - P);
+  GOut* sb = stg[warp];
   // volatile views: the compiler would otherwise hoist all of the row's table
   // values out of the q1 loop into registers and spill
   const volatile Real* Wv = &Ws[0][lane][0];
@@ -580,10 +617,17 @@ __global__ void __launch_bounds__(128) k_stage2_reg(StagedArgs A, int r_lo, int 
         for (int v = 0; v < 2; ++v) {
           const int q1 = v ? qb : qa;
           if (v && qb == qa) break;
-          GOut* dst = reinterpret_cast<GOut*>(A.G) + ((p3 * NG + g) * nq1 + q1) * nnz2 + pbase;
+          // the warp's values of this G row are contiguous (pbase0 + lane * BW + tt):
+          // through shared memory, so that each store of the warp is 32 consecutive values
+          __syncwarp();
 #pragma unroll
-          for (int tt = 0; tt < BW; ++tt) dst[tt] = toOut<GOut>(acc[v][tt]);
-          if (sizeof(GOut) < sizeof(Real) && A.Gb && (q1 < A.nbl || q1 >= A.hstart)) {
+          for (int tt = 0; tt < BW; ++tt) sb[lane * BW + tt] = toOut<GOut>(acc[v][tt]);
+          __syncwarp();
+          GOut* dst = reinterpret_cast<GOut*>(A.G) + ((p3 * NG + g) * nq1 + q1) * nnz2 + pbase0;
+#pragma unroll
+          for (int k = 0; k < BW; ++k)
+            if (lane + 32 * k < nval) dst[lane + 32 * k] = sb[lane + 32 * k];
+          if (sizeof(GOut) < sizeof(Real) && A.Gb && act && (q1 < A.nbl || q1 >= A.hstart)) {
             GE* dd = reinterpret_cast<GE*>(A.Gb) + ((p3 * NG + g) * A.nbq + edge_row(q1, A.nbl, A.hstart, A.nbq)) * nnz2 + pbase;
 #pragma unroll
             for (int tt = 0; tt < BW; ++tt) dd[tt] = toOut<GE>(acc[v][tt]);
@@ -698,11 +742,11 @@ static void launch_stage2_edge(const StagedArgs& A, int nq1, int64_t np3, cudaSt
 // K1: one thread per (p2, i1, p3): the 2P+1 values of row (i1, i2, i3) in the
 // column block (j2, j3). A block covers 32 consecutive p2 and 4 consecutive i1, so
 // the G rows of overlapping supports are read from L1.
-// EDGE64: the first and last P+1 rows of direction 1 run in type RE (FP64, or
-// double-float beside the tensor-core kernel) from the edge copy of G, where the
-// large, sign-alternating WQ weights near the boundary amplify FP32 rounding.
-// Rows [gap_lo, gap_lo + gap_len) of direction 1 are skipped (the tensor-core
-// kernel assembles them); gap_len = 0 assembles every row.
+// EDGE64: the first and last P+1 rows of direction 1 run in type RE (double-float)
+// from the edge copy of G, where the large, sign-alternating WQ weights near the
+// boundary amplify FP32 rounding. Rows [gap_lo, gap_lo + gap_len) of direction 1 are
+// skipped (the FFMA or tensor-core kernel assembles them); gap_len = 0 assembles
+// every row.
 template <int P, bool MASS, typename Real, typename OutT, bool EDGE64, typename RE = double>
 __global__ void __launch_bounds__(128) k_stage1(StagedArgs A, int gap_lo, int gap_len) {
   constexpr int BW = 2 * P + 1;
@@ -1044,93 +1088,70 @@ __global__ void k_s1_tables(const float* __restrict__ w1, const float* __restric
   out[e0] = v;
 }
 
-// The first and last P+1 rows of direction 1 for band pair (p2, p3): the support
-// overlaps are clipped there, and in the mixed mode they run in RE from the edge
-// copy of G (the large, sign-alternating boundary weights amplify FP32 rounding).
-template <int P, bool MASS, typename OutT, bool EDGE64, typename RE>
-__device__ void stage1_edge_rows(const StagedArgs& A, int64_t p2, int64_t p3l, int64_t p3) {
-  constexpr int NG = MASS ? 1 : 4;
-  const Dir& D1 = A.d[0];
-  const Dir& D2 = A.d[1];
-  const Dir& D3 = A.d[2];
-  const int64_t nnz2 = A.nnz1[1];
-  if (p2 >= nnz2) return;
-  const int n1 = D1.n, n2 = D2.n, n3 = D3.n, nq1 = D1.nqp, NQ = A.NQ;
-  const int i2 = D2.pair_row[p2], j2 = blo(i2, P) + (int)(p2 - D2.prefix[i2]);
-  const int i3 = D3.pair_row[p3], j3 = blo(i3, P) + (int)(p3 - D3.prefix[i3]);
-  const int bw2 = bw(i2, P, n2), bw3 = bw(i3, P, n3);
-  const int64_t N1 = D1.prefix[n1], N2 = D2.prefix[n2];
-  const int64_t pre23 = D3.prefix[i3] * N2 * N1 + (int64_t)bw3 * D2.prefix[i2] * N1;
-  const int64_t off23 = (int64_t)(j3 - blo(i3, P)) * bw2 + (j2 - blo(i2, P));
-  OutT* out = reinterpret_cast<OutT*>(A.vals);
-  const int64_t wk = (int64_t)n1 * NQ, bder = (int64_t)n1 * NQ;
-  for (int k = 0; k < 2 * P + 2; ++k) {
-    const int i1 = k <= P ? k : n1 - (2 * P + 2) + k;
-    const int bw1 = bw(i1, P, n1), jlo1 = blo(i1, P);
-    const int64_t base = pre23 + (int64_t)bw3 * bw2 * D1.prefix[i1] + off23 * bw1 - jlo1;
-    if (EDGE64 && A.Gb) {
-      const RE* Gd = reinterpret_cast<const RE*>(A.Gb) + ((p3l * NG) * A.nbq) * nnz2 + p2;
-      stage1_edge<P, MASS, RE, OutT, true>(Gd, (int64_t)A.nbq * nnz2, nnz2, tab<RE>(A.w1e) + (size_t)i1 * NQ, wk,
-                                           tab<RE>(A.bt1e), bder, D1, i1, n1, NQ, A.nbl, A.hstart, A.nbq, out, base);
-    } else {
-      const float* G = reinterpret_cast<const float*>(A.G) + ((p3l * NG) * nq1) * nnz2 + p2;
-      stage1_edge<P, MASS, float, OutT, false>(G, (int64_t)nq1 * nnz2, nnz2, tab<float>(D1.w) + (size_t)i1 * NQ, wk,
-                                               tab<float>(D1.bt), bder, D1, i1, n1, NQ, 0, 0, 0, out, base);
-    }
-  }
-}
-
-// blockIdx.x = tile of 256 band pairs * (n_chunks + 1) + role: roles 0 .. n_chunks - 1 take
-// 32 regular rows each, role n_chunks the edge rows of the tile, so that blocks doing
-// the FP64 (or double-float) edge rows run beside blocks doing FP32 regular rows.
-template <int P, bool MASS, typename OutT, bool EDGE64, typename RE>
-__global__ void __launch_bounds__(256) k_stage1_ffma(StagedArgs A, const float4* __restrict__ tabs, int i1_lo,
-                                                     int i1_hi, int n_chunks) {
-  constexpr int BW = 2 * P + 1, NG = MASS ? 1 : 4, MT = 256, CHUNK = 32;
-  const int role = blockIdx.x % (n_chunks + 1);
-  const int64_t p2_0 = (int64_t)(blockIdx.x / (n_chunks + 1)) * MT;
-  if (role == n_chunks) {
-    stage1_edge_rows<P, MASS, OutT, EDGE64, RE>(A, p2_0 + threadIdx.x, blockIdx.y, A.p3_off + blockIdx.y);
-    return;
-  }
+// Regular rows [i1_lo, i1_hi) of direction 1 in chunks of 32 rows (blockIdx.x = tile
+// of 256 band pairs * n_chunks + chunk, blockIdx.y = p3 of the slab). The first and last
+// P+1 rows run in k_stage1 (gap = these rows) beside this kernel on another stream.
+// Each warp hands its 32 x BW values to the CSR through a shared-memory slice: lane l
+// puts its BW values at l * BW + tt (BW odd: no bank conflicts), then the warp stores
+// element e = l + 32 k to out[base + off(e)], where off(e) = X(r) - X(0) + tt +
+// (yb(r) - yb(0)) * prefix1(i1) for r = e / BW, tt = e - r BW, X(r) the row-independent
+// part of lane r's CSR offset and yb(r) = bw3 bw2(r). The relative offsets are fixed
+// for the block, so a store costs a shared load, an integer multiply-add and the store
+// itself; consecutive lanes write consecutive addresses inside each row i2.
+template <int P, bool MASS, typename OutT>
+__global__ void __launch_bounds__(256, 2) k_stage1_ffma(StagedArgs A, const float4* __restrict__ tabs, int i1_lo,
+                                                        int i1_hi, int n_chunks) {
+  constexpr int BW = 2 * P + 1, NG = MASS ? 1 : 4, MT = 256, CHUNK = 32, WARPS = MT / 32;
   // Tables of a row, read as float4 broadcasts: the four rule weights of point t,
   // then for point t the (B, B') values of its band tt = (t + 1)/2 .. (t + 1)/2 + P
   // (P + 1 - (t & 1) of them; the rest zero), in a slot of SL float4.
-  constexpr int SL = (P + 2) / 2;                 // float4 per point: 2 (B, B') pairs each
+  constexpr int SL = (P + 2) / 2;  // float4 per point: 2 (B, B') pairs each
   constexpr int TF4 = BW + BW * SL;
-  __shared__ float stage[2][MT * BW];
   __shared__ float4 tbl[2][TF4];
-  __shared__ int64_t xb[MT];
-  __shared__ int yb[MT];
+  __shared__ float stage[WARPS][32 * BW];
+  __shared__ int soff[BW][MT];     // relative offset of element e = lane + 32 k (INT_MIN: no band pair)
+  __shared__ short syd[BW][MT];    // yb(r) - yb(0)
+  const int role = blockIdx.x % n_chunks;
+  const int64_t p2_0 = (int64_t)(blockIdx.x / n_chunks) * MT;
   const Dir& D1 = A.d[0];
   const Dir& D2 = A.d[1];
   const Dir& D3 = A.d[2];
   const int64_t nnz2 = A.nnz1[1];
   const int64_t p3l = blockIdx.y, p3 = A.p3_off + p3l;
   const int ia = i1_lo + role * CHUNK, ib = min(i1_hi, ia + CHUNK);
-  const int n1 = D1.n, n2 = D2.n, n3 = D3.n, nq1 = D1.nqp, NQ = A.NQ;
+  const int n1 = D1.n, n2 = D2.n, n3 = D3.n, nq1 = D1.nqp;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   // tables of row i1 (precomputed by k_s1_tables), one row ahead through cp.async
   auto build = [&](int i1, float4* t4) {
     for (int e = threadIdx.x; e < TF4; e += blockDim.x) tc::cp_async16(t4 + e, tabs + (size_t)(i1 - i1_lo) * TF4 + e);
   };
   build(ia, tbl[0]);
-  {
-    const int i3 = D3.pair_row[p3], j3 = blo(i3, P) + (int)(p3 - D3.prefix[i3]);
-    const int bw3 = bw(i3, P, n3);
-    const int64_t N1 = D1.prefix[n1], N2 = D2.prefix[n2];
-    for (int r = threadIdx.x; r < MT; r += blockDim.x) {
-      const int64_t q2 = p2_0 + r;
-      if (q2 < nnz2) {
-        const int i2 = D2.pair_row[q2], j2 = blo(i2, P) + (int)(q2 - D2.prefix[i2]);
-        const int bw2 = bw(i2, P, n2);
-        xb[r] = D3.prefix[i3] * N2 * N1 + (int64_t)bw3 * D2.prefix[i2] * N1 +
-                ((int64_t)(j3 - blo(i3, P)) * bw2 + (j2 - blo(i2, P))) * BW;
-        yb[r] = bw3 * bw2;
-      }
-    }
-  }
+  const int i3 = D3.pair_row[p3], j3 = blo(i3, P) + (int)(p3 - D3.prefix[i3]);
+  const int bw3 = bw(i3, P, n3);
+  const int64_t N1 = D1.prefix[n1], N2 = D2.prefix[n2];
   const int64_t p2 = p2_0 + threadIdx.x;
   const bool ok = p2 < nnz2;
+  // this lane's X and yb (the CSR offset of its block of row i1 is X + yb * prefix1(i1))
+  int64_t X = 0;
+  int yb = 0;
+  if (ok) {
+    const int i2 = D2.pair_row[p2], j2 = blo(i2, P) + (int)(p2 - D2.prefix[i2]);
+    const int bw2 = bw(i2, P, n2);
+    X = D3.prefix[i3] * N2 * N1 + (int64_t)bw3 * D2.prefix[i2] * N1 +
+        ((int64_t)(j3 - blo(i3, P)) * bw2 + (j2 - blo(i2, P))) * BW;
+    yb = bw3 * bw2;
+  }
+  const int64_t X0 = __shfl_sync(0xffffffffu, X, 0);
+  const int yb0 = __shfl_sync(0xffffffffu, yb, 0);
+#pragma unroll
+  for (int k = 0; k < BW; ++k) {
+    const int e = lane + 32 * k, r = e / BW;
+    const int64_t Xr = __shfl_sync(0xffffffffu, X, r);
+    const int ybr = __shfl_sync(0xffffffffu, yb, r);
+    const bool okr = p2_0 + warp * 32 + r < nnz2;
+    soff[k][threadIdx.x] = okr ? (int)(Xr - X0) + (e - r * BW) : INT_MIN;
+    syd[k][threadIdx.x] = (short)(ybr - yb0);
+  }
   const float* G = reinterpret_cast<const float*>(A.G) + (p3l * NG) * (int64_t)nq1 * nnz2 + (ok ? p2 : 0);
   const int64_t gstride = (int64_t)nq1 * nnz2;
   auto ldg = [&](int g, int q) { return (ok && q < nq1) ? __ldg(G + g * gstride + (int64_t)q * nnz2) : 0.0f; };
@@ -1145,6 +1166,7 @@ __global__ void __launch_bounds__(256) k_stage1_ffma(StagedArgs A, const float4*
   tc::cp_async_wait_all();
   __syncthreads();
   OutT* out = reinterpret_cast<OutT*>(A.vals);
+  float* sb = stage[warp];
   for (int i1 = ia; i1 < ib; ++i1) {
     const int cur = (i1 - ia) & 1;
     const bool more = i1 + 1 < ib;
@@ -1174,9 +1196,6 @@ __global__ void __launch_bounds__(256) k_stage1_ffma(StagedArgs A, const float4*
                                                            : fmaf(bv.w, h1, fmaf(bv.z, h0, sacc[tt0 + 2 * m + 1]));
       }
     }
-    float* sb = stage[cur];
-#pragma unroll
-    for (int tt = 0; tt < BW; ++tt) sb[threadIdx.x * BW + tt] = sacc[tt];
     if (more) {  // the window moves by two points
       const int qn = D1.q0[i1 + 1];
 #pragma unroll
@@ -1187,14 +1206,96 @@ __global__ void __launch_bounds__(256) k_stage1_ffma(StagedArgs A, const float4*
         gw[g][BW - 1] = ldg(g, qn + BW - 1);
       }
     }
+    __syncwarp();
+#pragma unroll
+    for (int tt = 0; tt < BW; ++tt) sb[lane * BW + tt] = sacc[tt];
+    __syncwarp();
+    const int pre = (int)D1.prefix[i1];
+    OutT* ob = out + (X0 + (int64_t)yb0 * pre);
+#pragma unroll
+    for (int k = 0; k < BW; ++k) {
+      const int o = soff[k][threadIdx.x];
+      if (o != INT_MIN) ob[o + (int)syd[k][threadIdx.x] * pre] = toOut<OutT>(sb[lane + 32 * k]);
+    }
     tc::cp_async_wait_all();
     __syncthreads();
-    const int64_t pre = D1.prefix[i1];
-    for (int e = threadIdx.x; e < MT * BW; e += blockDim.x) {
-      const int r = e / BW;
-      if (p2_0 + r < nnz2) out[xb[r] + (int64_t)yb[r] * pre + (e - r * BW)] = toOut<OutT>(sb[e]);
-    }
   }
+}
+
+// Stage 1 on edge row R of direction 1 (i1 = R or n1-1-R) with its compile-time
+// point pattern (n_el >= 2P+2 in direction 1, as for the stage-2 edge kernels): one
+// thread per band pair p2, a block row per p3. The row's rule weights and trial
+// values (zero outside the support overlap) sit in shared memory; the loop runs over
+// the row's NI points, folds the test weights into h_0, h_1 at the point and adds
+// B h_0 + B' h_1 to the band members whose support holds the point, so no per-point
+// array is kept. RE is the arithmetic: double-float from the edge copy of G (GB, the
+// mixed modes), or FP32 from G itself.
+template <int P, bool MASS, typename RE, typename OutT, bool GB, int R, bool H>
+__global__ void __launch_bounds__(128) k_stage1_edge(StagedArgs A) {
+  constexpr int NI = e_ni(P, R), NJ = e_nj(P, R);
+  constexpr int NG = MASS ? 1 : 4, NB = MASS ? 1 : 2;
+  __shared__ RE ws[NG][NI];
+  __shared__ RE bs[NB][NJ][NI];
+  const Dir& D1 = A.d[0];
+  const Dir& D2 = A.d[1];
+  const Dir& D3 = A.d[2];
+  const int n1 = D1.n, n2 = D2.n, n3 = D3.n, nq1 = D1.nqp, NQ = A.NQ;
+  const int i1 = H ? n1 - 1 - R : R, jlo = H ? n1 - 1 - R - P : 0, qi = H ? nq1 - NI : 0;
+  const RE* w1 = tab<RE>(GB ? A.w1e : D1.w);
+  const RE* b1 = tab<RE>(GB ? A.bt1e : D1.bt);
+  for (int e = threadIdx.x; e < NG * NI; e += blockDim.x) {
+    const int g = e / NI, t = e - g * NI;
+    ws[g][t] = w1[((size_t)g * n1 + i1) * NQ + t];
+  }
+  for (int e = threadIdx.x; e < NB * NJ * NI; e += blockDim.x) {
+    const int b = e / (NJ * NI), jj = (e / NI) % NJ, t = e % NI;
+    const int j1 = jlo + jj, loc = qi + t - D1.q0[j1];
+    bs[b][jj][t] = (loc >= 0 && loc < D1.nq[j1]) ? b1[((size_t)b * n1 + j1) * NQ + loc] : zeroR<RE>();
+  }
+  __syncthreads();
+  const int64_t nnz2 = A.nnz1[1];
+  const int64_t p2 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (p2 >= nnz2) return;
+  const int64_t p3l = blockIdx.y, p3 = A.p3_off + p3l;
+  const int nrow = GB ? A.nbq : nq1;                       // rows of the G array read
+  const int r0 = GB ? (H ? A.nbq - NI : 0) : qi;           // its row of point qi
+  const RE* G = reinterpret_cast<const RE*>(GB ? A.Gb : A.G) + ((p3l * NG) * nrow + r0) * nnz2 + p2;
+  const int64_t gstride = (int64_t)nrow * nnz2;
+  RE acc[NJ];
+#pragma unroll
+  for (int jj = 0; jj < NJ; ++jj) acc[jj] = zeroR<RE>();
+#pragma unroll 1
+  for (int t = 0; t < NI; ++t) {
+    const RE* gq = G + (int64_t)t * nnz2;
+    RE h0, h1 = zeroR<RE>();
+    if (MASS) {
+      h0 = mulR(ws[0][t], ro(gq));
+    } else {
+      h0 = fmaR<RE>(ws[0][t], ro(gq), mulR(ws[2][t], ro(gq + 2 * gstride)));
+      h1 = fmaR<RE>(ws[1][t], ro(gq + gstride), mulR(ws[3][t], ro(gq + 3 * gstride)));
+    }
+#pragma unroll
+    for (int jj = 0; jj < NJ; ++jj)
+      if (t >= e_tlo(P, R, H, jj) && t < e_thi(P, R, H, jj))
+        acc[jj] = MASS ? fmaR<RE>(bs[0][jj][t], h0, acc[jj])
+                       : fmaR<RE>(bs[1][jj][t], h1, fmaR<RE>(bs[0][jj][t], h0, acc[jj]));
+  }
+  const int i2 = D2.pair_row[p2], j2 = blo(i2, P) + (int)(p2 - D2.prefix[i2]);
+  const int i3 = D3.pair_row[p3], j3 = blo(i3, P) + (int)(p3 - D3.prefix[i3]);
+  const int bw2 = bw(i2, P, n2), bw3 = bw(i3, P, n3);
+  const int64_t N1 = D1.prefix[n1], N2 = D2.prefix[n2];
+  const int64_t base = D3.prefix[i3] * N2 * N1 + (int64_t)bw3 * (D2.prefix[i2] * N1 + (int64_t)bw2 * D1.prefix[i1]) +
+                       ((int64_t)(j3 - blo(i3, P)) * bw2 + (j2 - blo(i2, P))) * NJ;
+  OutT* out = reinterpret_cast<OutT*>(A.vals) + base;
+#pragma unroll
+  for (int jj = 0; jj < NJ; ++jj) out[jj] = toOut<OutT>(acc[jj]);
+}
+
+template <int P, bool MASS, typename RE, typename OutT, bool GB, int B = 0>
+static void launch_stage1_edge(const StagedArgs& A, int64_t np3, cudaStream_t s) {
+  k_stage1_edge<P, MASS, RE, OutT, GB, (B <= P ? B : B - P - 1), (B > P)>
+      <<<dim3((unsigned)((A.nnz1[1] + 127) / 128), (unsigned)np3), 128, 0, s>>>(A);
+  if constexpr (B + 1 < 2 * P + 2) launch_stage1_edge<P, MASS, RE, OutT, GB, B + 1>(A, np3, s);
 }
 
 __global__ void k_pair_rows(const int64_t* __restrict__ prefix, int n, int* __restrict__ pair_row) {
@@ -1275,13 +1376,13 @@ static wq_status staged_t(wq_plan_s* pl, const double* kappa, void* vals, cudaSt
   const int NT = MASS ? 1 : 9, NG = MASS ? 1 : 4;
   constexpr bool EDGE64 = sizeof(R1) < sizeof(Real);
   static_assert(!TC || std::is_same<R1, float>::value, "the tensor-core stage 1 reads FP32 G");
-  // arithmetic of the first and last P+1 rows of direction 1 in the mixed modes: FP64
-  // where they share a launch with the FP32 rows (the FP64 pipe is otherwise idle),
-  // double-float where they run in a launch of their own beside the tensor cores
-  using GE = typename std::conditional<TC, Real, double>::type;
+  // arithmetic of the first and last P+1 rows of direction 1 in the mixed modes:
+  // double-float, in launches of their own beside the kernel of the regular rows
+  // (their FP64 form is bound by the FP64 pipe: 7.6 ms against 3.2 ms at p = 5, 128^3)
+  using GE = Real;
   int nbl = 0, hstart = 0, nbq = 0;
   if (EDGE64) edge_points(pl, &nbl, &hstart, &nbq);
-  // slabs of direction 3: T3, G and the FP64 edge copy of G hold one slab at a time
+  // slabs of direction 3: T3, G and the edge copy of G hold one slab at a time
   const int n3 = (int)pl->n[2];
   std::vector<int64_t> P3(n3 + 1, 0);  // prefix sums of the band widths of direction 3
   for (int i = 0; i < n3; ++i) P3[i + 1] = P3[i] + (std::min(n3 - 1, i + P) - std::max(0, i - P) + 1);
@@ -1353,10 +1454,10 @@ static wq_status staged_t(wq_plan_s* pl, const double* kappa, void* vals, cudaSt
   A.nbq = A1.nbq = nbq;
   // tensor-core stage 1: B fragments of the regular rows of direction 1; FFMA stage 1
   // (FP32 G): the float4 tables of the regular rows
-  // FP32 mode: stage 1 by k_stage1_ffma. In the mixed mode the FP64 edge rows bound
-  // stage 1 (the FP64 pipe); k_stage1, whose warps interleave them with FP32 rows,
-  // does as well there.
-  constexpr bool FF = !TC && !EDGE64 && std::is_same<R1, float>::value;
+  // FP32 G (FP32 and mixed modes): the regular rows of stage 1 by k_stage1_ffma, the
+  // first and last P+1 rows beside it on the side stream (k_stage1_edge, or k_stage1
+  // where the two ends of direction 1 meet)
+  constexpr bool FF = !TC && std::is_same<R1, float>::value;
   const int tc_lo = P + 1, tc_rows = TC ? std::max(0, (int)pl->n[0] - 2 * P - 2) : 0;
   const int ff_rows = FF ? std::max(0, (int)pl->n[0] - 2 * P - 2) : 0;
   constexpr int FF_TF4 = (2 * P + 1) * (1 + (P + 2) / 2);
@@ -1443,15 +1544,9 @@ static wq_status staged_t(wq_plan_s* pl, const double* kappa, void* vals, cudaSt
         <<<dim3((unsigned)(((int64_t)nb * nq1 + 127) / 128), (unsigned)np3), 128, 0, s>>>(A, r_lo, r_hi);
   int gap_lo = 0, gap_len = 0;
   cudaStream_t s1 = s;  // stream of the k_stage1 launch (all rows, or the edge rows)
-  if (FF && ff_rows > 0) {
-    const int nch = (ff_rows + 31) / 32;
-    k_stage1_ffma<P, MASS, OutT, EDGE64, GE>
-        <<<dim3((unsigned)(((pl->nnz1[1] + 255) / 256) * (nch + 1)), (unsigned)np3), 256, 0, s>>>(
-            A1, reinterpret_cast<const float4*>(pl->stg_d), P + 1, P + 1 + ff_rows, nch);
-    count_launch();
-  } else if (TC && tc_rows > 0) {
-    // the edge rows (double-float, FFMA) run beside the tensor-core kernel on the
-    // plan's side stream, forked from and joined back into `s`
+  if ((FF && ff_rows > 0) || (TC && tc_rows > 0)) {
+    // the edge rows run beside the kernel of the regular rows on the plan's side
+    // stream, forked from and joined back into `s`
     if (!pl->side_stream) {
       WQ_CUDA_TRY(cudaStreamCreateWithFlags(&pl->side_stream, cudaStreamNonBlocking), "side stream");
       WQ_CUDA_TRY(cudaEventCreateWithFlags(&pl->ev_fork, cudaEventDisableTiming), "fork event");
@@ -1460,6 +1555,16 @@ static wq_status staged_t(wq_plan_s* pl, const double* kappa, void* vals, cudaSt
     WQ_CUDA_TRY(cudaEventRecord(pl->ev_fork, s), "fork event");
     WQ_CUDA_TRY(cudaStreamWaitEvent(pl->side_stream, pl->ev_fork, 0), "fork wait");
     s1 = pl->side_stream;
+  }
+  if (FF && ff_rows > 0) {
+    const int nch = (ff_rows + 31) / 32;
+    k_stage1_ffma<P, MASS, OutT>
+        <<<dim3((unsigned)(((pl->nnz1[1] + 255) / 256) * nch), (unsigned)np3), 256, 0, s>>>(
+            A1, reinterpret_cast<const float4*>(pl->stg_d), P + 1, P + 1 + ff_rows, nch);
+    gap_lo = P + 1;
+    gap_len = ff_rows;
+    count_launch();
+  } else if (TC && tc_rows > 0) {
     using SH = tc::Shape<P, MASS>;
     tc::k_stage1_mma<P, MASS, OutT>
         <<<dim3((unsigned)((pl->nnz1[1] + SH::MT - 1) / SH::MT), (unsigned)np3,
@@ -1469,7 +1574,13 @@ static wq_status staged_t(wq_plan_s* pl, const double* kappa, void* vals, cudaSt
     gap_len = tc_rows;
     count_launch();
   }
-  if (!(FF && ff_rows > 0))
+  // the first and last P+1 rows of direction 1: with compile-time point patterns
+  // where the two ends of direction 1 are apart, else by k_stage1
+  const bool edge1 = gap_len > 0 && gap_lo == P + 1 && gap_len == n1 - 2 * P - 2 && pl->dir[0].n_el >= 2 * P + 2;
+  if constexpr (FF || TC) {
+    if (edge1) launch_stage1_edge<P, MASS, typename std::conditional<EDGE64, GE, R1>::type, OutT, EDGE64>(A1, np3, s1);
+  }
+  if (!edge1 && n1 > gap_len)
     k_stage1<P, MASS, R1, OutT, EDGE64, GE>
         <<<dim3((unsigned)((pl->nnz1[1] + 31) / 32), (n1 - gap_len + 3) / 4, (unsigned)np3), dim3(32, 4), 0, s1>>>(
             A1, gap_lo, gap_len);
@@ -1477,7 +1588,7 @@ static wq_status staged_t(wq_plan_s* pl, const double* kappa, void* vals, cudaSt
     WQ_CUDA_TRY(cudaEventRecord(pl->ev_join, s1), "join event");
     WQ_CUDA_TRY(cudaStreamWaitEvent(s, pl->ev_join, 0), "join wait");
   }
-  count_launch(1 + (FF && ff_rows > 0 ? 0 : 1) + (r_hi > r_lo ? 1 : 0) + (edge2 ? 2 * P + 2 : 1));
+  count_launch(1 + (edge1 ? 2 * P + 2 : n1 > gap_len ? 1 : 0) + (r_hi > r_lo ? 1 : 0) + (edge2 ? 2 * P + 2 : 1));
   WQ_CUDA_TRY(cudaGetLastError(), "staged assembly launch");
   if (hook && hook->after) {
     wq_status hs = hook->after(hook->ctx, i3a, i3b, s);
