@@ -251,8 +251,9 @@ wq_status wq_assemble_mass(wq_plan_t plan, const double* d_kappa, void* d_vals,
  *   WQ_ALGO_STAGED three kernels, one per mode product, over the whole mesh; every
  *                  intermediate is computed once and kept in device memory. The
  *                  first staged call allocates plan-owned scratch of
- *                  nnz1_3 * (9 nqp1 nqp2 + 4 nqp1 nnz1_2) values (nnz1_l = band
- *                  pairs of direction l; 2.3 GB in FP64 at p = 4, 64^3).
+ *                  nnz1_3 * (9 nqp1 nqp2' + 4 nqp1 nnz1_2) values (nnz1_l = band
+ *                  pairs of direction l, nqp2' = nqp2 rounded up to even; 2.3 GB in
+ *                  FP64 at p = 4, 64^3).
  *   WQ_ALGO_AUTO   (default) staged
  * All give the same values up to rounding order. WQ_PREC_MIXED and WQ_PREC_F32X2
  * exist only as staged kernels and run staged under every setting; the mixed

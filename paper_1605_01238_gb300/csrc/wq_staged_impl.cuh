@@ -205,7 +205,8 @@ struct StagedArgs {
   int64_t nnz1[3];
   const void* cT;         // Real [7][nqp3][nqp1][nqp2]
   const void* kappaT;     // NULL or Real [nqp3][nqp1][nqp2]
-  void* T3;               // Real [nnz1_3][NT][nqp1][nqp2]
+  void* T3;               // Real [nnz1_3][NT][nqp1][t3w]: rows of nqp2 values padded to even t3w
+  int t3w;
   void* G;                // Real [nnz1_3][NG][nqp1][nnz1_2]
   void* vals;
   // Mixed precision only: a copy of G in the edge-row type GE (double-float) at the
@@ -216,6 +217,8 @@ struct StagedArgs {
   const void* w1e;        // [4][n1][NQ]: direction-1 rules in the edge-row type
   const void* bt1e;       // [2][n1][NQ]
   int nbl, hstart, nbq;
+  // the same point ranges of direction 2 (the q2 that its first and last P+1 rows read)
+  int nbl2, hstart2;
   // Slab of direction 3: rows i3 in [i3_off, i3_off + n3 of the launch), band pairs
   // p3 in [p3_off, ...); T3, G and Gb hold the slab only (index p3 - p3_off).
   int64_t p3_off;
@@ -231,6 +234,23 @@ __device__ __forceinline__ int edge_row(int q1, int nbl, int hstart, int nbq) {
 template <typename Real>
 __device__ __forceinline__ const Real* tab(const void* p) { return reinterpret_cast<const Real*>(p); }
 
+// two consecutive values of an array (p at an even index of a 16-byte aligned
+// array), in one vector load
+template <typename T>
+__device__ __forceinline__ void ld2(const T* p, T& a, T& b);
+template <>
+__device__ __forceinline__ void ld2<float>(const float* p, float& a, float& b) {
+  const float2 v = __ldg(reinterpret_cast<const float2*>(p));
+  a = v.x;
+  b = v.y;
+}
+template <>
+__device__ __forceinline__ void ld2<double>(const double* p, double& a, double& b) {
+  const double2 v = __ldg(reinterpret_cast<const double2*>(p));
+  a = v.x;
+  b = v.y;
+}
+
 // Loads of data that no kernel of the launch writes (tables, T3 in stage 2, G in
 // stage 1) go through the read-only path, so the compiler may move them across
 // the kernel's own stores.
@@ -240,6 +260,12 @@ template <>
 __device__ __forceinline__ f2 ro<f2>(const f2* p) {
   const float2 v = __ldg(reinterpret_cast<const float2*>(p));
   return f2{v.x, v.y};
+}
+template <>
+__device__ __forceinline__ void ld2<f2>(const f2* p, f2& a, f2& b) {
+  const float4 v = __ldg(reinterpret_cast<const float4*>(p));
+  a = f2{v.x, v.y};
+  b = f2{v.z, v.w};
 }
 
 __global__ void k_to_float(const double* __restrict__ in, float* __restrict__ out, int64_t n) {
@@ -274,9 +300,53 @@ __global__ void k_transpose_coef(const double* __restrict__ c, const double* __r
   }
 }
 
+// K3 on a regular row i3 (Q_i3 holds 2P+1 points; the overlap with Q_j3, jj = j3 -
+// i3 + P, is t in [2 jj - 2P, 2 jj], known at compile time, so c stays in registers),
+// in arithmetic T on tables and coefficients stored as Real.
+template <int P, bool MASS, typename T, typename Real>
+__device__ __forceinline__ void stage3_regular(const StagedArgs& A, const Real* a3, Real* T3, int i3, int q1, int q2,
+                                               int64_t p3base) {
+  constexpr int MAXQ = 4 * P + 1;
+  constexpr int NT = MASS ? 1 : 9;
+  constexpr int BW = 2 * P + 1;
+  const Dir& D3 = A.d[2];
+  const int nq1 = A.d[0].nqp, nq2 = A.d[1].nqp;
+  const int qi3 = D3.q0[i3];
+  const int64_t plane = (int64_t)nq1 * nq2;
+  const int64_t pt = (int64_t)q1 * nq2 + q2;
+  const int64_t tplane = (int64_t)nq1 * A.t3w;
+  const int nslots = MASS ? 1 : 6;
+#pragma unroll 1
+  for (int s = 0; s < nslots; ++s) {
+    const int slot = MASS ? 6 : s;
+    const Real* cs = tab<Real>(A.cT) + ((int64_t)slot * D3.nqp + qi3) * plane + pt;
+    const Real* ks = A.kappaT ? tab<Real>(A.kappaT) + (int64_t)qi3 * plane + pt : nullptr;
+    T c[BW];
+#pragma unroll
+    for (int t = 0; t < BW; ++t)
+      c[t] = ks ? mulR(fromStore<T>(ro(cs + t * plane)), fromStore<T>(ro(ks + t * plane))) : fromStore<T>(ro(cs + t * plane));
+    for (int k = 0; k < (MASS ? 1 : 2); ++k) {
+      const int term = MASS ? 0 : sSlotTerms[s][k];
+      if (term < 0) break;
+      const int l = MASS ? 0 : sTermL[term], m = MASS ? 0 : sTermM[term];
+      const int k3 = MASS ? 0 : 2 * (l == 2) + (m == 2);
+      Real* dst = T3 + ((p3base * NT + term) * nq1 + q1) * (int64_t)A.t3w + q2;
+#pragma unroll
+      for (int jj = 0; jj < BW; ++jj) {
+        const Real* a = a3 + (k3 * BW + jj) * MAXQ;
+        T acc = zeroR<T>();
+#pragma unroll
+        for (int t = (2 * jj - 2 * P > 0 ? 2 * jj - 2 * P : 0); t <= (2 * jj < 2 * P ? 2 * jj : 2 * P); ++t)
+          acc = fmaR<T>(fromStore<T>(a[t]), c[t], acc);
+        dst[(int64_t)jj * NT * tplane] = toOut<Real>(acc);
+      }
+    }
+  }
+}
+
 // K3: one thread per (q2, q1, i3); all terms and all j3 of the band. Blocks with
 // consecutive i3 (blockIdx.x) read overlapping coefficient planes back to back.
-template <int P, bool MASS, typename Real>
+template <int P, bool MASS, typename Real, bool SEL = false>
 __global__ void __launch_bounds__(128) k_stage3(StagedArgs A) {
   constexpr int MAXQ = 4 * P + 1;
   constexpr int NT = MASS ? 1 : 9;
@@ -319,34 +389,15 @@ __global__ void __launch_bounds__(128) k_stage3(StagedArgs A) {
   const int64_t p3base = D3.prefix[i3] - A.p3_off;  // slab-relative
   Real* T3 = reinterpret_cast<Real*>(A.T3);
   const int nslots = MASS ? 1 : 6;
-  if (i3 >= P + 1 && i3 <= D3.n - P - 2) {
-    // regular row: Q_i3 holds 2P+1 points and the overlap with Q_j3 (jj = j3 - i3 + P)
-    // is t in [2 jj - 2P, 2 jj], known at compile time, so c stays in registers
-#pragma unroll 1
-    for (int s = 0; s < nslots; ++s) {
-      const int slot = MASS ? 6 : s;
-      const Real* cs = tab<Real>(A.cT) + ((int64_t)slot * D3.nqp + qi3) * plane + pt;
-      const Real* ks = A.kappaT ? tab<Real>(A.kappaT) + (int64_t)qi3 * plane + pt : nullptr;
-      Real c[BW];
-#pragma unroll
-      for (int t = 0; t < BW; ++t) c[t] = ks ? mulR(ro(cs + t * plane), ro(ks + t * plane)) : ro(cs + t * plane);
-      for (int k = 0; k < (MASS ? 1 : 2); ++k) {
-        const int term = MASS ? 0 : sSlotTerms[s][k];
-        if (term < 0) break;
-        const int l = MASS ? 0 : sTermL[term], m = MASS ? 0 : sTermM[term];
-        const int k3 = MASS ? 0 : 2 * (l == 2) + (m == 2);
-        Real* dst = T3 + ((p3base * NT + term) * nq1 + q1) * (int64_t)nq2 + q2;
-#pragma unroll
-        for (int jj = 0; jj < BW; ++jj) {
-          const Real* a = a3[k3][jj];
-          Real acc = zeroR<Real>();
-#pragma unroll
-          for (int t = (2 * jj - 2 * P > 0 ? 2 * jj - 2 * P : 0); t <= (2 * jj < 2 * P ? 2 * jj : 2 * P); ++t)
-            acc = fmaR<Real>(a[t], c[t], acc);
-          dst[(int64_t)jj * NT * plane] = acc;
-        }
-      }
-    }
+  if (!std::is_same<Real, double>::value && i3 >= P + 1 && i3 <= D3.n - P - 2) {
+    // regular row (FP64 stays on the loop below: the FP64 pipe bounds it either way,
+    // and it measured 10% faster at p = 8). SEL (the mixed modes): double-float only
+    // at the points whose T3 value a first or last P+1 row of direction 1 or 2 reads
+    // later (there the large boundary weights amplify its rounding), FP32 elsewhere
+    if (SEL && !(q1 < A.nbl || q1 >= A.hstart || q2 < A.nbl2 || q2 >= A.hstart2))
+      stage3_regular<P, MASS, float, Real>(A, &a3[0][0][0], T3, i3, q1, q2, p3base);
+    else
+      stage3_regular<P, MASS, Real, Real>(A, &a3[0][0][0], T3, i3, q1, q2, p3base);
     return;
   }
   for (int s = 0; s < nslots; ++s) {
@@ -363,7 +414,7 @@ __global__ void __launch_bounds__(128) k_stage3(StagedArgs A) {
         const Real* a = a3[k3][jj];
         Real acc = zeroR<Real>();
         for (int t = olo[jj]; t < ohi[jj]; ++t) acc = fmaR<Real>(a[t], c[t], acc);
-        T3[(((p3base + jj) * NT + term) * nq1 + q1) * nq2 + q2] = acc;
+        T3[(((p3base + jj) * NT + term) * nq1 + q1) * (int64_t)A.t3w + q2] = acc;
       }
     }
   }
@@ -385,7 +436,7 @@ __global__ void __launch_bounds__(128) k_stage2(StagedArgs A, int r_lo, int r_hi
   constexpr bool ROLL = std::is_same<Real, f2>::value;
   constexpr int CU = ROLL ? 1 : NC;
   const Dir& D2 = A.d[1];
-  const int nq1 = A.d[0].nqp, nq2 = D2.nqp, NQ = A.NQ;
+  const int nq1 = A.d[0].nqp, NQ = A.NQ;
   const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t p3 = blockIdx.y;
   int i2, q1;
@@ -402,8 +453,8 @@ __global__ void __launch_bounds__(128) k_stage2(StagedArgs A, int r_lo, int r_hi
     i2 = b < r_lo ? b : r_hi + (b - r_lo);
   }
   const int64_t nnz2 = A.nnz1[1];
-  const Real* T3 = reinterpret_cast<const Real*>(A.T3) + ((p3 * NT) * nq1 + q1) * (int64_t)nq2;
-  const int64_t tstride = (int64_t)nq1 * nq2;
+  const Real* T3 = reinterpret_cast<const Real*>(A.T3) + ((p3 * NT) * nq1 + q1) * (int64_t)A.t3w;
+  const int64_t tstride = (int64_t)nq1 * A.t3w;
   const int qi = D2.q0[i2], ni = REG ? BW : D2.nq[i2];
   const int jlo = blo(i2, P), jhi = min(D2.n - 1, i2 + P);
   const int64_t pbase = D2.prefix[i2];
@@ -538,7 +589,7 @@ __global__ void __launch_bounds__(128) k_stage2_reg(StagedArgs A, int r_lo, int 
   __shared__ Real Bs[NB][NJS][BW];
   __shared__ GOut stg[4][RW * BW];   // per warp: its 32 rows x BW values of one G row
   const Dir& D2 = A.d[1];
-  const int nq1 = A.d[0].nqp, nq2 = D2.nqp, NQ = A.NQ, n2 = D2.n;
+  const int nq1 = A.d[0].nqp, NQ = A.NQ, n2 = D2.n;
   const int i0 = r_lo + blockIdx.x * RW;
   const int64_t p3 = blockIdx.y;
   const int lane = threadIdx.x, warp = threadIdx.y, tid = warp * 32 + lane;
@@ -565,29 +616,38 @@ __global__ void __launch_bounds__(128) k_stage2_reg(StagedArgs A, int r_lo, int 
   const int64_t nnz2 = A.nnz1[1];
   const int64_t pbase = D2.prefix[i2];
   const int64_t pbase0 = D2.prefix[i0];     // regular rows: pbase = pbase0 + lane * BW
-  const int64_t tstride = (int64_t)nq1 * nq2;
-  const TIn* T3p = reinterpret_cast<const TIn*>(A.T3) + (p3 * NT) * tstride + (2 * i2 - P);
+  const int64_t tstride = (int64_t)nq1 * A.t3w;
+  // the row's window q2 in [2 i2 - P, 2 i2 + P] is read as NV pairs from the even
+  // index 2 i2 - P - O (rows of T3 have even length): value t is entry t + O
+  constexpr int O = P & 1, NV = (BW + O + 1) / 2;
+  const TIn* T3p = reinterpret_cast<const TIn*>(A.T3) + (p3 * NT) * tstride + (2 * i2 - P - O);
   GOut* sb = stg[warp];
   // volatile views: the compiler would otherwise hoist all of the row's table
   // values out of the q1 loop into registers and spill
   const volatile Real* Wv = &Ws[0][lane][0];
   const volatile Real* Bv = &Bs[0][lane][0];
-  // two q1 points per iteration: every shared-memory value feeds two FMA chains
+  // NQB q1 points per iteration: every shared-memory value feeds NQB FMA chains (4
+  // measured no faster in FP32: the registers it takes cost occupancy)
+  constexpr int NQB = 2;
 #pragma unroll 1
-  for (int qa = q_lo + 2 * warp; qa < q_hi; qa += 8) {
-    const int qb = min(qa + 1, q_hi - 1);  // the last iteration may repeat qa
-    const TIn* Ta = T3p + (int64_t)qa * nq2;
-    const TIn* Tb = T3p + (int64_t)qb * nq2;
-    Real acc[2][BW];
+  for (int qa = q_lo + NQB * warp; qa < q_hi; qa += 4 * NQB) {
+    const TIn* Tq[NQB];
+#pragma unroll
+    for (int v = 0; v < NQB; ++v) Tq[v] = T3p + (int64_t)min(qa + v, q_hi - 1) * A.t3w;  // the last may repeat
+    Real acc[NQB][BW];
 #pragma unroll(CU)
     for (int c = 0; c < NC; ++c) {
       const ClassInfo ci = class_info<ROLL>(c);
       if (MASS || ci.first)
 #pragma unroll
-        for (int tt = 0; tt < BW; ++tt) acc[0][tt] = acc[1][tt] = zeroR<Real>();
-      Real h[2][BW];
+        for (int tt = 0; tt < BW; ++tt)
 #pragma unroll
-      for (int t = 0; t < BW; ++t) h[0][t] = h[1][t] = zeroR<Real>();
+          for (int v = 0; v < NQB; ++v) acc[v][tt] = zeroR<Real>();
+      Real h[NQB][BW];
+#pragma unroll
+      for (int t = 0; t < BW; ++t)
+#pragma unroll
+        for (int v = 0; v < NQB; ++v) h[v][t] = zeroR<Real>();
 #pragma unroll
       for (int k = 0; k < 2; ++k) {
         const int term = MASS ? 0 : ci.term[k];
@@ -595,10 +655,19 @@ __global__ void __launch_bounds__(128) k_stage2_reg(StagedArgs A, int r_lo, int 
         const int l = MASS ? 0 : term / 3, m = MASS ? 0 : term % 3;
         const int k2 = MASS ? 0 : 2 * (l == 1) + (m == 1);
 #pragma unroll
-        for (int t = 0; t < BW; ++t) {
-          const Real wv = vld(Wv + k2 * RW * BW + t);
-          h[0][t] = fmaR<Real>(wv, fromStore<Real>(ro(Ta + term * tstride + t)), h[0][t]);
-          h[1][t] = fmaR<Real>(wv, fromStore<Real>(ro(Tb + term * tstride + t)), h[1][t]);
+        for (int pv = 0; pv < NV; ++pv) {
+          TIn a[NQB][2];
+#pragma unroll
+          for (int v = 0; v < NQB; ++v) ld2(Tq[v] + term * tstride + 2 * pv, a[v][0], a[v][1]);
+#pragma unroll
+          for (int u = 0; u < 2; ++u) {
+            const int t = 2 * pv + u - O;
+            if (t >= 0 && t < BW) {
+              const Real wv = vld(Wv + k2 * RW * BW + t);
+#pragma unroll
+              for (int v = 0; v < NQB; ++v) h[v][t] = fmaR<Real>(wv, fromStore<Real>(a[v][u]), h[v][t]);
+            }
+          }
         }
       }
       const int g = MASS ? 0 : ci.g;
@@ -609,14 +678,14 @@ __global__ void __launch_bounds__(128) k_stage2_reg(StagedArgs A, int r_lo, int 
         for (int t = 0; t < BW; ++t)
           if (t >= 2 * tt - 2 * P && t <= 2 * tt) {
             const Real bv = vld(Bv + (b2 * NJS + tt) * BW + t - 2 * tt + 2 * P);
-            acc[0][tt] = fmaR<Real>(bv, h[0][t], acc[0][tt]);
-            acc[1][tt] = fmaR<Real>(bv, h[1][t], acc[1][tt]);
+#pragma unroll
+            for (int v = 0; v < NQB; ++v) acc[v][tt] = fmaR<Real>(bv, h[v][t], acc[v][tt]);
           }
       if (MASS || ci.last) {
 #pragma unroll
-        for (int v = 0; v < 2; ++v) {
-          const int q1 = v ? qb : qa;
-          if (v && qb == qa) break;
+        for (int v = 0; v < NQB; ++v) {
+          const int q1 = qa + v;
+          if (q1 >= q_hi) break;
           // the warp's values of this G row are contiguous (pbase0 + lane * BW + tt):
           // through shared memory, so that each store of the warp is 32 consecutive values
           __syncwarp();
@@ -666,21 +735,23 @@ __device__ __forceinline__ void stage2_edge_row(const StagedArgs& A, int q1, int
   constexpr int NG = MASS ? 1 : 4;
   constexpr int NC = MASS ? 1 : 6;
   constexpr int NI = e_ni(P, R), NJ = e_nj(P, R);
-  constexpr bool ROLL = std::is_same<Real, f2>::value;
-  constexpr int CU = ROLL ? 1 : NC;
+  constexpr int CU = 1;  // classes rolled: unrolled, the six classes took 255 registers and spilled
   const Dir& D2 = A.d[1];
   const int nq1 = A.d[0].nqp, nq2 = D2.nqp, NQ = A.NQ, n2 = D2.n;
   const int i2 = H ? n2 - 1 - R : R;
   const int qi = H ? nq2 - NI : 0;
   const int jlo = H ? n2 - 1 - R - P : 0;
   const int64_t nnz2 = A.nnz1[1];
-  const Real* T3 = reinterpret_cast<const Real*>(A.T3) + ((p3 * NT) * nq1 + q1) * (int64_t)nq2 + qi;
-  const int64_t tstride = (int64_t)nq1 * nq2;
+  // the row's points are read as NV pairs from the even index qi - O (nq2 is odd, so
+  // qi = nq2 - NI has the parity of P at the high end; T3 rows have even length)
+  constexpr int O = H ? (P & 1) : 0, NV = (NI + O + 1) / 2;
+  const Real* T3 = reinterpret_cast<const Real*>(A.T3) + ((p3 * NT) * nq1 + q1) * (int64_t)A.t3w + qi - O;
+  const int64_t tstride = (int64_t)nq1 * A.t3w;
   const int64_t pbase = D2.prefix[i2];
   Real acc[NJ];  // one G group at a time (classes come grouped)
 #pragma unroll(CU)
   for (int c = 0; c < NC; ++c) {
-    const ClassInfo ci = class_info<ROLL>(c);
+    const ClassInfo ci = class_info<true>(c);  // rolled: from constant memory
     if (MASS || ci.first)
 #pragma unroll
       for (int jj = 0; jj < NJ; ++jj) acc[jj] = zeroR<Real>();
@@ -696,7 +767,15 @@ __device__ __forceinline__ void stage2_edge_row(const StagedArgs& A, int q1, int
       const Real* wrow = tab<Real>(D2.w) + ((size_t)k2 * n2 + i2) * NQ;
       const Real* trow = T3 + term * tstride;
 #pragma unroll
-      for (int t = 0; t < NI; ++t) h[t] = fmaR<Real>(ro(wrow + t), ro(trow + t), h[t]);
+      for (int v = 0; v < NV; ++v) {
+        Real a[2];
+        ld2(trow + 2 * v, a[0], a[1]);
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+          const int t = 2 * v + u - O;
+          if (t >= 0 && t < NI) h[t] = fmaR<Real>(ro(wrow + t), a[u], h[t]);
+        }
+      }
     }
     const int g = MASS ? 0 : ci.g;
     const int b2 = MASS ? 0 : ci.b2;
@@ -1099,7 +1178,7 @@ __global__ void k_s1_tables(const float* __restrict__ w1, const float* __restric
 // for the block, so a store costs a shared load, an integer multiply-add and the store
 // itself; consecutive lanes write consecutive addresses inside each row i2.
 template <int P, bool MASS, typename OutT>
-__global__ void __launch_bounds__(256, 2) k_stage1_ffma(StagedArgs A, const float4* __restrict__ tabs, int i1_lo,
+__global__ void __launch_bounds__(256, P <= 6 ? 2 : 1) k_stage1_ffma(StagedArgs A, const float4* __restrict__ tabs, int i1_lo,
                                                         int i1_hi, int n_chunks) {
   constexpr int BW = 2 * P + 1, NG = MASS ? 1 : 4, MT = 256, CHUNK = 32, WARPS = MT / 32;
   // Tables of a row, read as float4 broadcasts: the four rule weights of point t,
@@ -1107,10 +1186,15 @@ __global__ void __launch_bounds__(256, 2) k_stage1_ffma(StagedArgs A, const floa
   // (P + 1 - (t & 1) of them; the rest zero), in a slot of SL float4.
   constexpr int SL = (P + 2) / 2;  // float4 per point: 2 (B, B') pairs each
   constexpr int TF4 = BW + BW * SL;
-  __shared__ float4 tbl[2][TF4];
-  __shared__ float stage[WARPS][32 * BW];
-  __shared__ int soff[BW][MT];     // relative offset of element e = lane + 32 k (INT_MIN: no band pair)
-  __shared__ short syd[BW][MT];    // yb(r) - yb(0)
+  // dynamic shared memory (ffma_smem<P>() bytes): the tables of the chunk's rows,
+  // loaded once, so the warps run through the rows without block barriers; the
+  // per-warp store slices; the store offsets
+  extern __shared__ float4 dsm[];
+  float4* tbl = dsm;                                                 // [CHUNK][TF4]
+  float* stage = reinterpret_cast<float*>(dsm + CHUNK * TF4);        // [WARPS][32 BW]
+  int* soff = reinterpret_cast<int*>(stage + WARPS * 32 * BW);       // [BW][MT]: relative offset of
+                                                                     // element e = lane + 32 k (INT_MIN: none)
+  short* syd = reinterpret_cast<short*>(soff + BW * MT);             // [BW][MT]: yb(r) - yb(0)
   const int role = blockIdx.x % n_chunks;
   const int64_t p2_0 = (int64_t)(blockIdx.x / n_chunks) * MT;
   const Dir& D1 = A.d[0];
@@ -1121,11 +1205,9 @@ __global__ void __launch_bounds__(256, 2) k_stage1_ffma(StagedArgs A, const floa
   const int ia = i1_lo + role * CHUNK, ib = min(i1_hi, ia + CHUNK);
   const int n1 = D1.n, n2 = D2.n, n3 = D3.n, nq1 = D1.nqp;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  // tables of row i1 (precomputed by k_s1_tables), one row ahead through cp.async
-  auto build = [&](int i1, float4* t4) {
-    for (int e = threadIdx.x; e < TF4; e += blockDim.x) tc::cp_async16(t4 + e, tabs + (size_t)(i1 - i1_lo) * TF4 + e);
-  };
-  build(ia, tbl[0]);
+  // tables of the chunk's rows (precomputed by k_s1_tables), through cp.async
+  for (int e = threadIdx.x; e < (ib - ia) * TF4; e += blockDim.x)
+    tc::cp_async16(tbl + e, tabs + (size_t)(ia - i1_lo) * TF4 + e);
   const int i3 = D3.pair_row[p3], j3 = blo(i3, P) + (int)(p3 - D3.prefix[i3]);
   const int bw3 = bw(i3, P, n3);
   const int64_t N1 = D1.prefix[n1], N2 = D2.prefix[n2];
@@ -1149,8 +1231,8 @@ __global__ void __launch_bounds__(256, 2) k_stage1_ffma(StagedArgs A, const floa
     const int64_t Xr = __shfl_sync(0xffffffffu, X, r);
     const int ybr = __shfl_sync(0xffffffffu, yb, r);
     const bool okr = p2_0 + warp * 32 + r < nnz2;
-    soff[k][threadIdx.x] = okr ? (int)(Xr - X0) + (e - r * BW) : INT_MIN;
-    syd[k][threadIdx.x] = (short)(ybr - yb0);
+    soff[k * MT + threadIdx.x] = okr ? (int)(Xr - X0) + (e - r * BW) : INT_MIN;
+    syd[k * MT + threadIdx.x] = (short)(ybr - yb0);
   }
   const float* G = reinterpret_cast<const float*>(A.G) + (p3l * NG) * (int64_t)nq1 * nnz2 + (ok ? p2 : 0);
   const int64_t gstride = (int64_t)nq1 * nnz2;
@@ -1166,13 +1248,11 @@ __global__ void __launch_bounds__(256, 2) k_stage1_ffma(StagedArgs A, const floa
   tc::cp_async_wait_all();
   __syncthreads();
   OutT* out = reinterpret_cast<OutT*>(A.vals);
-  float* sb = stage[warp];
+  float* sb = stage + warp * 32 * BW;
   for (int i1 = ia; i1 < ib; ++i1) {
-    const int cur = (i1 - ia) & 1;
     const bool more = i1 + 1 < ib;
-    if (more) build(i1 + 1, tbl[cur ^ 1]);
-    const float4* tw = tbl[cur];
-    const float4* tb = tbl[cur] + BW;
+    const float4* tw = tbl + (i1 - ia) * TF4;
+    const float4* tb = tw + BW;
     float sacc[BW];
 #pragma unroll
     for (int tt = 0; tt < BW; ++tt) sacc[tt] = 0.0f;
@@ -1214,12 +1294,16 @@ __global__ void __launch_bounds__(256, 2) k_stage1_ffma(StagedArgs A, const floa
     OutT* ob = out + (X0 + (int64_t)yb0 * pre);
 #pragma unroll
     for (int k = 0; k < BW; ++k) {
-      const int o = soff[k][threadIdx.x];
-      if (o != INT_MIN) ob[o + (int)syd[k][threadIdx.x] * pre] = toOut<OutT>(sb[lane + 32 * k]);
+      const int o = soff[k * MT + threadIdx.x];
+      if (o != INT_MIN) ob[o + (int)syd[k * MT + threadIdx.x] * pre] = toOut<OutT>(sb[lane + 32 * k]);
     }
-    tc::cp_async_wait_all();
-    __syncthreads();
   }
+}
+
+template <int P>
+constexpr size_t ffma_smem() {
+  return sizeof(float4) * 32 * ((2 * P + 1) * (1 + (P + 2) / 2)) + sizeof(float) * 256 * (2 * P + 1) +
+         (sizeof(int) + sizeof(short)) * 256 * (2 * P + 1);
 }
 
 // Stage 1 on edge row R of direction 1 (i1 = R or n1-1-R) with its compile-time
@@ -1359,8 +1443,8 @@ static wq_status staged_scratch(wq_plan_s* pl, size_t t3, size_t g, size_t gb, b
 // The q1 points that the first and last p+1 rows of direction 1 read: [0, nbl) and
 // [hstart, nqp) (Q_i = points inside the support of B_i; the whole range when the
 // two ends meet).
-static void edge_points(const wq_plan_s* pl, int* nbl, int* hstart, int* nbq) {
-  const int p = pl->p, ne = pl->dir[0].n_el, nqp = (int)pl->nqp[0], n1 = (int)pl->n[0];
+static void edge_points(const wq_plan_s* pl, int* nbl, int* hstart, int* nbq, int dir = 0) {
+  const int p = pl->p, ne = pl->dir[dir].n_el, nqp = (int)pl->nqp[dir], n1 = (int)pl->n[dir];
   const int il = std::min(p, n1 - 1), ih = std::max(n1 - p - 1, 0);
   const int hi = std::min(ne, il + 1), lo = std::max(0, ih - p);
   *nbl = (hi == ne ? nqp - 1 : 2 * hi + p - 2) + 1;
@@ -1386,7 +1470,8 @@ static wq_status staged_t(wq_plan_s* pl, const double* kappa, void* vals, cudaSt
   const int n3 = (int)pl->n[2];
   std::vector<int64_t> P3(n3 + 1, 0);  // prefix sums of the band widths of direction 3
   for (int i = 0; i < n3; ++i) P3[i + 1] = P3[i] + (std::min(n3 - 1, i + P) - std::max(0, i - P) + 1);
-  const size_t per_p3 = (size_t)NT * pl->nqp[0] * pl->nqp[1] * sizeof(Real) +
+  const int t3w = (int)((pl->nqp[1] + 1) & ~1LL);  // T3 row length (even: pair loads)
+  const size_t per_p3 = (size_t)NT * pl->nqp[0] * t3w * sizeof(Real) +
                         (size_t)NG * pl->nqp[0] * pl->nnz1[1] * sizeof(R1) + (size_t)NG * nbq * pl->nnz1[1] * sizeof(GE);
   int rows = hook && hook->rows > 0 ? hook->rows : n3;
   if (!(hook && hook->rows > 0) && pl->opt.scratch_limit > 0)
@@ -1394,7 +1479,7 @@ static wq_status staged_t(wq_plan_s* pl, const double* kappa, void* vals, cudaSt
   rows = std::max(1, std::min(rows, n3));
   int64_t np3_max = 0;
   for (int a = 0; a < n3; a += rows) np3_max = std::max(np3_max, P3[std::min(n3, a + rows)] - P3[a]);
-  wq_status st = staged_scratch(pl, (size_t)np3_max * NT * pl->nqp[0] * pl->nqp[1] * sizeof(Real),
+  wq_status st = staged_scratch(pl, (size_t)np3_max * NT * pl->nqp[0] * t3w * sizeof(Real),
                                 (size_t)np3_max * NG * pl->nqp[0] * pl->nnz1[1] * sizeof(R1),
                                 (size_t)np3_max * NG * nbq * pl->nnz1[1] * sizeof(GE),
                                 sizeof(Real) == sizeof(float) || sizeof(R1) == sizeof(float), s);
@@ -1437,6 +1522,7 @@ static wq_status staged_t(wq_plan_s* pl, const double* kappa, void* vals, cudaSt
     A.nnz1[l] = A1.nnz1[l] = pl->nnz1[l];
   }
   A.NQ = A1.NQ = pl->nq_max;
+  A.t3w = A1.t3w = t3w;
   const int nq1 = (int)pl->nqp[0], nq2 = (int)pl->nqp[1], nq3 = (int)pl->nqp[2];
   const int64_t NQP = pl->n_qp_total;
   Real* cT = reinterpret_cast<Real*>(pl->coefT);
@@ -1452,6 +1538,12 @@ static wq_status staged_t(wq_plan_s* pl, const double* kappa, void* vals, cudaSt
   A.nbl = A1.nbl = nbl;
   A.hstart = A1.hstart = hstart;
   A.nbq = A1.nbq = nbq;
+  {
+    int nbl2 = 0, hstart2 = 0, nbq2 = 0;
+    if (EDGE64) edge_points(pl, &nbl2, &hstart2, &nbq2, 1);
+    A.nbl2 = A1.nbl2 = nbl2;
+    A.hstart2 = A1.hstart2 = hstart2;
+  }
   // tensor-core stage 1: B fragments of the regular rows of direction 1; FFMA stage 1
   // (FP32 G): the float4 tables of the regular rows
   // FP32 G (FP32 and mixed modes): the regular rows of stage 1 by k_stage1_ffma, the
@@ -1513,7 +1605,7 @@ static wq_status staged_t(wq_plan_s* pl, const double* kappa, void* vals, cudaSt
   A.p3_off = A1.p3_off = P3[i3a];
   A.i3_off = A1.i3_off = i3a;
   const int64_t np3 = P3[i3b] - P3[i3a];
-  k_stage3<P, MASS, Real><<<dim3(i3b - i3a, (unsigned)(((int64_t)nq1 * nq2 + 127) / 128)), 128, 0, s>>>(A);
+  k_stage3<P, MASS, Real, EDGE64><<<dim3(i3b - i3a, (unsigned)(((int64_t)nq1 * nq2 + 127) / 128)), 128, 0, s>>>(A);
   // Regular rows: k_stage2_reg (tables in shared memory, 32 rows per block) unless
   // the FP64 pipe, not L1, bounds the flat mapping (FP64, P <= 4: measured at 97%
   // of the DFMA rate) and 32-row blocks would leave more than 4% of lanes idle.
@@ -1558,8 +1650,16 @@ static wq_status staged_t(wq_plan_s* pl, const double* kappa, void* vals, cudaSt
   }
   if (FF && ff_rows > 0) {
     const int nch = (ff_rows + 31) / 32;
+    static unsigned long long smem_set = 0;  // per instantiation, a bit per device
+    int dev = 0;
+    WQ_CUDA_TRY(cudaGetDevice(&dev), "current device");
+    if (dev < 64 && !((smem_set >> dev) & 1ULL)) {
+      WQ_CUDA_TRY(cudaFuncSetAttribute(k_stage1_ffma<P, MASS, OutT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)ffma_smem<P>()), "stage-1 shared memory");
+      smem_set |= 1ULL << dev;
+    }
     k_stage1_ffma<P, MASS, OutT>
-        <<<dim3((unsigned)(((pl->nnz1[1] + 255) / 256) * nch), (unsigned)np3), 256, 0, s>>>(
+        <<<dim3((unsigned)(((pl->nnz1[1] + 255) / 256) * nch), (unsigned)np3), 256, ffma_smem<P>(), s>>>(
             A1, reinterpret_cast<const float4*>(pl->stg_d), P + 1, P + 1 + ff_rows, nch);
     gap_lo = P + 1;
     gap_len = ff_rows;
