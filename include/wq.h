@@ -279,13 +279,18 @@ wq_status wq_plan_set_tiles(wq_plan_t plan, int t1, int t2);
 wq_status wq_plan_get_tiles(wq_plan_t plan, int* t1, int* t2);
 
 /* End-to-end call with host buffers: copies h_ctrl (NULL = keep) to the device,
- * refreshes the plan, assembles S (which = 0) or M (which = 1) in FP64 into the
- * caller's device staging array d_vals (nnz doubles) and copies the values to
- * h_vals (nnz doubles). With the staged algorithm the assembly runs in slabs of
- * direction 3 and each slab's values (a contiguous range of the CSR rows) are
- * copied back on a plan-owned copy stream while the next slab is assembled;
- * page-locked h_vals (wq_host_alloc) makes those copies asynchronous. Returns after
- * both streams have finished. */
+ * refreshes the plan and assembles S (which = 0) or M (which = 1) in FP64 into
+ * h_vals (nnz doubles). With the staged algorithm:
+ *   - h_vals page-locked and addressable by the device (wq_host_alloc, or memory
+ *     registered with the device): the last mode product stores the values straight
+ *     into h_vals, each warp writing runs of consecutive addresses; d_vals is not
+ *     touched (it may be NULL);
+ *   - any other h_vals: the assembly runs in slabs of direction 3 into the device
+ *     staging array d_vals (nnz doubles), and each slab's values (a contiguous range
+ *     of the CSR rows) are copied back on a plan-owned copy stream while the next
+ *     slab is assembled.
+ * Other algorithms assemble into d_vals and copy once. Returns after all work has
+ * finished. */
 wq_status wq_assemble_host(wq_plan_t plan, int which, const double* h_ctrl, double* d_vals,
                            double* h_vals, void* stream);
 

@@ -321,9 +321,10 @@ class Plan:
     def assemble_host(self, which: str, h_ctrl, d_vals, h_vals, stream=None) -> None:
         """End-to-end call with host buffers (wq_assemble_host): h_ctrl host float64
         control points or None, d_vals a CUDA float64 staging tensor of nnz
-        elements, h_vals a host float64 tensor/array of nnz elements."""
+        elements (None when h_vals is a HostBuffer, which the last mode product
+        writes directly), h_vals a host float64 tensor/array of nnz elements."""
         torch = _torch()
-        vp = _dev_ptr(d_vals, torch.float64, self.nnz, "d_vals")
+        vp = None if d_vals is None else _dev_ptr(d_vals, torch.float64, self.nnz, "d_vals")
         if isinstance(h_vals, torch.Tensor):
             if h_vals.is_cuda or h_vals.dtype != torch.float64 or h_vals.numel() != self.nnz:
                 raise ValueError("h_vals must be a host float64 tensor of nnz elements")

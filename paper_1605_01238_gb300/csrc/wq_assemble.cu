@@ -758,18 +758,38 @@ wq_status copy_slab(void* ctx, int i3a, int i3b, cudaStream_t s) {
 
 extern "C" wq_status wq_assemble_host(wq_plan_t plan, int which, const double* h_ctrl, double* d_vals, double* h_vals,
                                       void* stream) {
-  if (!plan || !d_vals || !h_vals || (which != 0 && which != 1)) return set_error(WQ_ERR_INVALID_ARG, "bad argument");
+  if (!plan || !h_vals || (which != 0 && which != 1)) return set_error(WQ_ERR_INVALID_ARG, "bad argument");
   cudaStream_t s = (cudaStream_t)stream;
   wq_status st = wq_plan_refresh(plan, h_ctrl, 0, stream);
   if (st != WQ_OK) return st;
   const bool staged = plan->algorithm == WQ_ALGO_STAGED || plan->algorithm == WQ_ALGO_AUTO;
   if (!staged || plan->opt.checked || plan->nurbs_basis) {
+    if (!d_vals) return set_error(WQ_ERR_INVALID_ARG, "d_vals is NULL");
     st = assemble(plan, which == 1, nullptr, d_vals, WQ_VALUES_F64, WQ_PREC_FP64, stream);
     if (st != WQ_OK) return st;
     WQ_CUDA_TRY(cudaMemcpyAsync(h_vals, d_vals, sizeof(double) * plan->nnz, cudaMemcpyDeviceToHost, s), "value copy");
     WQ_CUDA_TRY(cudaStreamSynchronize(s), "stream synchronize");
     return WQ_OK;
   }
+  // page-locked host values the device can address (wq_host_alloc, or registered
+  // memory): stage 1 stores straight into them, so the values cross the host link once,
+  // as they are produced, with no second pass over device memory and no copy engine
+  cudaPointerAttributes at{};
+  void* h_dev = nullptr;
+  const cudaError_t pe = cudaPointerGetAttributes(&at, h_vals);
+  if (pe == cudaSuccess && at.type == cudaMemoryTypeHost)
+    h_dev = at.devicePointer;
+  else if (pe != cudaSuccess)
+    cudaGetLastError();  // not memory the runtime knows: the copy path below
+  if (h_dev) {
+    wq::SlabHook hook;
+    hook.host_vals = true;
+    st = wq::launch_staged(plan, which == 1, nullptr, h_dev, WQ_VALUES_F64, WQ_PREC_FP64, s, &hook);
+    if (st != WQ_OK) return st;
+    WQ_CUDA_TRY(cudaStreamSynchronize(s), "stream synchronize");
+    return WQ_OK;
+  }
+  if (!d_vals) return set_error(WQ_ERR_INVALID_ARG, "d_vals is NULL and h_vals is not device-addressable page-locked memory");
   if (!plan->copy_stream) {
     WQ_CUDA_TRY(cudaStreamCreateWithFlags(&plan->copy_stream, cudaStreamNonBlocking), "copy stream");
     WQ_CUDA_TRY(cudaEventCreateWithFlags(&plan->slab_done, cudaEventDisableTiming), "slab event");

@@ -193,6 +193,10 @@ struct SlabHook {
   int rows = 0;
   wq_status (*after)(void* ctx, int i3a, int i3b, cudaStream_t s) = nullptr;
   void* ctx = nullptr;
+  // vals is page-locked host memory the device addresses: stage 1 (FP64) stores each
+  // warp's values as runs of consecutive addresses, so that they cross the host link
+  // as whole lines
+  bool host_vals = false;
 };
 
 // vals = NULL: allocate the mode's scratch only (wq_plan_reserve).

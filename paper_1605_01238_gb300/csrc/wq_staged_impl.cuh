@@ -818,6 +818,92 @@ static void launch_stage2_edge(const StagedArgs& A, int nq1, int64_t np3, cudaSt
   if constexpr (B + 1 < 2 * P + 2) launch_stage2_edge<P, MASS, Real, GOut, GE, B + 1>(A, nq1, np3, s);
 }
 
+// Stage 1 of one (p2, i1, p3) for the HOST form of k_stage1: the same arithmetic as
+// k_stage1, the values into the warp's slice sl (lane-major, bw1 per lane), then the
+// warp's stores. Lanes with p2 >= nnz2 compute nothing and store nothing.
+template <int P, bool MASS, typename Real, typename OutT, bool EDGE64, typename RE>
+__device__ __forceinline__ void k_stage1_host(const StagedArgs& A, int64_t p2, int i1, int64_t p3l, int64_t p3, OutT* sl,
+                                              int64_t* hb) {
+  constexpr int BW = 2 * P + 1;
+  constexpr int NG = MASS ? 1 : 4;
+  const Dir& D1 = A.d[0];
+  const Dir& D2 = A.d[1];
+  const Dir& D3 = A.d[2];
+  const int64_t nnz2 = A.nnz1[1];
+  const int n1 = D1.n, n2 = D2.n, n3 = D3.n, nq1 = D1.nqp, NQ = A.NQ;
+  const int lane = threadIdx.x;
+  const bool act = p2 < nnz2;
+  const int bw1 = bw(i1, P, n1), jlo1 = blo(i1, P);
+  if (act) {
+    const int i2 = D2.pair_row[p2], j2 = blo(i2, P) + (int)(p2 - D2.prefix[i2]);
+    const int i3 = D3.pair_row[p3], j3 = blo(i3, P) + (int)(p3 - D3.prefix[i3]);
+    const int qi1 = D1.q0[i1];
+    const bool reg = i1 >= P + 1 && i1 <= n1 - P - 2;
+    const Real* G = reinterpret_cast<const Real*>(A.G) + ((p3l * NG) * nq1) * nnz2 + p2;
+    const int64_t gstride = (int64_t)nq1 * nnz2;
+    const int64_t N1 = D1.prefix[n1], N2 = D2.prefix[n2];
+    const int bw2 = bw(i2, P, n2), bw3 = bw(i3, P, n3);
+    const int64_t row = D3.prefix[i3] * N2 * N1 + (int64_t)bw3 * (D2.prefix[i2] * N1 + (int64_t)bw2 * D1.prefix[i1]);
+    hb[lane] = row + ((int64_t)(j3 - blo(i3, P)) * bw2 + (j2 - blo(i2, P))) * bw1;
+    const Real* w = tab<Real>(D1.w) + (size_t)i1 * NQ;
+    const Real* bt1 = tab<Real>(D1.bt);
+    const int64_t wk = (int64_t)n1 * NQ, bder = (int64_t)n1 * NQ;
+    if (reg) {
+      Real s[BW];
+#pragma unroll
+      for (int tt = 0; tt < BW; ++tt) s[tt] = zeroR<Real>();
+#pragma unroll
+      for (int t = 0; t <= 2 * P; ++t) {
+        const Real* gq = G + (int64_t)(qi1 + t) * nnz2;
+        Real h0, h1 = zeroR<Real>();
+        if (MASS) {
+          h0 = mulR(w[t], gq[0]);
+        } else {
+          h0 = fmaR<Real>(w[t], gq[0], mulR(w[t + 2 * wk], gq[2 * gstride]));
+          h1 = fmaR<Real>(w[t + wk], gq[gstride], mulR(w[t + 3 * wk], gq[3 * gstride]));
+        }
+#pragma unroll
+        for (int tt = 0; tt < BW; ++tt) {
+          if (t >= 2 * tt - 2 * P && t <= 2 * tt) {
+            const int j1 = i1 - P + tt;
+            const int64_t idx = (int64_t)j1 * NQ + (qi1 + t - D1.q0[j1]);
+            if (MASS)
+              s[tt] = fmaR<Real>(bt1[idx], h0, s[tt]);
+            else
+              s[tt] = fmaR<Real>(bt1[idx + bder], h1, fmaR<Real>(bt1[idx], h0, s[tt]));
+          }
+        }
+      }
+#pragma unroll
+      for (int tt = 0; tt < BW; ++tt) sl[lane * BW + tt] = toOut<OutT>(s[tt]);  // bw1 = BW here
+    } else if (EDGE64 && A.Gb) {
+      const RE* Gd = reinterpret_cast<const RE*>(A.Gb) + ((p3l * NG) * A.nbq) * nnz2 + p2;
+      stage1_edge<P, MASS, RE, OutT, true>(Gd, (int64_t)A.nbq * nnz2, nnz2, tab<RE>(A.w1e) + (size_t)i1 * NQ, wk,
+                                           tab<RE>(A.bt1e), bder, D1, i1, n1, NQ, A.nbl, A.hstart, A.nbq, sl,
+                                           (int64_t)lane * bw1 - jlo1);
+    } else {
+      stage1_edge<P, MASS, Real, OutT, false>(G, gstride, nnz2, w, wk, bt1, bder, D1, i1, n1, NQ, 0, 0, 0, sl,
+                                              (int64_t)lane * bw1 - jlo1);
+    }
+  }
+  __syncwarp();
+  OutT* out = reinterpret_cast<OutT*>(A.vals);
+  const int64_t left = nnz2 - (p2 - lane);
+  const int nact = left < 32 ? (int)left : 32;  // active lanes of the warp
+  if (bw1 == BW) {
+#pragma unroll
+    for (int k = 0; k < BW; ++k) {
+      const int e = lane + 32 * k, r = e / BW;
+      if (r < nact) out[hb[r] + (e - r * BW)] = sl[e];
+    }
+  } else {
+    for (int e = lane; e < nact * bw1; e += 32) {
+      const int r = e / bw1;
+      out[hb[r] + (e - r * bw1)] = sl[e];
+    }
+  }
+}
+
 // K1: one thread per (p2, i1, p3): the 2P+1 values of row (i1, i2, i3) in the
 // column block (j2, j3). A block covers 32 consecutive p2 and 4 consecutive i1, so
 // the G rows of overlapping supports are read from L1.
@@ -826,10 +912,16 @@ static void launch_stage2_edge(const StagedArgs& A, int nq1, int64_t np3, cudaSt
 // boundary amplify FP32 rounding. Rows [gap_lo, gap_lo + gap_len) of direction 1 are
 // skipped (the FFMA or tensor-core kernel assembles them); gap_len = 0 assembles
 // every row.
-template <int P, bool MASS, typename Real, typename OutT, bool EDGE64, typename RE = double>
+// HOST: out is page-locked host memory; each warp (one row i1, 32 consecutive p2)
+// puts its values in a shared-memory slice and stores them as runs of consecutive
+// addresses (lane l's bw1 values are contiguous, and neighbouring p2 of one row i2
+// are neighbouring blocks), so the values cross the host link as whole lines.
+template <int P, bool MASS, typename Real, typename OutT, bool EDGE64, typename RE = double, bool HOST = false>
 __global__ void __launch_bounds__(128) k_stage1(StagedArgs A, int gap_lo, int gap_len) {
   constexpr int BW = 2 * P + 1;
   constexpr int NG = MASS ? 1 : 4;
+  __shared__ OutT hs[HOST ? 4 : 1][HOST ? 32 * BW : 1];   // per warp: 32 x bw1 values
+  __shared__ int64_t hb[HOST ? 4 : 1][32];                // per warp: each lane's first address
   const Dir& D1 = A.d[0];
   const Dir& D2 = A.d[1];
   const Dir& D3 = A.d[2];
@@ -839,7 +931,12 @@ __global__ void __launch_bounds__(128) k_stage1(StagedArgs A, int gap_lo, int ga
   const int64_t p3l = blockIdx.z, p3 = A.p3_off + p3l;  // slab-relative and absolute band pair
   const int64_t nnz2 = A.nnz1[1];
   const int n1 = D1.n, n2 = D2.n, n3 = D3.n, nq1 = D1.nqp, NQ = A.NQ;
-  if (p2 >= nnz2 || i1 >= n1) return;
+  if (i1 >= n1) return;                                  // whole warps
+  if (!HOST && p2 >= nnz2) return;
+  if (HOST) {
+    k_stage1_host<P, MASS, Real, OutT, EDGE64, RE>(A, p2, i1, p3l, p3, hs[threadIdx.y], hb[threadIdx.y]);
+    return;
+  }
   const int i2 = D2.pair_row[p2], j2 = blo(i2, P) + (int)(p2 - D2.prefix[i2]);
   const int i3 = D3.pair_row[p3], j3 = blo(i3, P) + (int)(p3 - D3.prefix[i3]);
   const int qi1 = D1.q0[i1];
@@ -1680,10 +1777,16 @@ static wq_status staged_t(wq_plan_s* pl, const double* kappa, void* vals, cudaSt
   if constexpr (FF || TC) {
     if (edge1) launch_stage1_edge<P, MASS, typename std::conditional<EDGE64, GE, R1>::type, OutT, EDGE64>(A1, np3, s1);
   }
-  if (!edge1 && n1 > gap_len)
-    k_stage1<P, MASS, R1, OutT, EDGE64, GE>
-        <<<dim3((unsigned)((pl->nnz1[1] + 31) / 32), (n1 - gap_len + 3) / 4, (unsigned)np3), dim3(32, 4), 0, s1>>>(
-            A1, gap_lo, gap_len);
+  const dim3 g1((unsigned)((pl->nnz1[1] + 31) / 32), (n1 - gap_len + 3) / 4, (unsigned)np3);
+  bool host_done = false;
+  if constexpr (std::is_same<R1, double>::value && std::is_same<OutT, double>::value && !FF && !TC) {
+    if (hook && hook->host_vals) {
+      k_stage1<P, MASS, R1, OutT, EDGE64, GE, true><<<g1, dim3(32, 4), 0, s1>>>(A1, gap_lo, gap_len);
+      host_done = true;
+    }
+  }
+  if (!host_done && !edge1 && n1 > gap_len)
+    k_stage1<P, MASS, R1, OutT, EDGE64, GE><<<g1, dim3(32, 4), 0, s1>>>(A1, gap_lo, gap_len);
   if (s1 != s) {
     WQ_CUDA_TRY(cudaEventRecord(pl->ev_join, s1), "join event");
     WQ_CUDA_TRY(cudaStreamWaitEvent(s, pl->ev_join, 0), "join wait");

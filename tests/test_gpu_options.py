@@ -173,22 +173,28 @@ def test_slabs_of_direction_3_give_identical_values(wq):
         plan.close()
 
 
-def test_end_to_end_call_pipelines_slabs_into_page_locked_memory(wq):
-    """wq_assemble_host (slab by slab, copies on a second stream) returns the device
-    path's values bit for bit, into page-locked (wq_host_alloc) and pageable memory."""
+@pytest.mark.parametrize("p,nel", [(3, (8, 6, 19)), (8, (9, 11, 10))])
+def test_end_to_end_call_into_host_memory(wq, p, nel):
+    """wq_assemble_host returns the device path's values bit for bit: stored straight
+    into page-locked memory by the last mode product (wq_host_alloc, with or without a
+    staging array), and slab by slab through the staging array and a copy stream into
+    pageable memory. n_el = 11 in direction 2 leaves a partial last warp of band pairs."""
     from wq_synth import perturbed_cube
-    patch = perturbed_cube(3, (8, 6, 19), seed=74)
+    patch = perturbed_cube(p, nel, seed=74)
     plan = wq.Plan(patch.p, patch.knots, patch.ctrl)
     S = plan.stiffness().cpu().numpy()
     M = plan.mass().cpu().numpy()
     d = torch.empty(plan.nnz, dtype=torch.float64, device="cuda")
     hb = wq.HostBuffer(plan.nnz)
     for which, want in (("stiffness", S), ("mass", M)):
-        hb.array[:] = np.nan
-        plan.assemble_host(which, patch.ctrl.reshape(-1), d, hb.array)
-        np.testing.assert_array_equal(hb.array, want)
+        for stage in (d, None):
+            hb.array[:] = np.nan
+            plan.assemble_host(which, patch.ctrl.reshape(-1), stage, hb.array)
+            np.testing.assert_array_equal(hb.array, want)
         pageable = np.full(plan.nnz, np.nan)
         plan.assemble_host(which, None, d, pageable)
         np.testing.assert_array_equal(pageable, want)
+    with pytest.raises(wq.WqError):
+        plan.assemble_host("stiffness", None, None, np.zeros(plan.nnz))   # pageable needs staging
     hb.close()
     plan.close()
