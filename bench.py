@@ -48,7 +48,7 @@ METRIC = "WQ 3D stiffness nnz/s and % of HBM-write roofline; mixed vs FP64 at â‰
 # dram__bytes_write.sum on a smaller case of the same degree (the full-size case is
 # too large to capture), scaled to the bench workload by the nonzeros assembled. It
 # is reported only while the kernel sources still hash to the captured value.
-TRAFFIC_CAPTURE = {"p": 8, "workload": "cube_8_32", "nnz": None, "bytes": None, "sources": None,
+TRAFFIC_CAPTURE = {"p": 8, "workload": "cube_8_32", "nnz": 224755712, "bytes": 6271688448, "sources": "3a5508ab4aaf0ac3",
                    "files": ("paper_1605_01238_gb300/csrc/wq_staged_impl.cuh", "paper_1605_01238_gb300/csrc/wq_internal.h")}
 
 
@@ -165,7 +165,7 @@ def workload_sizes(patch):
     return n, int(np.prod(n)), int(nnz)
 
 
-def workload_config(name: str, patch, n_gpus: int) -> dict:
+def workload_config(name: str, patch, n_gpus: int, precision: str = "fp64") -> dict:
     """The `config` object of a bench line; both arms print the same one."""
     n, n_dof, nnz = workload_sizes(patch)
     ne = patch.n_el
@@ -176,7 +176,7 @@ def workload_config(name: str, patch, n_gpus: int) -> dict:
             "geometry": f"degree-{patch.p} spline cube, Greville control points + seeded U[-0.05h, 0.05h] "
                         f"(seed {patch.meta.get('seed')})",
             "step": "plan refresh (points, tables, integrals, rules, CSR pattern, coefficients) "
-                    "+ FP64 stiffness assembly",
+                    + ("+ FP64 stiffness assembly" if precision == "fp64" else f"+ {precision} stiffness assembly"),
             "l2": f"no flush: each step writes {12 * nnz / 1e9:.1f} GB (values + columns) > 126 MB L2",
             "parallelism": f"{n_gpus} independent patches, one per GPU"}
 
@@ -472,14 +472,17 @@ def run_ours(args):
     plan.set_algorithm(args.algo)
     nnz, N = plan.nnz, plan.n_rows
     ctrl_d = torch.as_tensor(patch.ctrl.reshape(-1), device="cuda")
-    vals = torch.empty(nnz, dtype=torch.float64, device="cuda")
+    # --precision (with --steps-only, for profiler captures of the reduced-precision
+    # kernels): the step's assembly in that mode and its value type
+    prec, vdt = PRECISION_MODES[args.precision][:2] if args.precision != "fp64" else ("fp64", "f64")
+    vals = torch.empty(nnz, dtype=torch.float64 if vdt == "f64" else torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
 
     def step(ev=None):
         plan.refresh(ctrl_d)
         if ev is not None:
             ev[0].record(stream)
-        plan.stiffness(out=vals)
+        plan.stiffness(out=vals, dtype=vals.dtype, precision=prec)
         if ev is not None:
             ev[1].record(stream)
 
@@ -511,11 +514,11 @@ def run_ours(args):
     kernel_ms = statistics.mean(a.elapsed_time(b) for a, b in kev)
     plan.sync_check()
     value = aggregate_value(world, nnz, ms_step)
-    config = workload_config(args.workload, patch, args.gpus)
+    config = workload_config(args.workload, patch, args.gpus, args.precision)
     if args.steps_only:
         if rank == 0:
             print(json.dumps({"metric": METRIC, "value": value, "unit": "nnz/s", "ms_per_step": ms_step,
-                              "assembly_ms": kernel_ms, "config": config, "algo": args.algo,
+                              "assembly_ms": kernel_ms, "config": config, "algo": args.algo, "precision": args.precision,
                               "gpu_launches": int(launches)}), flush=True)
         plan.close()
         if dist is not None:
@@ -568,6 +571,9 @@ def run_ours(args):
                                 f"{2 * p + 2} edge-row kernels), k_stage1" if args.algo in ("auto", "staged")
                                 else f"k_assemble<{p},stiffness,fp64> (fused)"),
                      "flops_per_launch": flops,
+                     "traffic_note": "DRAM read + write bytes of one assembly from an ncu capture at p=8, 32^3, "
+                                     "scaled by nnz: an upper estimate (edge rows are 18 of 40 rows per direction "
+                                     "there, 18 of 101 here)",
                      "note": f"FP64 FMA pipe: {fpn:.1f} algorithmic flop/nnz (exact census of the factorisation "
                              f"for this mesh), divided by the call's CUDA-event time; peak = 152 SMs x 2 "
                              f"DFMA/clk x {pk.get('sm_max_mhz', 2070.0):.0f} MHz (derived from unit counts "
@@ -618,8 +624,12 @@ def main():
                     help="skip the precision study and the p=4 assembly")
     ap.add_argument("--steps-only", action="store_true",
                     help="time the steps only (no variants, e2e or CPU baseline); for profiler captures")
+    ap.add_argument("--precision", default="fp64", choices=["fp64"] + list(PRECISION_MODES),
+                    help="with --steps-only: the step's precision mode (default fp64)")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
+    if args.precision != "fp64" and not args.steps_only:
+        ap.error("--precision applies to --steps-only runs")
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)
