@@ -811,12 +811,47 @@ __global__ void __launch_bounds__(128) k_stage2_edge(StagedArgs A, int64_t np3) 
   stage2_edge_row<P, MASS, Real, GOut, R, H, GE>(A, (int)(e % nq1), e / nq1);
 }
 
+// The P+1 edge rows of one side in one launch (FP32): blockIdx.x = tile * (P+1) + R,
+// so the blocks of the rows that read the same T3 points of a tile run together and
+// share them through L2 (as separate launches each row read them from DRAM again, and
+// in FP32 those reads bound the edge kernels: 2.38 -> 1.34 ms at p = 5, 128^3). The
+// double-float and FP64 forms are bound by arithmetic and keep one launch per row (the
+// merged double-float form measured 3.17 -> 3.58 ms: the largest row's registers set
+// every row's occupancy).
+template <int P, bool MASS, typename Real, typename GOut, bool H, typename GE, int R = 0>
+__device__ __forceinline__ void stage2_edge_any(const StagedArgs& A, int r, int q1, int64_t p3) {
+  if (r == R) {
+    stage2_edge_row<P, MASS, Real, GOut, R, H, GE>(A, q1, p3);
+    return;
+  }
+  if constexpr (R < P) stage2_edge_any<P, MASS, Real, GOut, H, GE, R + 1>(A, r, q1, p3);
+}
+
+template <int P, bool MASS, typename Real, typename GOut, bool H, typename GE>
+__global__ void __launch_bounds__(128) k_stage2_edge_side(StagedArgs A, int64_t np3) {
+  const int nq1 = A.d[0].nqp;
+  const int r = blockIdx.x % (P + 1);
+  const int64_t e = (blockIdx.x / (P + 1)) * (int64_t)blockDim.x + threadIdx.x;  // p3 * nq1 + q1
+  if (e >= np3 * nq1) return;
+  stage2_edge_any<P, MASS, Real, GOut, H, GE>(A, r, (int)(e % nq1), e / nq1);
+}
+
 template <int P, bool MASS, typename Real, typename GOut, typename GE, int B = 0>
 static void launch_stage2_edge(const StagedArgs& A, int nq1, int64_t np3, cudaStream_t s) {
-  k_stage2_edge<P, MASS, Real, GOut, (B <= P ? B : B - P - 1), (B > P), GE>
-      <<<(unsigned)((np3 * nq1 + 127) / 128), 128, 0, s>>>(A, np3);
-  if constexpr (B + 1 < 2 * P + 2) launch_stage2_edge<P, MASS, Real, GOut, GE, B + 1>(A, nq1, np3, s);
+  if constexpr (std::is_same<Real, float>::value) {
+    // FP32: one launch per side
+    const unsigned tiles = (unsigned)((np3 * nq1 + 127) / 128);
+    k_stage2_edge_side<P, MASS, Real, GOut, false, GE><<<tiles * (P + 1), 128, 0, s>>>(A, np3);
+    k_stage2_edge_side<P, MASS, Real, GOut, true, GE><<<tiles * (P + 1), 128, 0, s>>>(A, np3);
+  } else {
+    k_stage2_edge<P, MASS, Real, GOut, (B <= P ? B : B - P - 1), (B > P), GE>
+        <<<(unsigned)((np3 * nq1 + 127) / 128), 128, 0, s>>>(A, np3);
+    if constexpr (B + 1 < 2 * P + 2) launch_stage2_edge<P, MASS, Real, GOut, GE, B + 1>(A, nq1, np3, s);
+  }
 }
+
+template <int P, typename Real>
+constexpr int stage2_edge_launches() { return std::is_same<Real, float>::value ? 2 : 2 * P + 2; }
 
 // Stage 1 of one (p2, i1, p3) for the HOST form of k_stage1: the same arithmetic as
 // k_stage1, the values into the warp's slice sl (lane-major, bw1 per lane), then the
@@ -1412,7 +1447,7 @@ constexpr size_t ffma_smem() {
 // array is kept. RE is the arithmetic: double-float from the edge copy of G (GB, the
 // mixed modes), or FP32 from G itself.
 template <int P, bool MASS, typename RE, typename OutT, bool GB, int R, bool H>
-__global__ void __launch_bounds__(128) k_stage1_edge(StagedArgs A) {
+__device__ __forceinline__ void stage1_edge_row(const StagedArgs& A, int64_t tile) {
   constexpr int NI = e_ni(P, R), NJ = e_nj(P, R);
   constexpr int NG = MASS ? 1 : 4, NB = MASS ? 1 : 2;
   __shared__ RE ws[NG][NI];
@@ -1435,7 +1470,7 @@ __global__ void __launch_bounds__(128) k_stage1_edge(StagedArgs A) {
   }
   __syncthreads();
   const int64_t nnz2 = A.nnz1[1];
-  const int64_t p2 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t p2 = tile * blockDim.x + threadIdx.x;
   if (p2 >= nnz2) return;
   const int64_t p3l = blockIdx.y, p3 = A.p3_off + p3l;
   const int nrow = GB ? A.nbq : nq1;                       // rows of the G array read
@@ -1472,11 +1507,40 @@ __global__ void __launch_bounds__(128) k_stage1_edge(StagedArgs A) {
   for (int jj = 0; jj < NJ; ++jj) out[jj] = toOut<OutT>(acc[jj]);
 }
 
+// The P+1 rows of one side in one launch in FP32: blockIdx.x = tile * (P+1) + R, so the
+// rows that read the same points of G run together and share them through L2 (1.60 ->
+// 1.16 ms at p = 5, 128^3); double-float keeps one launch per row (merged, 3.06 -> 4.28
+// ms: it is bound by arithmetic, and the largest row's registers set every row's
+// occupancy).
+template <int P, bool MASS, typename RE, typename OutT, bool GB, bool H, int R = 0>
+__device__ __forceinline__ void stage1_edge_any(const StagedArgs& A, int r, int64_t tile) {
+  if (r == R) {
+    stage1_edge_row<P, MASS, RE, OutT, GB, R, H>(A, tile);
+    return;
+  }
+  if constexpr (R < P) stage1_edge_any<P, MASS, RE, OutT, GB, H, R + 1>(A, r, tile);
+}
+
+template <int P, bool MASS, typename RE, typename OutT, bool GB, bool H>
+__global__ void __launch_bounds__(128) k_stage1_edge(StagedArgs A) {
+  stage1_edge_any<P, MASS, RE, OutT, GB, H>(A, blockIdx.x % (P + 1), blockIdx.x / (P + 1));
+}
+
+template <int P, bool MASS, typename RE, typename OutT, bool GB, int R, bool H>
+__global__ void __launch_bounds__(128) k_stage1_edge_row(StagedArgs A) {
+  stage1_edge_row<P, MASS, RE, OutT, GB, R, H>(A, blockIdx.x);
+}
+
 template <int P, bool MASS, typename RE, typename OutT, bool GB, int B = 0>
 static void launch_stage1_edge(const StagedArgs& A, int64_t np3, cudaStream_t s) {
-  k_stage1_edge<P, MASS, RE, OutT, GB, (B <= P ? B : B - P - 1), (B > P)>
-      <<<dim3((unsigned)((A.nnz1[1] + 127) / 128), (unsigned)np3), 128, 0, s>>>(A);
-  if constexpr (B + 1 < 2 * P + 2) launch_stage1_edge<P, MASS, RE, OutT, GB, B + 1>(A, np3, s);
+  const unsigned tiles = (unsigned)((A.nnz1[1] + 127) / 128);
+  if constexpr (std::is_same<RE, float>::value) {
+    k_stage1_edge<P, MASS, RE, OutT, GB, false><<<dim3(tiles * (P + 1), (unsigned)np3), 128, 0, s>>>(A);
+    k_stage1_edge<P, MASS, RE, OutT, GB, true><<<dim3(tiles * (P + 1), (unsigned)np3), 128, 0, s>>>(A);
+  } else {
+    k_stage1_edge_row<P, MASS, RE, OutT, GB, (B <= P ? B : B - P - 1), (B > P)><<<dim3(tiles, (unsigned)np3), 128, 0, s>>>(A);
+    if constexpr (B + 1 < 2 * P + 2) launch_stage1_edge<P, MASS, RE, OutT, GB, B + 1>(A, np3, s);
+  }
 }
 
 __global__ void k_pair_rows(const int64_t* __restrict__ prefix, int n, int* __restrict__ pair_row) {
@@ -1791,7 +1855,9 @@ static wq_status staged_t(wq_plan_s* pl, const double* kappa, void* vals, cudaSt
     WQ_CUDA_TRY(cudaEventRecord(pl->ev_join, s1), "join event");
     WQ_CUDA_TRY(cudaStreamWaitEvent(s, pl->ev_join, 0), "join wait");
   }
-  count_launch(1 + (edge1 ? 2 * P + 2 : n1 > gap_len ? 1 : 0) + (r_hi > r_lo ? 1 : 0) + (edge2 ? 2 * P + 2 : 1));
+  count_launch(1 + (edge1 ? (std::is_same<typename std::conditional<EDGE64, GE, R1>::type, float>::value ? 2 : 2 * P + 2)
+                          : n1 > gap_len ? 1 : 0) +
+               (r_hi > r_lo ? 1 : 0) + (edge2 ? stage2_edge_launches<P, Real>() : 1));
   WQ_CUDA_TRY(cudaGetLastError(), "staged assembly launch");
   if (hook && hook->after) {
     wq_status hs = hook->after(hook->ctx, i3a, i3b, s);
