@@ -1366,17 +1366,19 @@ __global__ void __launch_bounds__(256, P <= 6 ? 2 : 1) k_stage1_ffma(StagedArgs 
     soff[k * MT + threadIdx.x] = okr ? (int)(Xr - X0) + (e - r * BW) : INT_MIN;
     syd[k * MT + threadIdx.x] = (short)(ybr - yb0);
   }
+  // the thread's G column (lanes past nnz2 read column 0 and store nothing); regular
+  // rows' windows [2 i1 - P, 2 i1 + P] lie inside [0, nq1)
   const float* G = reinterpret_cast<const float*>(A.G) + (p3l * NG) * (int64_t)nq1 * nnz2 + (ok ? p2 : 0);
   const int64_t gstride = (int64_t)nq1 * nnz2;
-  auto ldg = [&](int g, int q) { return (ok && q < nq1) ? __ldg(G + g * gstride + (int64_t)q * nnz2) : 0.0f; };
   float gw[NG][BW];  // the q1 window of this thread's G column
-  {
-    const int qi = D1.q0[ia];
+  const float* gq = G + (int64_t)D1.q0[ia] * nnz2;
 #pragma unroll
-    for (int g = 0; g < NG; ++g)
+  for (int g = 0; g < NG; ++g)
 #pragma unroll
-      for (int t = 0; t < BW; ++t) gw[g][t] = ldg(g, qi + t);
-  }
+    for (int t = 0; t < BW; ++t) gw[g][t] = __ldg(gq + g * gstride + (int64_t)t * nnz2);
+  gq += (int64_t)BW * nnz2;  // the window's next two points (the window moves by two per row)
+  // warps whose band pairs all have yb = yb0 store without the per-element yb term
+  const bool yu = __all_sync(0xffffffffu, !ok || yb == yb0);
   tc::cp_async_wait_all();
   __syncthreads();
   OutT* out = reinterpret_cast<OutT*>(A.vals);
@@ -1409,14 +1411,14 @@ __global__ void __launch_bounds__(256, P <= 6 ? 2 : 1) k_stage1_ffma(StagedArgs 
       }
     }
     if (more) {  // the window moves by two points
-      const int qn = D1.q0[i1 + 1];
 #pragma unroll
       for (int g = 0; g < NG; ++g) {
 #pragma unroll
         for (int t = 0; t + 2 < BW; ++t) gw[g][t] = gw[g][t + 2];
-        gw[g][BW - 2] = ldg(g, qn + BW - 2);
-        gw[g][BW - 1] = ldg(g, qn + BW - 1);
+        gw[g][BW - 2] = __ldg(gq + g * gstride);
+        gw[g][BW - 1] = __ldg(gq + g * gstride + nnz2);
       }
+      gq += 2 * nnz2;
     }
     __syncwarp();
 #pragma unroll
@@ -1424,10 +1426,18 @@ __global__ void __launch_bounds__(256, P <= 6 ? 2 : 1) k_stage1_ffma(StagedArgs 
     __syncwarp();
     const int pre = (int)D1.prefix[i1];
     OutT* ob = out + (X0 + (int64_t)yb0 * pre);
+    if (yu) {
 #pragma unroll
-    for (int k = 0; k < BW; ++k) {
-      const int o = soff[k * MT + threadIdx.x];
-      if (o != INT_MIN) ob[o + (int)syd[k * MT + threadIdx.x] * pre] = toOut<OutT>(sb[lane + 32 * k]);
+      for (int k = 0; k < BW; ++k) {
+        const int o = soff[k * MT + threadIdx.x];
+        if (o != INT_MIN) ob[o] = toOut<OutT>(sb[lane + 32 * k]);
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < BW; ++k) {
+        const int o = soff[k * MT + threadIdx.x];
+        if (o != INT_MIN) ob[o + (int)syd[k * MT + threadIdx.x] * pre] = toOut<OutT>(sb[lane + 32 * k]);
+      }
     }
   }
 }
