@@ -474,7 +474,7 @@ def run_ours(args):
     ctrl_d = torch.as_tensor(patch.ctrl.reshape(-1), device="cuda")
     # --precision (with --steps-only, for profiler captures of the reduced-precision
     # kernels): the step's assembly in that mode and its value type
-    prec, vdt = PRECISION_MODES[args.precision][:2] if args.precision != "fp64" else ("fp64", "f64")
+    prec, vdt = PRECISION_MODES[args.step_precision][:2] if args.step_precision != "fp64" else ("fp64", "f64")
     vals = torch.empty(nnz, dtype=torch.float64 if vdt == "f64" else torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
 
@@ -514,11 +514,11 @@ def run_ours(args):
     kernel_ms = statistics.mean(a.elapsed_time(b) for a, b in kev)
     plan.sync_check()
     value = aggregate_value(world, nnz, ms_step)
-    config = workload_config(args.workload, patch, args.gpus, args.precision)
+    config = workload_config(args.workload, patch, args.gpus, args.step_precision)
     if args.steps_only:
         if rank == 0:
             print(json.dumps({"metric": METRIC, "value": value, "unit": "nnz/s", "ms_per_step": ms_step,
-                              "assembly_ms": kernel_ms, "config": config, "algo": args.algo, "precision": args.precision,
+                              "assembly_ms": kernel_ms, "config": config, "algo": args.algo, "precision": args.step_precision,
                               "gpu_launches": int(launches)}), flush=True)
         plan.close()
         if dist is not None:
@@ -604,7 +604,7 @@ def run_ours(args):
     return 0
 
 
-def main():
+def parse_args(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
@@ -624,12 +624,17 @@ def main():
                     help="skip the precision study and the p=4 assembly")
     ap.add_argument("--steps-only", action="store_true",
                     help="time the steps only (no variants, e2e or CPU baseline); for profiler captures")
-    ap.add_argument("--precision", default="fp64", choices=["fp64"] + list(PRECISION_MODES),
+    ap.add_argument("--precision", dest="step_precision", default="fp64", choices=["fp64"] + list(PRECISION_MODES),
                     help="with --steps-only: the step's precision mode (default fp64)")
-    args = ap.parse_args()
+    args = ap.parse_args(argv)
     args.warmup = max(3, args.warmup)
-    if args.precision != "fp64" and not args.steps_only:
+    if args.step_precision != "fp64" and not args.steps_only:
         ap.error("--precision applies to --steps-only runs")
+    return args
+
+
+def main():
+    args = parse_args()
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

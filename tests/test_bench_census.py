@@ -76,3 +76,15 @@ def test_traffic_capture_scales_by_nonzeros_and_follows_the_sources(monkeypatch)
     assert bench.captured_traffic(bench.TRAFFIC_CAPTURE["p"] - 1, 4e8) is None
     monkeypatch.setitem(bench.TRAFFIC_CAPTURE, "sources", "0" * 16)
     assert bench.captured_traffic(bench.TRAFFIC_CAPTURE["p"], 4e8) is None
+
+
+def test_bench_arguments():
+    """The default run measures the FP64 step and keeps the precision study; --precision
+    selects the step's mode for --steps-only captures only."""
+    a = bench.parse_args([])
+    assert a.step_precision == "fp64" and a.precision is True and a.workload == "sweep8" and a.warmup >= 3
+    b = bench.parse_args(["--steps-only", "--precision", "mixed", "--workload", "p5_128"])
+    assert b.step_precision == "mixed" and bench.PRECISION_MODES[b.step_precision][:2] == ("mixed", "f32")
+    assert bench.parse_args(["--no-precision"]).precision is False
+    with pytest.raises(SystemExit):
+        bench.parse_args(["--precision", "fp32"])
