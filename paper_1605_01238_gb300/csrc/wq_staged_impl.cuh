@@ -1777,11 +1777,15 @@ static wq_status staged_t(wq_plan_s* pl, const double* kappa, void* vals, cudaSt
   A.i3_off = A1.i3_off = i3a;
   const int64_t np3 = P3[i3b] - P3[i3a];
   k_stage3<P, MASS, Real, EDGE64><<<dim3(i3b - i3a, (unsigned)(((int64_t)nq1 * nq2 + 127) / 128)), 128, 0, s>>>(A);
-  // Regular rows: k_stage2_reg (tables in shared memory, 32 rows per block) unless
-  // the FP64 pipe, not L1, bounds the flat mapping (FP64, P <= 4: measured at 97%
-  // of the DFMA rate) and 32-row blocks would leave more than 4% of lanes idle.
+  // Regular rows: k_stage2_reg (tables in shared memory, 32 rows per block) unless,
+  // in FP64, the FP64 pipe bounds the flat mapping too and the 32-row blocks would
+  // leave lanes idle: more than 4% of them for P <= 4 (flat measured at 97% of the DFMA
+  // rate), more than 10% for P = 8 (83 regular rows, 13.5% idle: flat 244.1 ms per step
+  // against 251.2 ms). At p = 5 the flat form measured far slower (121 rows, 5.5% idle:
+  // 155.8 ms against 127.6 ms), so P = 5..7 keep the blocks.
   const int nreg = r_hi - r_lo;
-  const bool flat = std::is_same<Real, double>::value && P <= 4 && 32 * ((nreg + 31) / 32) * 100 > 104 * nreg;
+  const int idle_pct = nreg > 0 ? (int)(100 * (32 * ((nreg + 31) / 32) - nreg) / (32 * ((nreg + 31) / 32))) : 0;
+  const bool flat = std::is_same<Real, double>::value && ((P <= 4 && idle_pct > 3) || (P >= 8 && idle_pct > 10));
   if (nreg > 0 && flat)
     k_stage2<P, MASS, Real, true, R1, GE>
         <<<dim3((unsigned)(((int64_t)nreg * nq1 + 127) / 128), (unsigned)np3), 128, 0, s>>>(A, r_lo, r_hi);
