@@ -811,13 +811,13 @@ __global__ void __launch_bounds__(128) k_stage2_edge(StagedArgs A, int64_t np3) 
   stage2_edge_row<P, MASS, Real, GOut, R, H, GE>(A, (int)(e % nq1), e / nq1);
 }
 
-// The P+1 edge rows of one side in one launch (FP32): blockIdx.x = tile * (P+1) + R,
-// so the blocks of the rows that read the same T3 points of a tile run together and
-// share them through L2 (as separate launches each row read them from DRAM again, and
-// in FP32 those reads bound the edge kernels: 2.38 -> 1.34 ms at p = 5, 128^3). The
-// double-float and FP64 forms are bound by arithmetic and keep one launch per row (the
-// merged double-float form measured 3.17 -> 3.58 ms: the largest row's registers set
-// every row's occupancy).
+// The P+1 edge rows of one side in one launch (FP32, FP64): blockIdx.x = tile * (P+1)
+// + R, so the blocks of the rows that read the same T3 points of a tile run together
+// and share them through L2 (as separate launches each row read them from DRAM again;
+// FP32 2.38 -> 1.34 ms at p = 5, 128^3, FP64 243.96 -> 242.68 ms per step at p = 8,
+// 93^3). The double-float form keeps one launch per row: merged it measured 3.17 ->
+// 3.58 ms (bound by arithmetic, and the largest row's registers set every row's
+// occupancy).
 template <int P, bool MASS, typename Real, typename GOut, bool H, typename GE, int R = 0>
 __device__ __forceinline__ void stage2_edge_any(const StagedArgs& A, int r, int q1, int64_t p3) {
   if (r == R) {
@@ -838,8 +838,8 @@ __global__ void __launch_bounds__(128) k_stage2_edge_side(StagedArgs A, int64_t 
 
 template <int P, bool MASS, typename Real, typename GOut, typename GE, int B = 0>
 static void launch_stage2_edge(const StagedArgs& A, int nq1, int64_t np3, cudaStream_t s) {
-  if constexpr (std::is_same<Real, float>::value) {
-    // FP32: one launch per side
+  if constexpr (!std::is_same<Real, f2>::value) {
+    // FP32, FP64: one launch per side
     const unsigned tiles = (unsigned)((np3 * nq1 + 127) / 128);
     k_stage2_edge_side<P, MASS, Real, GOut, false, GE><<<tiles * (P + 1), 128, 0, s>>>(A, np3);
     k_stage2_edge_side<P, MASS, Real, GOut, true, GE><<<tiles * (P + 1), 128, 0, s>>>(A, np3);
@@ -851,7 +851,7 @@ static void launch_stage2_edge(const StagedArgs& A, int nq1, int64_t np3, cudaSt
 }
 
 template <int P, typename Real>
-constexpr int stage2_edge_launches() { return std::is_same<Real, float>::value ? 2 : 2 * P + 2; }
+constexpr int stage2_edge_launches() { return std::is_same<Real, f2>::value ? 2 * P + 2 : 2; }
 
 // Stage 1 of one (p2, i1, p3) for the HOST form of k_stage1: the same arithmetic as
 // k_stage1, the values into the warp's slice sl (lane-major, bw1 per lane), then the
