@@ -573,8 +573,12 @@ __device__ __forceinline__ void stage1_edge(const T* G, int64_t gstride, int64_t
 // aligned to the regular pattern: Bs[b][j2 - i0 + P][u] is B^(b)_j2 at point 2 j2 - P + u.
 // TIn is the stored type of T3 (the mixed mode runs this kernel in FP32 on double-float
 // T3 for the points q1 that no first or last P+1 row of direction 1 reads).
+// Double-float up to P = 6 is held to 128 registers (4 blocks per SM; a few dozen bytes
+// of spills): 168 registers gave 3 (p = 5, 128^3: mixed 22.04 -> 21.92 ms, f32x2 81.6 ->
+// 79.6 ms); at P = 8 the cap spilled ~0.5 KB per thread.
 template <int P, bool MASS, typename Real, typename GOut, typename TIn = Real, typename GE = Real>
-__global__ void __launch_bounds__(128) k_stage2_reg(StagedArgs A, int r_lo, int r_hi, int q_lo, int q_hi) {
+__global__ void __launch_bounds__(128, std::is_same<Real, f2>::value && P <= 6 ? 4 : 0)
+    k_stage2_reg(StagedArgs A, int r_lo, int r_hi, int q_lo, int q_hi) {
   constexpr int BW = 2 * P + 1;
   constexpr int NT = MASS ? 1 : 9;
   constexpr int NG = MASS ? 1 : 4;
