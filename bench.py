@@ -48,7 +48,7 @@ METRIC = "WQ 3D stiffness nnz/s and % of HBM-write roofline; mixed vs FP64 at â‰
 # dram__bytes_write.sum on a smaller case of the same degree (the full-size case is
 # too large to capture), scaled to the bench workload by the nonzeros assembled. It
 # is reported only while the kernel sources still hash to the captured value.
-TRAFFIC_CAPTURE = {"p": 8, "workload": "cube_8_32", "nnz": 224755712, "bytes": 4941078528, "sources": "539b59ed42a32a8a",
+TRAFFIC_CAPTURE = {"p": 8, "workload": "cube_8_32", "nnz": 224755712, "bytes": 4941111296, "sources": "802675a704c1bf7f",
                    "files": ("paper_1605_01238_gb300/csrc/wq_staged_impl.cuh", "paper_1605_01238_gb300/csrc/wq_internal.h")}
 
 
