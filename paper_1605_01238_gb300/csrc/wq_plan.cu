@@ -468,12 +468,21 @@ __global__ void k_row_ptr(PatternArgs a) {
 // Column indices: one warp per row, ascending j1 + n1 (j2 + n2 j3). Each lane
 // walks its entries e = lane, lane + 32, ... keeping (t1, t2, t3) up to date by
 // carries; N_DOF < 2^31, so the column arithmetic stays in 32 bits.
+// Rows whose band is full in all three directions (every row away from the
+// boundary) share one pattern of column offsets, t1 + n1 t2 + n1 n2 t3 in
+// lexicographic order of (t3, t2, t1): it sits in shared memory (dynamic, (2p+1)^3
+// ints), so such a row costs a load, an add and a store per column.
 __global__ void k_cols(PatternArgs a) {
+  extern __shared__ int tmpl[];
   const int64_t N = (int64_t)a.n1 * a.n2 * a.n3;
   const int lane = threadIdx.x & 31;
   int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   const int n12 = a.n1 * a.n2;
+  const int BW = 2 * a.p + 1, full = BW * BW * BW;
+  for (int e = threadIdx.x; e < full; e += blockDim.x)
+    tmpl[e] = e % BW + a.n1 * ((e / BW) % BW) + n12 * (e / (BW * BW));
+  __syncthreads();
   for (int64_t r = warp; r < N; r += nwarps) {
     const int rr = (int)r;
     const int i1 = rr % a.n1, i2 = (rr / a.n1) % a.n2, i3 = rr / n12;
@@ -481,6 +490,10 @@ __global__ void k_cols(PatternArgs a) {
     const int c0 = band_lo(i1, a.p) + a.n1 * band_lo(i2, a.p) + n12 * band_lo(i3, a.p);
     int32_t* out = a.col + a.row_ptr[r];
     const int cnt = w1 * w2 * w3;
+    if (cnt == full) {
+      for (int e = lane; e < full; e += 32) out[e] = c0 + tmpl[e];
+      continue;
+    }
     int t1 = lane % w1, rest = lane / w1;
     int t2 = rest % w2, t3 = rest / w2;
     const int s1 = 32 % w1, c1 = 32 / w1;        // step of 32 entries: +s1 in t1, +c1 carried to t2
@@ -868,7 +881,8 @@ wq_status run_setup(wq_plan_s* pl, cudaStream_t s, bool with_pattern) {
     int64_t blocks = (warps_needed + 7) / 8;
     int64_t cap = (int64_t)dev_sms * 16;
     if (blocks > cap) blocks = cap;
-    k_cols<<<(unsigned)blocks, 256, 0, s>>>(pa);
+    const int bw = 2 * pl->p + 1;
+    k_cols<<<(unsigned)blocks, 256, sizeof(int) * bw * bw * bw, s>>>(pa);
     count_launch(2);
     WQ_CUDA_TRY(cudaGetLastError(), "pattern kernels");
   }
